@@ -1,0 +1,378 @@
+"""Pins for the FP64 oracle: each test ties an oracle routine to something other
+than itself (a closed form, an invariant, a theorem of the paper, brute force,
+finite differences, or an independent library routine), chosen so that a
+dropped term, a wrong sign, a wrong index or a transposed operand in
+``oracle/lasso_oracle.c`` fails at least one of them.
+
+Citations are to arXiv 1905.11071.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_11071_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dict(n, m, seed):
+    return synth.gaussian_dictionary(n, m, np.random.default_rng(seed)).astype(np.float64)
+
+
+def _lam_frac(D, X, frac):
+    return frac * np.abs(X @ D).max()
+
+
+# --------------------------------------------------------------------------
+# Soft-thresholding (Section 1, after Eq. ista; sign(0) = 0 from Section 2)
+# --------------------------------------------------------------------------
+
+def test_st_closed_form_table():
+    rows = np.loadtxt(os.path.join(GOLDEN, "st_table.txt"), comments="#")
+    for v, u, want in rows:
+        assert oracle.st(v, u) == want, (v, u)
+
+
+# --------------------------------------------------------------------------
+# Gram quantities and lambda_max against independent numpy evaluations
+# --------------------------------------------------------------------------
+
+def test_gram_definition_matches_numpy():
+    rng = np.random.default_rng(3)
+    D = _dict(7, 13, 1)
+    X = rng.standard_normal((9, 7))
+    B, C, xsq = oracle.gram(D, X)
+    np.testing.assert_allclose(B, D.T @ D, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(C, X @ D, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(xsq, (X * X).sum(axis=1), rtol=1e-14)
+    # unit-norm columns: the Gram diagonal is exactly the squared column norms
+    np.testing.assert_allclose(np.diag(B), 1.0, atol=1e-12)
+    assert np.array_equal(B, B.T)
+
+
+def test_lambda_max_matches_numpy():
+    rng = np.random.default_rng(4)
+    D = _dict(6, 11, 2)
+    X = rng.standard_normal((5, 6))
+    np.testing.assert_allclose(oracle.lambda_max(D, X), np.abs(X @ D).max(axis=1), rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Largest eigenvalues: L (Section 1) and L_S (Eq. spca)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 5, 17, 40])
+def test_jacobi_matches_eigvalsh(k):
+    rng = np.random.default_rng(k)
+    A = rng.standard_normal((k, k))
+    A = A + A.T  # symmetric, indefinite: the largest *algebraic* eigenvalue
+    got = oracle.sym_max_eig(A)
+    assert abs(got - np.linalg.eigvalsh(A).max()) <= 1e-11 * max(1.0, abs(got))
+
+
+def test_lipschitz_and_support_lipschitz():
+    D = _dict(10, 24, 5)
+    L = oracle.lipschitz(D)
+    assert abs(L - np.linalg.eigvalsh(D.T @ D).max()) < 1e-11
+    rng = np.random.default_rng(6)
+    for _ in range(5):
+        mask = rng.random(24) < 0.3
+        want = np.linalg.eigvalsh(D[:, mask].T @ D[:, mask]).max() if mask.any() else L
+        assert abs(oracle.support_lipschitz(D, mask, L) - want) < 1e-11
+    # |S| = 1: L_S is the squared column norm (1 for unit columns)
+    for j in (0, 7, 23):
+        mask = np.zeros(24, bool)
+        mask[j] = True
+        assert abs(oracle.support_lipschitz(D, mask, L) - D[:, j] @ D[:, j]) < 1e-14
+    # convention L_empty = L (Eq. spca)
+    assert oracle.support_lipschitz(D, np.zeros(24, bool), L) == L
+    # L_S <= L for every S (Section 3)
+    for _ in range(5):
+        mask = rng.random(24) < 0.6
+        assert oracle.support_lipschitz(D, mask, L) <= L + 1e-12
+
+
+def test_marchenko_pastur_ratio():
+    """Proposition 3.4: L_S / L -> ((1 + sqrt(zeta gamma)) / (1 + sqrt(gamma)))^2
+    for i.i.d. N(0,1) entries, here at the paper's 200 x 600 illustration size
+    (Fig. B.1), gamma = 3."""
+    rng = np.random.default_rng(7)
+    n, m = 200, 600
+    D = rng.standard_normal((n, m))
+    gamma = m / n
+    L = oracle.sym_max_eig(D @ D.T)  # same non-zero spectrum as D^T D
+    for zeta in (0.1, 0.25, 0.5, 0.75):
+        k = int(zeta * m)
+        S = np.sort(rng.choice(m, size=k, replace=False))
+        if k <= n:
+            mask = np.zeros(m, bool)
+            mask[S] = True
+            LS = oracle.support_lipschitz(D, mask, L)
+        else:
+            LS = oracle.sym_max_eig(D[:, S] @ D[:, S].T)
+        want = ((1 + np.sqrt(zeta * gamma)) / (1 + np.sqrt(gamma))) ** 2
+        assert abs(LS / L - want) < 0.06 * want, (zeta, LS / L, want)
+
+
+# --------------------------------------------------------------------------
+# Unfolded proximal gradient (Eq. ista, Eq. pgd, Eq. steprec)
+# --------------------------------------------------------------------------
+
+def test_zero_above_lambda_max_every_variant():
+    """argmin F_x = {0} iff lam >= lam_max (Section 2); from z^(0) = 0 every
+    layer returns exactly 0 because |alpha D^T x| <= alpha lam."""
+    rng = np.random.default_rng(8)
+    D = _dict(8, 16, 8)
+    X = rng.standard_normal((6, 8))
+    lam = np.abs(X @ D).max() * 1.0001
+    L = oracle.lipschitz(D)
+    alpha = np.array([0.3, 1.0, 2.0, 0.5]) / L
+    assert not oracle.pgd(D, X, lam, alpha).any()
+    assert not oracle.ista(D, X, lam, L, 7).any()
+    Z, _, acc, _ = oracle.oista(D, X, lam, L, 7)
+    assert not Z.any()
+
+
+def test_ista_objective_monotone():
+    """ISTA is a majorisation-minimisation step (Eq. majorization2), so
+    F_x(z^(t+1)) <= F_x(z^(t)) when the step is 1/L (or smaller)."""
+    w = synth.ista_10x20(N=20, T=60)
+    D = w.D.astype(np.float64)
+    L = oracle.lipschitz(D)
+    for scale in (1.0, 0.5):
+        Zall = oracle.pgd(D, w.X, w.lam, np.full(w.T, scale / L), keep_all=True)
+        F = np.stack([oracle.objective(D, w.X, Zall[t], w.lam, with_gap=False) for t in range(w.T + 1)])
+        assert (np.diff(F, axis=0) <= 1e-13).all()
+
+
+def test_ista_kkt_at_convergence():
+    """After 10^4 ISTA iterations (the paper's F* recipe, Appendix E) the KKT
+    conditions of Lemma 2.1 hold to 1e-9."""
+    w = synth.ista_10x20(N=5, T=10000)
+    D = w.D.astype(np.float64)
+    L = oracle.lipschitz(D)
+    Z = oracle.ista(D, w.X, w.lam, L, w.T)
+    for i in range(w.N):
+        assert oracle.kkt_violation(D, w.X[i], Z[i], w.lam) < 1e-9
+
+
+def _small_problem(seed, n=6, m=8, frac=0.25):
+    rng = np.random.default_rng(seed)
+    D = _dict(n, m, seed)
+    x = rng.standard_normal(n)
+    lam = frac * np.abs(D.T @ x).max()
+    return D, x, lam
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_bruteforce_matches_ista_limit_and_gap(seed):
+    """Sign enumeration of the KKT system (Lemma 2.1) gives the unique z*
+    (Assumption 2.2 holds a.s.); ISTA converges to it, its duality gap is 0
+    and F* is below every ISTA iterate."""
+    D, x, lam = _small_problem(seed)
+    zstar, count = oracle.lasso_bruteforce(D, x, lam)
+    assert count == 1
+    L = oracle.lipschitz(D)
+    z = oracle.ista(D, x[None, :], lam, L, 20000)[0]
+    np.testing.assert_allclose(z, zstar, atol=1e-8)
+    F, gap = oracle.objective(D, x[None, :], zstar[None, :], lam)
+    assert abs(gap[0]) < 1e-12
+    assert oracle.kkt_violation(D, x, zstar, lam) < 1e-12
+    Zall = oracle.pgd(D, x[None, :], lam, np.full(50, 1.0 / L), keep_all=True)
+    Fs = np.array([oracle.objective(D, x[None, :], Zall[t], lam, with_gap=False)[0] for t in range(51)])
+    assert (Fs >= F[0] - 1e-14).all()
+    # worst-case ISTA rate F(z^t) - F* <= L ||z*||^2 / (2t) (Section 3, after Prop. 3.2)
+    t = np.arange(1, 51)
+    assert (Fs[1:] - F[0] <= L * (zstar @ zstar) / (2 * t) + 1e-14).all()
+
+
+def test_stability_closed_form():
+    """Lemma 4.2: for unit columns, c = max_{l != j} |D_l^T D_j| and
+    x = D_j + eps with eps orthogonal to D_j, ||eps|| < lam (1 - c), the Lasso
+    solution is (1 - lam) e_j."""
+    D = _dict(6, 8, 11)
+    D /= np.linalg.norm(D, axis=0)  # exactly unit columns in float64
+    rng = np.random.default_rng(12)
+    lam = 0.6
+    for j in range(8):
+        c = np.max(np.abs(np.delete(D.T @ D[:, j], j)))
+        assert c < 1
+        e = rng.standard_normal(6)
+        e -= (e @ D[:, j]) * D[:, j]
+        e *= 0.9 * lam * (1 - c) / np.linalg.norm(e)
+        x = D[:, j] + e
+        want = np.zeros(8)
+        want[j] = 1 - lam
+        zstar, count = oracle.lasso_bruteforce(D, x, lam)
+        assert count == 1
+        np.testing.assert_allclose(zstar, want, atol=1e-12)
+        assert oracle.kkt_violation(D, x, want, lam) < 1e-12
+        L = oracle.lipschitz(D)
+        z = oracle.ista(D, x[None, :], lam, L, 5000)[0]
+        np.testing.assert_allclose(z, want, atol=1e-9)
+
+
+def test_orthogonal_dictionary_one_step():
+    """With D^T D = Id (L = 1), one ISTA step from 0 gives ST(D^T x, lam), which
+    is already the Lasso solution (Section 3, before Prop. 3.3); OISTA takes the
+    same step since every L_S equals 1."""
+    rng = np.random.default_rng(13)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 8)))
+    D = Q
+    X = rng.standard_normal((4, 12))
+    lam = 0.3
+    L = oracle.lipschitz(D)
+    assert abs(L - 1.0) < 1e-12
+    z1 = oracle.ista(D, X, lam, L, 1)
+    st = np.sign(X @ D) * np.maximum(np.abs(X @ D) - lam, 0)
+    np.testing.assert_allclose(z1, st, atol=1e-14)
+    for i in range(4):
+        assert oracle.kkt_violation(D, X[i], z1[i], lam) < 1e-13
+    z5 = oracle.ista(D, X, lam, L, 5)
+    np.testing.assert_allclose(z5, z1, atol=1e-14)
+    zo, LS, acc, dec = oracle.oista(D, X, lam, L, 5)
+    np.testing.assert_allclose(zo, z1, atol=1e-14)
+
+
+def test_pgd_step_sequence_is_layerwise():
+    """Eq. steprec with a varying step sequence equals chaining single layers."""
+    w = synth.slista_64x256(N=3, T=6)
+    D = w.D.astype(np.float64)
+    L = oracle.lipschitz(D)
+    alpha = synth.step_sizes(6, 1.0 / L, 0.5, seed=1).astype(np.float64)
+    Zall = oracle.pgd(D, w.X, w.lam, alpha, keep_all=True)
+    # a single layer on an arbitrary start: recompute layer t from z^(t) by hand
+    X = w.X.astype(np.float64)
+    for t in range(6):
+        z = Zall[t]
+        u = z - alpha[t] * ((z @ D.T - X) @ D)
+        want = np.sign(u) * np.maximum(np.abs(u) - alpha[t] * w.lam, 0)
+        np.testing.assert_allclose(Zall[t + 1], want, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Objective and duality gap (Eq. lasso; gap: standard Lasso dual)
+# --------------------------------------------------------------------------
+
+def test_objective_special_values_and_weak_duality():
+    rng = np.random.default_rng(14)
+    D = _dict(9, 30, 14)
+    X = rng.standard_normal((10, 9))
+    lam = 0.2 * np.abs(X @ D).max()
+    F0, gap0 = oracle.objective(D, X, np.zeros((10, 30)), lam)
+    np.testing.assert_allclose(F0, 0.5 * (X * X).sum(axis=1), rtol=1e-14)
+    Z = rng.standard_normal((10, 30)) * (rng.random((10, 30)) < 0.2)
+    F, gap = oracle.objective(D, X, Z, lam)
+    assert (gap >= -1e-12).all()
+    # lam above lam_max: z = 0 is optimal and the gap there is exactly zero
+    big = np.abs(X @ D).max() * 1.01
+    _, g0 = oracle.objective(D, X, np.zeros((10, 30)), big)
+    assert np.abs(g0).max() < 1e-12
+    # scaling: F(z) depends on lam only through lam ||z||_1
+    F2 = oracle.objective(D, X, Z, 2 * lam, with_gap=False)
+    np.testing.assert_allclose(F2 - F, lam * np.abs(Z).sum(axis=1), rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Oracle-ISTA (Algorithm 1)
+# --------------------------------------------------------------------------
+
+def test_oista_monotone_and_safe_regime():
+    """Every OISTA step decreases F_x (Section 3: both branches minimise a
+    majoriser), and after finite support identification condition (star)
+    always holds (Prop. 3.1).  Toy setup of Fig. 3: D 10 x 50, lam = 0.5, x in
+    B_inf."""
+    w = synth.paper_binf(10, 50, N=4, lam=0.5, T=400, seed=3)
+    D = w.D.astype(np.float64)
+    L = oracle.lipschitz(D)
+    Zall, LS, acc, dec = oracle.oista(D, w.X, w.lam, L, w.T, keep_all=True)
+    F = np.stack([oracle.objective(D, w.X, Zall[t], w.lam, with_gap=False) for t in range(w.T + 1)])
+    assert (np.diff(F, axis=0) <= 1e-13).all()
+    assert dec[-100:].all()
+    assert acc[-1] == w.N
+    # the L_S reported for the last layer is that of supp(z^(T-1))
+    for i in range(w.N):
+        mask = Zall[w.T - 1, i] != 0
+        assert abs(LS[i] - oracle.support_lipschitz(D, mask, L)) < 1e-12
+
+
+def test_oista_faster_than_ista():
+    """Fig. B.2: OISTA reaches F* + 1e-13 in no more iterations than ISTA
+    (D 100 x 200, samples in B_inf, high regularisation)."""
+    w = synth.paper_binf(100, 200, N=2, lam=0.6, T=1500, seed=5)
+    D = w.D.astype(np.float64)
+    L = oracle.lipschitz(D)
+    Fstar = oracle.objective(D, w.X, oracle.ista(D, w.X, w.lam, L, 20000), w.lam, with_gap=False)
+    Zi = oracle.pgd(D, w.X, w.lam, np.full(w.T, 1.0 / L), keep_all=True)
+    Zo, _, _, _ = oracle.oista(D, w.X, w.lam, L, w.T, keep_all=True)
+
+    def first_hit(Zall):
+        F = np.stack([oracle.objective(D, w.X, Zall[t], w.lam, with_gap=False) for t in range(w.T + 1)])
+        ok = F < Fstar[None, :] + 1e-13
+        return np.where(ok.any(axis=0), ok.argmax(axis=0), w.T + 1)
+
+    hi, ho = first_hit(Zi), first_hit(Zo)
+    assert (ho <= hi).all(), (ho, hi)
+    assert (ho < w.T).all()
+
+
+# --------------------------------------------------------------------------
+# Step-LISTA sub-gradient (Eq. steprec, Appendix E)
+# --------------------------------------------------------------------------
+
+def _fd_check(D, X, lam, alpha, rel_tol):
+    da, loss = oracle.slista_grad(D, X, lam, alpha)
+    F = oracle.objective(D, X, oracle.pgd(D, X, lam, alpha), lam, with_gap=False)
+    assert abs(loss - F.sum()) <= 1e-12 * abs(loss)
+    checked = 0
+    for t in range(len(alpha)):
+        h = 1e-7 * alpha[t]
+        for _ in range(6):
+            ap = alpha.copy(); ap[t] += h
+            am = alpha.copy(); am[t] -= h
+            Zp = oracle.pgd(D, X, lam, ap, keep_all=True)
+            Zm = oracle.pgd(D, X, lam, am, keep_all=True)
+            if np.array_equal(Zp != 0, Zm != 0):
+                break
+            h *= 0.5
+        else:
+            continue  # a support change sits inside every window: skip
+        lp = oracle.objective(D, X, Zp[-1], lam, with_gap=False).sum()
+        lm = oracle.objective(D, X, Zm[-1], lam, with_gap=False).sum()
+        fd = (lp - lm) / (2 * h)
+        scale = max(np.abs(da).max(), 1e-12)
+        assert abs(fd - da[t]) <= rel_tol * scale, (t, fd, da[t])
+        checked += 1
+    assert checked >= len(alpha) - 1
+
+
+def test_slista_grad_finite_differences_small():
+    """Hand adjoint vs central differences in FP64, N = 64 (10 x 20, T = 20)."""
+    w = synth.paper_binf(10, 20, N=64, lam=0.2, T=20, seed=21)
+    D = w.D.astype(np.float64)
+    L = oracle.lipschitz(D)
+    alpha = synth.step_sizes(w.T, 1.0 / L, 0.6, seed=22).astype(np.float64)
+    _fd_check(D, w.X.astype(np.float64), w.lam, alpha, 1e-6)
+
+
+def test_slista_grad_finite_differences_64x256():
+    """Hand adjoint vs central differences on the 64 x 256 model (N = 8, T = 8)."""
+    w = synth.slista_64x256(N=8, T=8)
+    D = w.D.astype(np.float64)
+    L = oracle.lipschitz(D)
+    alpha = synth.step_sizes(w.T, 1.0 / L, 0.5, seed=23).astype(np.float64)
+    _fd_check(D, w.X.astype(np.float64), w.lam, alpha, 1e-6)
+
+
+def test_slista_grad_zero_when_output_zero():
+    """lam >= lam_max: every layer outputs 0, every mask is empty, so the
+    sub-gradient with respect to every step vanishes."""
+    rng = np.random.default_rng(24)
+    D = _dict(8, 16, 24)
+    X = rng.standard_normal((5, 8))
+    lam = np.abs(X @ D).max() * 1.01
+    da, loss = oracle.slista_grad(D, X, lam, np.full(6, 0.1))
+    assert not da.any()
+    np.testing.assert_allclose(loss, 0.5 * (X * X).sum(), rtol=1e-14)
