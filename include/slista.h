@@ -1,0 +1,177 @@
+/*
+ * slista.h - C ABI of the GB300 (sm_103a) library for batched unfolded ISTA,
+ * Step-LISTA (SLISTA) and Oracle-ISTA (OISTA) on the Lasso
+ *
+ *     F_x(z) = 1/2 ||x - D z||^2 + lam ||z||_1          (arXiv 1905.11071, Eq. lasso)
+ *
+ * solved for N samples at once by T unfolded proximal-gradient layers
+ *
+ *     z^(t+1) = ST(z^(t) - alpha_t (B z^(t) - c), alpha_t lam),  z^(0) = 0
+ *
+ * with B = D^T D and c = D^T x (Eq. pgd / Eq. steprec; ISTA is alpha_t = 1/L,
+ * Eq. ista).
+ *
+ * Data layout (all row-major, sample-major):
+ *   D     n x m   float32   dictionary (unit-norm columns in the paper's setups)
+ *   X     N x n   float32   samples
+ *   B     m x m   float32   Gram matrix D^T D (symmetric)
+ *   C     N x m   float32   correlations, row i = (D^T x_i)^T
+ *   xsq   N       float64   ||x_i||^2
+ *   Z     N x m   float32   codes z_i^(T)
+ *   alpha T       float32   per-layer step sizes (device memory)
+ *   L     1       float64   Lipschitz constant, largest eigenvalue of B (device memory)
+ *   masks T x N x W uint32  W = ceil(m/32); bit (j % 32) of word j/32 of row i of
+ *                           layer t is 1 iff z_ij^(t+1) != 0 (the support after layer t)
+ *   ckpt            float32  checkpoints every K = ckpt_every layers: checkpoint s
+ *                           (s = 1 .. ceil(T/K)-1, layer t = sK) holds z^(t) (N x m)
+ *                           followed by g^(t) = c - B z^(t) (N x m)
+ *
+ * Conventions for every entry point:
+ *   - Every pointer is a DEVICE pointer owned by the caller unless stated
+ *     otherwise; the library allocates no memory.  Scratch space is passed as
+ *     (ws, ws_bytes); size it with slista_workspace_bytes().
+ *   - Calls are asynchronous on the CUDA stream passed as `stream`
+ *     (a cudaStream_t cast to void*; NULL = legacy default stream).
+ *   - Return value: SLISTA_OK (0) or a negative SLISTA_ERR_* code; the message
+ *     of the last failure on the calling host thread is slista_last_error().
+ *     Arguments are validated before anything is launched; on error no kernel
+ *     runs and outputs are untouched.
+ *   - Calls on distinct streams with distinct output and workspace buffers may
+ *     run concurrently.
+ */
+#ifndef SLISTA_H
+#define SLISTA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SLISTA_API __attribute__((visibility("default")))
+#else
+#define SLISTA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SLISTA_OK               0
+#define SLISTA_ERR_ARG         -1  /* null pointer, non-positive size, alpha <= 0, lam < 0 ... */
+#define SLISTA_ERR_UNSUPPORTED -2  /* shape or precision not built */
+#define SLISTA_ERR_WORKSPACE   -3  /* ws_bytes smaller than slista_workspace_bytes() */
+#define SLISTA_ERR_CUDA        -4  /* a CUDA runtime call failed */
+#define SLISTA_ERR_TIMEOUT     -5  /* a kernel's bounded wait expired (see slista_device_status) */
+
+/* ---- precision of the B z contraction ---------------------------------- */
+#define SLISTA_PREC_FP32    0  /* FP32 on the CUDA cores (SIMT); any m */
+#define SLISTA_PREC_TF32    1  /* reserved, returns SLISTA_ERR_UNSUPPORTED */
+#define SLISTA_PREC_BF16    2  /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
+#define SLISTA_PREC_BF16X3  3  /* tcgen05, split BF16: hi*hi + hi*lo + lo*hi, FP32 accumulation */
+
+/* ---- function ids for slista_workspace_bytes --------------------------- */
+#define SLISTA_FN_GRAM       0
+#define SLISTA_FN_ISTA       1
+#define SLISTA_FN_SLISTA_FWD 2
+#define SLISTA_FN_SLISTA_BWD 3
+#define SLISTA_FN_OISTA      4
+#define SLISTA_FN_OBJECTIVE  5
+
+/* Message describing the last failed call on this host thread ("" if none). */
+SLISTA_API const char *slista_last_error(void);
+
+/* Synchronises `stream`, then reads and clears the library's device-side
+ * error flag, which a kernel sets when one of its bounded waits expires.
+ * Returns SLISTA_OK, SLISTA_ERR_TIMEOUT or SLISTA_ERR_CUDA. */
+SLISTA_API int slista_device_status(void *stream);
+
+/* Bytes of scratch the call `fn` needs for these sizes (0 if none). */
+SLISTA_API size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_every);
+
+/* Number of float32 values in the checkpoint buffer of slista_forward /
+ * slista_backward: 2 * N * m * (ceil(T / ckpt_every) - 1). */
+SLISTA_API size_t slista_ckpt_floats(int m, int N, int T, int ckpt_every);
+
+/* Number of uint32 words in the per-layer support masks: T * N * ceil(m/32). */
+SLISTA_API size_t slista_mask_words(int m, int N, int T);
+
+/* Gram quantities of the Lasso: B = D^T D (the matrix behind W_z = Id - D^T D / L,
+ * Section 4), C = X D (the D^T x term of the gradient D^T(Dz - x), Eq. ista),
+ * xsq_i = ||x_i||^2, and optionally L = largest eigenvalue of D^T D (Section 1,
+ * after Eq. ista) by power iteration (FP32 products, FP64 Rayleigh quotient,
+ * relative accuracy about 1e-7).
+ * D: n x m, X: N x n (inputs).  B: m x m, C: N x m, xsq: N, L: 1 (outputs;
+ * L may be NULL to skip it).  n, m >= 1, N >= 0. */
+SLISTA_API int lasso_gram(const float *D, int n, int m, const float *X, int N,
+               float *B, float *C, double *xsq, double *L, void *stream);
+
+/* L = largest eigenvalue of the symmetric PSD matrix B (m x m) by power
+ * iteration (Section 1: L is the largest eigenvalue of D^T D). */
+SLISTA_API int lasso_lipschitz(const float *B, int m, double *L, void *stream);
+
+/* ISTA, Eq. ista: T layers with the constant step 1/L from z^(0) = 0.
+ * L is a device pointer to one double (for example the output of lasso_gram).
+ * Z (N x m) receives z^(T).  prec: SLISTA_PREC_*. */
+SLISTA_API int ista_forward(const float *B, const float *C, int m, int N, float lam, const double *L,
+                 int T, int prec, float *Z, void *ws, size_t ws_bytes, void *stream);
+
+/* Step-LISTA forward, Eq. steprec (Section 4): T layers with the learned
+ * steps alpha[0..T-1] (device, all > 0 - checked on the device side is not
+ * possible, so positivity is the caller's contract; the host-side wrapper
+ * checks it).  Z (N x m) receives z^(T).
+ * masks (nullable): per-layer support bits, layout above.
+ * ckpt (nullable, needs masks): checkpoints every ckpt_every layers, layout above;
+ * ckpt_every >= 1 (ignored when ckpt is NULL).  masks and ckpt are what
+ * slista_backward consumes. */
+SLISTA_API int slista_forward(const float *B, const float *C, int m, int N, float lam,
+                   const float *alpha, int T, int prec, float *Z,
+                   uint32_t *masks, float *ckpt, int ckpt_every,
+                   void *ws, size_t ws_bytes, void *stream);
+
+/* Step-LISTA backward: the sub-gradient of sum_i F_{x_i}(z_i^(T)) (the
+ * empirical form of Eq. unsupervised) with respect to alpha, obtained by the
+ * chain rule on Eq. steprec, with derivative 0 at the kinks of ST and of |z|
+ * (sign(0) = 0).  The paper takes it by automatic differentiation
+ * (Appendix E); here it is the hand-written adjoint
+ *     G = dF/dz^(T) = B z^(T) - c + lam sign(z^(T))   (or gZ if not NULL)
+ *     for t = T-1 .. 0:  h = G * mask_t;
+ *                        dalpha_t = sum_i <h_i, g_i^(t) - lam sign(z_i^(t+1))>;
+ *                        G = h - alpha_t B h
+ * where g^(t) = c - B z^(t).  Iterates between checkpoints are recomputed
+ * from `ckpt` with the same arithmetic as slista_forward, so masks, ckpt and
+ * ckpt_every must come from a slista_forward call with the same B, C, lam,
+ * alpha, T and prec.  gZ (nullable, N x m): upstream gradient dLoss/dz^(T).
+ * dalpha (T, float32) receives the sub-gradient.  Only SLISTA_PREC_FP32. */
+SLISTA_API int slista_backward(const float *B, const float *C, int m, int N, float lam,
+                    const float *alpha, int T, int prec,
+                    const uint32_t *masks, const float *ckpt, int ckpt_every,
+                    const float *gZ, float *dalpha,
+                    void *ws, size_t ws_bytes, void *stream);
+
+/* Oracle-ISTA, Algorithm 1 (Section 3): at every layer, S = supp(z^(t)),
+ * L_S = largest eigenvalue of B_SS (Eq. spca; L_empty = L, recomputed only
+ * when S changes), y = ST(z - (Bz - c)/L_S, lam/L_S); z^(t+1) = y when
+ * supp(y) is inside S (condition (star)), else the ISTA step with 1/L.
+ * L_S comes from a masked power iteration (FP32 products, FP64 Rayleigh
+ * quotient).  Outputs: Z (N x m) = z^(T); LS (N, nullable) = the L_S used at
+ * the last layer; accepted (T ints, nullable) = number of samples whose step
+ * t met condition (star) (zeroed by the call).  Only SLISTA_PREC_FP32. */
+SLISTA_API int oista_forward(const float *B, const float *C, int m, int N, float lam, const double *L,
+                  int T, int prec, float *Z, double *LS, int *accepted,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* Per-sample Lasso objective (Eq. lasso) evaluated from the Gram quantities,
+ *     F_i = 1/2 xsq_i - c_i^T z_i + 1/2 z_i^T B z_i + lam ||z_i||_1,
+ * and (gap nullable) the duality gap of the standard Lasso dual (not in the
+ * paper): with r = x - Dz, s = min(1, lam / ||c - Bz||_inf),
+ *     gap_i = F_i - (s x^T r - s^2 ||r||^2 / 2),
+ * x^T r = xsq - c^T z, ||r||^2 = xsq - 2 c^T z + z^T B z.
+ * B z in FP32, every reduction in FP64.  F, gap: N doubles. */
+SLISTA_API int lasso_objective(const float *B, const float *C, const double *xsq, const float *Z,
+                    int m, int N, float lam, double *F, double *gap, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLISTA_H */

@@ -63,7 +63,7 @@ def _load():
             lib.orc_support_lipschitz.argtypes = [dp, i, i, up, d]
             lib.orc_support_lipschitz.restype = d
             lib.orc_pgd.argtypes = [dp, i, i, dp, i, d, dp, i, dp, dp]
-            lib.orc_oista.argtypes = [dp, i, i, dp, i, d, d, i, dp, dp, ip, up, dp]
+            lib.orc_oista.argtypes = [dp, i, i, dp, i, d, d, i, dp, dp, ip, up, dp, dp]
             lib.orc_slista_grad.argtypes = [dp, i, i, dp, i, d, dp, i, dp, dp]
             lib.orc_lasso_bruteforce.argtypes = [dp, i, i, dp, d, dp]
             lib.orc_lasso_bruteforce.restype = i
@@ -164,13 +164,15 @@ def ista(D, X, lam, L, T):
     return pgd(D, X, lam, np.full(T, 1.0 / L))
 
 
-def oista(D, X, lam, L, T, keep_all: bool = False):
+def oista(D, X, lam, L, T, keep_all: bool = False, with_margin: bool = False):
     """Oracle-ISTA, Algorithm 1.
 
     Returns (Z, LS, accepted, decision): z^(T) (or every iterate,
     (T+1) x N x m, if ``keep_all``); the L_S used at the last layer per
     sample; per-layer count of samples whose step met condition (star); and
-    the per-layer, per-sample (star) outcome (T x N, uint8).
+    the per-layer, per-sample (star) outcome (T x N, uint8).  With
+    ``with_margin`` a fifth value: per sample, the smallest distance of a
+    pre-threshold value to its threshold along the trajectory.
     """
     D = _f64(D); X = _f64(X)
     n, m = D.shape
@@ -179,11 +181,13 @@ def oista(D, X, lam, L, T, keep_all: bool = False):
     acc = np.zeros(T, dtype=np.int32)
     dec = np.zeros((T, N), dtype=np.uint8)
     Zall = np.empty((T + 1, N, m)) if keep_all else None
+    marg = np.empty(N) if with_margin else None
     _load().orc_oista(_p(D), n, m, _p(X), N, float(lam), float(L), int(T), _p(Z), _p(LS),
                       acc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                       dec.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
-                      _p(Zall) if keep_all else None)
-    return (Zall if keep_all else Z), LS, acc, dec
+                      _p(Zall) if keep_all else None, _p(marg) if with_margin else None)
+    out = ((Zall if keep_all else Z), LS, acc, dec)
+    return out + (marg,) if with_margin else out
 
 
 def slista_grad(D, X, lam, alpha):

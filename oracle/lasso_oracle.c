@@ -314,10 +314,15 @@ void orc_pgd(const double *D, int n, int m, const double *X, int N, double lam,
  * layer; accepted (T, may be NULL) = number of samples whose step t satisfied
  * condition (star); decision (T x N, may be NULL) = 1 if sample's step t
  * satisfied (star), else 0; Zall ((T+1) x N x m, may be NULL) = every
- * iterate. */
+ * iterate; margin (N, may be NULL) = for each sample, the smallest distance
+ * to a threshold met on its trajectory: over all layers, |lam/L_S - |u_j||
+ * for the candidate's pre-threshold values u off S (how close condition
+ * (star) came to flipping) and ||u_j| - a lam| for the step actually taken
+ * (how close the support came to changing).  Decisions of samples with a
+ * tiny margin are at the mercy of rounding. */
 void orc_oista(const double *D, int n, int m, const double *X, int N, double lam,
                double L, int T, double *Z, double *LS, int *accepted, unsigned char *decision,
-               double *Zall)
+               double *Zall, double *margin)
 {
     double *z = (double *)malloc(sizeof(double) * (size_t)m);
     double *y = (double *)malloc(sizeof(double) * (size_t)m);
@@ -331,6 +336,7 @@ void orc_oista(const double *D, int n, int m, const double *X, int N, double lam
     for (int s = 0; s < N; ++s) {
         const double *x = X + (size_t)s * n;
         double LSval = L;
+        double marg = INFINITY;
         int have_prev = 0;
         for (int j = 0; j < m; ++j) z[j] = 0.0;
         if (Zall) memcpy(Zall + (size_t)s * m, z, sizeof(double) * (size_t)m);
@@ -349,6 +355,20 @@ void orc_oista(const double *D, int n, int m, const double *X, int N, double lam
             int ok = 1;
             for (int j = 0; j < m; ++j)
                 if (y[j] != 0.0 && !S[j]) { ok = 0; break; }
+            if (margin) {
+                /* work + n holds D^T(Dz - x) from the psi call above */
+                const double *grad = work + n;
+                for (int j = 0; j < m; ++j) {
+                    double u = z[j] - grad[j] / LSval;
+                    double dist = fabs(fabs(u) - lam / LSval);
+                    if ((!S[j] || ok) && dist < marg) marg = dist;
+                    if (!ok) {
+                        double uL = z[j] - grad[j] / L;
+                        double dL = fabs(fabs(uL) - lam / L);
+                        if (dL < marg) marg = dL;
+                    }
+                }
+            }
             if (ok) {
                 memcpy(z, y, sizeof(double) * (size_t)m);
                 if (accepted) accepted[t] += 1;
@@ -362,6 +382,7 @@ void orc_oista(const double *D, int n, int m, const double *X, int N, double lam
         }
         memcpy(Z + (size_t)s * m, z, sizeof(double) * (size_t)m);
         if (LS && T == 0) LS[s] = L;
+        if (margin) margin[s] = marg;
     }
     free(z); free(y); free(work); free(ework); free(idx); free(S); free(Sprev);
 }

@@ -1,0 +1,253 @@
+"""ctypes binding of libslista.so (include/slista.h).
+
+Argument marshalling only: every function here forwards torch tensors' device
+pointers and sizes to the C entry point of the same name and raises
+``SlistaError`` on a non-zero status.  There is no fallback: if the CUDA
+library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libslista.so")
+
+SLISTA_OK = 0
+SLISTA_ERR_ARG = -1
+SLISTA_ERR_UNSUPPORTED = -2
+SLISTA_ERR_WORKSPACE = -3
+SLISTA_ERR_CUDA = -4
+SLISTA_ERR_TIMEOUT = -5
+
+PREC_FP32 = 0
+PREC_TF32 = 1
+PREC_BF16 = 2
+PREC_BF16X3 = 3
+PRECISIONS = {"fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3}
+
+FN_GRAM = 0
+FN_ISTA = 1
+FN_SLISTA_FWD = 2
+FN_SLISTA_BWD = 3
+FN_OISTA = 4
+FN_OBJECTIVE = 5
+
+EXPORTS = [
+    "slista_last_error", "slista_device_status", "slista_workspace_bytes", "slista_ckpt_floats",
+    "slista_mask_words", "lasso_gram", "lasso_lipschitz", "ista_forward", "slista_forward",
+    "slista_backward", "oista_forward", "lasso_objective",
+]
+
+
+class SlistaError(RuntimeError):
+    def __init__(self, code: int, fn: str, msg: str):
+        super().__init__("%s failed with status %d: %s" % (fn, code, msg))
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the library (once) and declares the C signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError("libslista.so not found at %s: build it with "
+                               "paper_1905_11071_gb300.build.build()" % path)
+        lib = ctypes.CDLL(path)
+        vp = ctypes.c_void_p
+        i = ctypes.c_int
+        f = ctypes.c_float
+        sz = ctypes.c_size_t
+        lib.slista_last_error.restype = ctypes.c_char_p
+        lib.slista_last_error.argtypes = []
+        lib.slista_device_status.argtypes = [vp]
+        lib.slista_workspace_bytes.restype = sz
+        lib.slista_workspace_bytes.argtypes = [i, i, i, i, i, i]
+        lib.slista_ckpt_floats.restype = sz
+        lib.slista_ckpt_floats.argtypes = [i, i, i, i]
+        lib.slista_mask_words.restype = sz
+        lib.slista_mask_words.argtypes = [i, i, i]
+        lib.lasso_gram.argtypes = [vp, i, i, vp, i, vp, vp, vp, vp, vp]
+        lib.lasso_lipschitz.argtypes = [vp, i, vp, vp]
+        lib.ista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, sz, vp]
+        lib.slista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp, i, vp, sz, vp]
+        lib.slista_backward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, i, vp, vp, vp, sz, vp]
+        lib.oista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
+        lib.lasso_objective.argtypes = [vp, vp, vp, vp, i, i, f, vp, vp, vp]
+        for name in EXPORTS:
+            if name not in ("slista_last_error", "slista_workspace_bytes", "slista_ckpt_floats",
+                            "slista_mask_words"):
+                getattr(lib, name).restype = i
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, fn: str):
+    if rc != SLISTA_OK:
+        msg = load().slista_last_error()
+        raise SlistaError(rc, fn, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    """Device pointer of a tensor (None -> NULL)."""
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t, dtype, shape, name):
+    import torch
+    if t is None:
+        raise ValueError("%s is required" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s (got %s)" % (name, dtype, t.dtype))
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s (got %s)" % (name, tuple(shape), tuple(t.shape)))
+    return t
+
+
+def _opt(t, dtype, shape, name):
+    return None if t is None else _need(t, dtype, shape, name)
+
+
+def slista_last_error() -> str:
+    msg = load().slista_last_error()
+    return msg.decode() if msg else ""
+
+
+def slista_device_status(stream=None) -> None:
+    _check(load().slista_device_status(_stream(stream)), "slista_device_status")
+
+
+def slista_workspace_bytes(fn: int, m: int, N: int, T: int, prec: int, ckpt_every: int = 1) -> int:
+    return int(load().slista_workspace_bytes(fn, m, N, T, prec, ckpt_every))
+
+
+def slista_ckpt_floats(m: int, N: int, T: int, ckpt_every: int) -> int:
+    return int(load().slista_ckpt_floats(m, N, T, ckpt_every))
+
+
+def slista_mask_words(m: int, N: int, T: int) -> int:
+    return int(load().slista_mask_words(m, N, T))
+
+
+def lasso_gram(D, X, B, C, xsq, L=None, stream=None) -> None:
+    import torch
+    n, m = D.shape
+    N = X.shape[0]
+    _need(D, torch.float32, (n, m), "D")
+    _need(X, torch.float32, (N, n), "X")
+    _need(B, torch.float32, (m, m), "B")
+    _need(C, torch.float32, (N, m), "C")
+    _need(xsq, torch.float64, (N,), "xsq")
+    _opt(L, torch.float64, (1,), "L")
+    _check(load().lasso_gram(_ptr(D), n, m, _ptr(X), N, _ptr(B), _ptr(C), _ptr(xsq), _ptr(L),
+                             _stream(stream)), "lasso_gram")
+
+
+def lasso_lipschitz(B, L, stream=None) -> None:
+    import torch
+    m = B.shape[0]
+    _need(B, torch.float32, (m, m), "B")
+    _need(L, torch.float64, (1,), "L")
+    _check(load().lasso_lipschitz(_ptr(B), m, _ptr(L), _stream(stream)), "lasso_lipschitz")
+
+
+def ista_forward(B, C, lam, L, T, prec, Z, ws=None, stream=None) -> None:
+    import torch
+    m = B.shape[0]
+    N = C.shape[0]
+    _need(B, torch.float32, (m, m), "B")
+    _need(C, torch.float32, (N, m), "C")
+    _need(L, torch.float64, (1,), "L")
+    _need(Z, torch.float32, (N, m), "Z")
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().ista_forward(_ptr(B), _ptr(C), m, N, float(lam), _ptr(L), int(T), int(prec), _ptr(Z),
+                               _ptr(ws), wsb, _stream(stream)), "ista_forward")
+
+
+def slista_forward(B, C, lam, alpha, prec, Z, masks=None, ckpt=None, ckpt_every=1, ws=None,
+                   stream=None) -> None:
+    import torch
+    m = B.shape[0]
+    N = C.shape[0]
+    T = alpha.shape[0]
+    _need(B, torch.float32, (m, m), "B")
+    _need(C, torch.float32, (N, m), "C")
+    _need(alpha, torch.float32, (T,), "alpha")
+    _need(Z, torch.float32, (N, m), "Z")
+    _opt(masks, torch.int32, None, "masks")
+    _opt(ckpt, torch.float32, None, "ckpt")
+    if masks is not None and masks.numel() < slista_mask_words(m, N, T):
+        raise ValueError("masks too small")
+    if ckpt is not None and ckpt.numel() < slista_ckpt_floats(m, N, T, ckpt_every):
+        raise ValueError("ckpt too small")
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().slista_forward(_ptr(B), _ptr(C), m, N, float(lam), _ptr(alpha), T, int(prec), _ptr(Z),
+                                 _ptr(masks), _ptr(ckpt), int(ckpt_every), _ptr(ws), wsb, _stream(stream)),
+           "slista_forward")
+
+
+def slista_backward(B, C, lam, alpha, prec, masks, ckpt, ckpt_every, dalpha, gZ=None, ws=None,
+                    stream=None) -> None:
+    import torch
+    m = B.shape[0]
+    N = C.shape[0]
+    T = alpha.shape[0]
+    _need(B, torch.float32, (m, m), "B")
+    _need(C, torch.float32, (N, m), "C")
+    _need(alpha, torch.float32, (T,), "alpha")
+    _need(masks, torch.int32, None, "masks")
+    _opt(ckpt, torch.float32, None, "ckpt")
+    _opt(gZ, torch.float32, (N, m), "gZ")
+    _need(dalpha, torch.float32, (T,), "dalpha")
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().slista_backward(_ptr(B), _ptr(C), m, N, float(lam), _ptr(alpha), T, int(prec), _ptr(masks),
+                                  _ptr(ckpt), int(ckpt_every), _ptr(gZ), _ptr(dalpha), _ptr(ws), wsb,
+                                  _stream(stream)), "slista_backward")
+
+
+def oista_forward(B, C, lam, L, T, prec, Z, LS=None, accepted=None, ws=None, stream=None) -> None:
+    import torch
+    m = B.shape[0]
+    N = C.shape[0]
+    _need(B, torch.float32, (m, m), "B")
+    _need(C, torch.float32, (N, m), "C")
+    _need(L, torch.float64, (1,), "L")
+    _need(Z, torch.float32, (N, m), "Z")
+    _opt(LS, torch.float64, (N,), "LS")
+    _opt(accepted, torch.int32, (T,), "accepted")
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().oista_forward(_ptr(B), _ptr(C), m, N, float(lam), _ptr(L), int(T), int(prec), _ptr(Z),
+                                _ptr(LS), _ptr(accepted), _ptr(ws), wsb, _stream(stream)), "oista_forward")
+
+
+def lasso_objective(B, C, xsq, Z, lam, F, gap=None, stream=None) -> None:
+    import torch
+    m = B.shape[0]
+    N = C.shape[0]
+    _need(B, torch.float32, (m, m), "B")
+    _need(C, torch.float32, (N, m), "C")
+    _need(xsq, torch.float64, (N,), "xsq")
+    _need(Z, torch.float32, (N, m), "Z")
+    _need(F, torch.float64, (N,), "F")
+    _opt(gap, torch.float64, (N,), "gap")
+    _check(load().lasso_objective(_ptr(B), _ptr(C), _ptr(xsq), _ptr(Z), m, N, float(lam), _ptr(F), _ptr(gap),
+                                  _stream(stream)), "lasso_objective")

@@ -1,0 +1,202 @@
+"""Tensor-level API over the C ABI: allocates outputs and workspaces with torch
+and calls the entry points of ``_lib`` (every computation runs in the CUDA
+library).  Also provides the autograd function that trains Step-LISTA step
+sizes on the unsupervised loss sum_i F_{x_i}(Phi(x_i)) (Eq. unsupervised).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+from . import _lib
+
+
+def default_ckpt_every(T: int) -> int:
+    """Checkpoint spacing ceil(sqrt(T)): memory ~ sqrt(T) states, ~1 recompute."""
+    return max(1, int(math.ceil(math.sqrt(max(T, 1)))))
+
+
+def _prec(prec) -> int:
+    if isinstance(prec, str):
+        return _lib.PRECISIONS[prec]
+    return int(prec)
+
+
+_ws_cache: dict = {}
+
+
+def workspace(nbytes: int, device, tag: str = "default") -> Optional[torch.Tensor]:
+    """A cached uint8 device buffer of at least nbytes (None if nbytes == 0)."""
+    if nbytes <= 0:
+        return None
+    key = (str(device), tag)
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        _ws_cache[key] = buf
+    return buf
+
+
+@dataclass
+class Gram:
+    B: torch.Tensor      # m x m float32
+    C: torch.Tensor      # N x m float32
+    xsq: torch.Tensor    # N float64
+    L: torch.Tensor      # 1 float64 (device)
+
+
+def gram(D: torch.Tensor, X: torch.Tensor, with_L: bool = True, stream=None) -> Gram:
+    n, m = D.shape
+    N = X.shape[0]
+    dev = D.device
+    B = torch.empty((m, m), dtype=torch.float32, device=dev)
+    C = torch.empty((N, m), dtype=torch.float32, device=dev)
+    xsq = torch.empty((N,), dtype=torch.float64, device=dev)
+    L = torch.empty((1,), dtype=torch.float64, device=dev) if with_L else None
+    _lib.lasso_gram(D, X, B, C, xsq, L, stream=stream)
+    return Gram(B, C, xsq, L)
+
+
+def lipschitz(B: torch.Tensor, stream=None) -> torch.Tensor:
+    L = torch.empty((1,), dtype=torch.float64, device=B.device)
+    _lib.lasso_lipschitz(B, L, stream=stream)
+    return L
+
+
+def ista(B, C, lam, L, T, prec="fp32", stream=None) -> torch.Tensor:
+    N, m = C.shape
+    p = _prec(prec)
+    Z = torch.empty((N, m), dtype=torch.float32, device=C.device)
+    ws = workspace(_lib.slista_workspace_bytes(_lib.FN_ISTA, m, N, T, p), C.device, "fwd")
+    _lib.ista_forward(B, C, lam, L, T, p, Z, ws=ws, stream=stream)
+    return Z
+
+
+@dataclass
+class ForwardState:
+    """What slista_backward needs from a forward call."""
+    masks: torch.Tensor
+    ckpt: Optional[torch.Tensor]
+    ckpt_every: int
+
+
+def slista(B, C, lam, alpha, prec="fp32", keep_for_backward: bool = False,
+           ckpt_every: Optional[int] = None, stream=None):
+    """Step-LISTA forward (Eq. steprec).  Returns Z, or (Z, ForwardState)."""
+    N, m = C.shape
+    T = alpha.shape[0]
+    p = _prec(prec)
+    dev = C.device
+    Z = torch.empty((N, m), dtype=torch.float32, device=dev)
+    ws = workspace(_lib.slista_workspace_bytes(_lib.FN_SLISTA_FWD, m, N, T, p), dev, "fwd")
+    if not keep_for_backward:
+        _lib.slista_forward(B, C, lam, alpha, p, Z, ws=ws, stream=stream)
+        return Z
+    K = ckpt_every or default_ckpt_every(T)
+    masks = torch.empty((max(1, _lib.slista_mask_words(m, N, T)),), dtype=torch.int32, device=dev)
+    nck = _lib.slista_ckpt_floats(m, N, T, K)
+    ckpt = torch.empty((nck,), dtype=torch.float32, device=dev) if nck > 0 else None
+    _lib.slista_forward(B, C, lam, alpha, p, Z, masks=masks, ckpt=ckpt, ckpt_every=K, ws=ws, stream=stream)
+    return Z, ForwardState(masks, ckpt, K)
+
+
+def slista_grad(B, C, lam, alpha, state: ForwardState, gZ=None, prec="fp32", stream=None) -> torch.Tensor:
+    """Sub-gradient of sum_i F(z_i^(T)) (or of <gZ, z^(T)>) w.r.t. alpha."""
+    N, m = C.shape
+    T = alpha.shape[0]
+    p = _prec(prec)
+    dalpha = torch.empty((T,), dtype=torch.float32, device=C.device)
+    ws = workspace(_lib.slista_workspace_bytes(_lib.FN_SLISTA_BWD, m, N, T, p, state.ckpt_every), C.device,
+                   "bwd")
+    _lib.slista_backward(B, C, lam, alpha, p, state.masks, state.ckpt, state.ckpt_every, dalpha, gZ=gZ,
+                         ws=ws, stream=stream)
+    return dalpha
+
+
+def oista(B, C, lam, L, T, stream=None):
+    """Oracle-ISTA (Algorithm 1).  Returns (Z, LS, accepted)."""
+    N, m = C.shape
+    dev = C.device
+    Z = torch.empty((N, m), dtype=torch.float32, device=dev)
+    LS = torch.empty((N,), dtype=torch.float64, device=dev)
+    acc = torch.empty((max(T, 1),), dtype=torch.int32, device=dev)
+    ws = workspace(_lib.slista_workspace_bytes(_lib.FN_OISTA, m, N, T, 0), dev, "oista")
+    _lib.oista_forward(B, C, lam, L, T, _lib.PREC_FP32, Z, LS=LS, accepted=acc[:T] if T > 0 else None,
+                       ws=ws, stream=stream)
+    return Z, LS, acc[:T]
+
+
+def objective(B, C, xsq, Z, lam, with_gap: bool = True, stream=None):
+    N = C.shape[0]
+    F = torch.empty((N,), dtype=torch.float64, device=C.device)
+    gap = torch.empty((N,), dtype=torch.float64, device=C.device) if with_gap else None
+    _lib.lasso_objective(B, C, xsq, Z, lam, F, gap, stream=stream)
+    return (F, gap) if with_gap else F
+
+
+class SlistaLoss(torch.autograd.Function):
+    """sum_i F_{x_i}(Phi_alpha(x_i)) with Phi the T-layer Step-LISTA network.
+
+    forward(alpha, B, C, xsq, lam, ckpt_every) -> scalar loss (float64)
+    backward -> d loss / d alpha from the hand-written adjoint kernel.
+    """
+
+    @staticmethod
+    def forward(ctx, alpha, B, C, xsq, lam, ckpt_every=None):
+        Z, st = slista(B, C, lam, alpha, keep_for_backward=True, ckpt_every=ckpt_every)
+        F = objective(B, C, xsq, Z, lam, with_gap=False)
+        ctx.save_for_backward(alpha, B, C)
+        ctx.state = st
+        ctx.lam = lam
+        return F.sum()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        alpha, B, C = ctx.saved_tensors
+        da = slista_grad(B, C, ctx.lam, alpha, ctx.state)
+        return (da * grad_out.to(da.dtype)), None, None, None, None, None
+
+
+def slista_loss(alpha, g: Gram, lam, ckpt_every=None):
+    return SlistaLoss.apply(alpha, g.B, g.C, g.xsq, lam, ckpt_every)
+
+
+def train_step_sizes(alpha0: torch.Tensor, g: Gram, lam: float, steps: int = 50, lr0: Optional[float] = None,
+                     grow: float = 1.2, max_halvings: int = 20, min_alpha: float = 1e-6):
+    """Full-batch sub-gradient descent with backtracking on the step sizes
+    (Appendix E).  A trial step alpha - lr * dalpha is accepted when the loss
+    does not increase; otherwise lr is halved (at most max_halvings times).
+    After an accepted step lr grows by `grow`.  Steps stay >= min_alpha.
+    Returns (alpha, history of losses)."""
+    alpha = alpha0.detach().clone()
+    hist = []
+    a = alpha.clone().requires_grad_(True)
+    loss = slista_loss(a, g, lam)
+    loss.backward()
+    cur = float(loss)
+    grad = a.grad.detach().clone()
+    hist.append(cur)
+    if lr0 is None:
+        gmax = float(grad.abs().max())
+        lr0 = 0.1 * float(alpha.abs().max()) / gmax if gmax > 0 else 0.0
+    lr = lr0
+    for _ in range(steps):
+        accepted = False
+        for _h in range(max_halvings):
+            trial = torch.clamp(alpha - lr * grad, min=min_alpha)
+            t = trial.clone().requires_grad_(True)
+            tl = slista_loss(t, g, lam)
+            if float(tl) <= cur:
+                tl.backward()
+                alpha, cur, grad = trial, float(tl), t.grad.detach().clone()
+                lr *= grow
+                accepted = True
+                break
+            lr *= 0.5
+        hist.append(cur)
+        if not accepted:
+            break
+    return alpha, hist

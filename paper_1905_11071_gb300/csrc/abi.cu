@@ -1,0 +1,243 @@
+// C ABI of the library (include/slista.h): argument validation, status
+// reporting and dispatch to the kernel translation units.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace slista {
+
+static thread_local char g_msg[1024] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_msg[0] = '\0'; }
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int check_launch(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(SLISTA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return SLISTA_OK;
+}
+
+int num_sms()
+{
+    static int cached = 0;
+    if (cached == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            cached = v;
+        else
+            cached = 1;
+    }
+    return cached;
+}
+
+}  // namespace slista
+
+using namespace slista;
+
+namespace {
+
+bool valid_prec(int prec)
+{
+    return prec == SLISTA_PREC_FP32 || prec == SLISTA_PREC_TF32 || prec == SLISTA_PREC_BF16 ||
+           prec == SLISTA_PREC_BF16X3;
+}
+
+int check_lam(float lam)
+{
+    if (!(lam >= 0.0f) || isinf(lam)) return fail(SLISTA_ERR_ARG, "lam must be finite and >= 0 (got %g)", (double)lam);
+    return SLISTA_OK;
+}
+
+int forward_common(const PgdArgs &a, int prec, void *ws, size_t ws_bytes, cudaStream_t st, const char *name)
+{
+    SLISTA_REQUIRE(valid_prec(prec), SLISTA_ERR_ARG, "%s: unknown precision %d", name, prec);
+    if (prec == SLISTA_PREC_FP32) {
+        SLISTA_REQUIRE(simt::padded_mp(a.m) != 0, SLISTA_ERR_UNSUPPORTED, "%s: FP32 path supports m <= 256", name);
+        return simt::launch_forward(a, st);
+    }
+    if (prec == SLISTA_PREC_TF32) return fail(SLISTA_ERR_UNSUPPORTED, "%s: TF32 is not built", name);
+    SLISTA_REQUIRE(tc::supported(a.m), SLISTA_ERR_UNSUPPORTED, "%s: tensor-core path does not support m = %d", name,
+                   a.m);
+    SLISTA_REQUIRE(a.ckpt == nullptr, SLISTA_ERR_UNSUPPORTED,
+                   "%s: checkpoints are produced by the FP32 path only", name);
+    const size_t need = tc::forward_ws_bytes(a.m);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws != nullptr), SLISTA_ERR_WORKSPACE,
+                   "%s: workspace of %zu bytes needed, %zu given", name, need, ws_bytes);
+    return tc::launch_forward(a, prec, ws, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *slista_last_error(void) { return g_msg; }
+
+int slista_device_status(void *stream)
+{
+    clear_error();
+    cudaStream_t st = as_stream(stream);
+    SLISTA_CUDA_TRY(cudaStreamSynchronize(st));
+    return read_and_clear_device_flag(st);
+}
+
+size_t slista_ckpt_floats(int m, int N, int T, int ckpt_every)
+{
+    if (m <= 0 || N <= 0 || T <= 0 || ckpt_every <= 0) return 0;
+    const size_t nck = (size_t)((T + ckpt_every - 1) / ckpt_every) - 1;
+    return 2 * (size_t)N * (size_t)m * nck;
+}
+
+size_t slista_mask_words(int m, int N, int T)
+{
+    if (m <= 0 || N <= 0 || T <= 0) return 0;
+    return (size_t)T * (size_t)N * (size_t)((m + 31) / 32);
+}
+
+size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_every)
+{
+    if (m <= 0 || N < 0 || T < 0) return 0;
+    switch (fn) {
+        case SLISTA_FN_ISTA:
+        case SLISTA_FN_SLISTA_FWD:
+            if (prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3) return tc::forward_ws_bytes(m);
+            return 0;
+        case SLISTA_FN_SLISTA_BWD:
+            if (ckpt_every <= 0 || T <= 0) return 0;
+            return simt::backward_ws_bytes(m, N, T, ckpt_every < T ? ckpt_every : T);
+        case SLISTA_FN_OISTA: return simt::oista_ws_bytes(m, N);
+        default: return 0;
+    }
+}
+
+int lasso_gram(const float *D, int n, int m, const float *X, int N, float *B, float *C, double *xsq, double *L,
+               void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(n >= 1 && m >= 1 && N >= 0, SLISTA_ERR_ARG, "lasso_gram: bad sizes n=%d m=%d N=%d", n, m, N);
+    SLISTA_REQUIRE(D && B, SLISTA_ERR_ARG, "lasso_gram: D and B must not be NULL");
+    SLISTA_REQUIRE(N == 0 || (X && C && xsq), SLISTA_ERR_ARG, "lasso_gram: X, C, xsq must not be NULL");
+    SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "lasso_gram: m <= 256 supported (got %d)", m);
+    cudaStream_t st = as_stream(stream);
+    int rc = gram::launch_gram(D, n, m, X, N, B, C, xsq, st);
+    if (rc) return rc;
+    if (L) {
+        if ((n <= m ? n : m) <= 128) return gram::launch_lipschitz_from_D(D, n, m, L, st);
+        return gram::launch_lipschitz_from_B(B, m, L, st);
+    }
+    return SLISTA_OK;
+}
+
+int lasso_lipschitz(const float *B, int m, double *L, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(B && L, SLISTA_ERR_ARG, "lasso_lipschitz: B and L must not be NULL");
+    SLISTA_REQUIRE(m >= 1 && m <= 1024, SLISTA_ERR_ARG, "lasso_lipschitz: 1 <= m <= 1024 (got %d)", m);
+    return gram::launch_lipschitz_from_B(B, m, L, as_stream(stream));
+}
+
+int ista_forward(const float *B, const float *C, int m, int N, float lam, const double *L, int T, int prec,
+                 float *Z, void *ws, size_t ws_bytes, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 0, SLISTA_ERR_ARG, "ista_forward: bad sizes m=%d N=%d T=%d", m, N, T);
+    SLISTA_REQUIRE(B && L, SLISTA_ERR_ARG, "ista_forward: B and L must not be NULL");
+    SLISTA_REQUIRE(N == 0 || (C && Z), SLISTA_ERR_ARG, "ista_forward: C and Z must not be NULL");
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    PgdArgs a{B, C, m, N, lam, nullptr, L, T, Z, nullptr, nullptr, 1};
+    return forward_common(a, prec, ws, ws_bytes, as_stream(stream), "ista_forward");
+}
+
+int slista_forward(const float *B, const float *C, int m, int N, float lam, const float *alpha, int T, int prec,
+                   float *Z, uint32_t *masks, float *ckpt, int ckpt_every, void *ws, size_t ws_bytes, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 0, SLISTA_ERR_ARG, "slista_forward: bad sizes m=%d N=%d T=%d", m, N,
+                   T);
+    SLISTA_REQUIRE(B && (T == 0 || alpha), SLISTA_ERR_ARG, "slista_forward: B and alpha must not be NULL");
+    SLISTA_REQUIRE(N == 0 || (C && Z), SLISTA_ERR_ARG, "slista_forward: C and Z must not be NULL");
+    SLISTA_REQUIRE(!ckpt || ckpt_every >= 1, SLISTA_ERR_ARG, "slista_forward: ckpt_every must be >= 1");
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    PgdArgs a{B, C, m, N, lam, alpha, nullptr, T, Z, masks, ckpt, ckpt ? ckpt_every : 1};
+    return forward_common(a, prec, ws, ws_bytes, as_stream(stream), "slista_forward");
+}
+
+int slista_backward(const float *B, const float *C, int m, int N, float lam, const float *alpha, int T, int prec,
+                    const uint32_t *masks, const float *ckpt, int ckpt_every, const float *gZ, float *dalpha,
+                    void *ws, size_t ws_bytes, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 1, SLISTA_ERR_ARG, "slista_backward: bad sizes m=%d N=%d T=%d", m, N,
+                   T);
+    SLISTA_REQUIRE(prec == SLISTA_PREC_FP32, SLISTA_ERR_UNSUPPORTED, "slista_backward: only SLISTA_PREC_FP32");
+    SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "slista_backward: m <= 256 supported");
+    SLISTA_REQUIRE(B && alpha && dalpha, SLISTA_ERR_ARG, "slista_backward: B, alpha, dalpha must not be NULL");
+    SLISTA_REQUIRE(ckpt_every >= 1, SLISTA_ERR_ARG, "slista_backward: ckpt_every must be >= 1");
+    const int K = ckpt_every < T ? ckpt_every : T;
+    SLISTA_REQUIRE(N == 0 || (C && masks), SLISTA_ERR_ARG, "slista_backward: C and masks must not be NULL");
+    SLISTA_REQUIRE(N == 0 || K >= T || ckpt, SLISTA_ERR_ARG, "slista_backward: ckpt must not be NULL");
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    const size_t need = simt::backward_ws_bytes(m, N, T, K);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
+                   "slista_backward: workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    BwdArgs a{B, C, m, N, lam, alpha, T, masks, ckpt, K, gZ, dalpha};
+    return simt::launch_backward(a, ws, as_stream(stream));
+}
+
+int oista_forward(const float *B, const float *C, int m, int N, float lam, const double *L, int T, int prec,
+                  float *Z, double *LS, int *accepted, void *ws, size_t ws_bytes, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 0, SLISTA_ERR_ARG, "oista_forward: bad sizes m=%d N=%d T=%d", m, N, T);
+    SLISTA_REQUIRE(prec == SLISTA_PREC_FP32, SLISTA_ERR_UNSUPPORTED, "oista_forward: only SLISTA_PREC_FP32");
+    SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "oista_forward: m <= 256 supported");
+    SLISTA_REQUIRE(B && L, SLISTA_ERR_ARG, "oista_forward: B and L must not be NULL");
+    SLISTA_REQUIRE(N == 0 || (C && Z), SLISTA_ERR_ARG, "oista_forward: C and Z must not be NULL");
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    const size_t need = simt::oista_ws_bytes(m, N);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
+                   "oista_forward: workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    OistaArgs a{B, C, m, N, lam, L, T, Z, LS, accepted};
+    return simt::launch_oista(a, ws, as_stream(stream));
+}
+
+int lasso_objective(const float *B, const float *C, const double *xsq, const float *Z, int m, int N, float lam,
+                    double *F, double *gap, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(m >= 1 && N >= 0, SLISTA_ERR_ARG, "lasso_objective: bad sizes m=%d N=%d", m, N);
+    SLISTA_REQUIRE(B, SLISTA_ERR_ARG, "lasso_objective: B must not be NULL");
+    SLISTA_REQUIRE(N == 0 || (C && xsq && Z && F), SLISTA_ERR_ARG,
+                   "lasso_objective: C, xsq, Z, F must not be NULL");
+    SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "lasso_objective: m <= 256 supported");
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    ObjArgs a{B, C, xsq, Z, m, N, lam, F, gap};
+    return simt::launch_objective(a, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal launcher interface between the C ABI (abi.cu) and the kernel
+// translation units.  Arguments have been validated by the caller.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace slista {
+
+struct PgdArgs {
+    const float *B, *C;
+    int m, N;
+    float lam;
+    const float *alpha;  // T steps, or nullptr for ISTA (step 1/L)
+    const double *L;     // used when alpha == nullptr
+    int T;
+    float *Z;
+    uint32_t *masks;     // nullable
+    float *ckpt;         // nullable
+    int ckpt_every;
+};
+
+struct BwdArgs {
+    const float *B, *C;
+    int m, N;
+    float lam;
+    const float *alpha;
+    int T;
+    const uint32_t *masks;
+    const float *ckpt;
+    int ckpt_every;
+    const float *gZ;     // nullable
+    float *dalpha;
+};
+
+struct ObjArgs {
+    const float *B, *C;
+    const double *xsq;
+    const float *Z;
+    int m, N;
+    float lam;
+    double *F, *gap;
+};
+
+struct OistaArgs {
+    const float *B, *C;
+    int m, N;
+    float lam;
+    const double *L;
+    int T;
+    float *Z;
+    double *LS;          // nullable
+    int *accepted;       // nullable
+};
+
+namespace simt {
+int padded_mp(int m);  // 32/64/128/256, or 0 if m > 256
+int launch_forward(const PgdArgs &a, cudaStream_t st);
+int launch_backward(const BwdArgs &a, void *ws, cudaStream_t st);
+size_t backward_ws_bytes(int m, int N, int T, int K);
+int launch_objective(const ObjArgs &a, cudaStream_t st);
+int launch_oista(const OistaArgs &a, void *ws, cudaStream_t st);
+size_t oista_ws_bytes(int m, int N);
+}  // namespace simt
+
+namespace gram {
+int launch_gram(const float *D, int n, int m, const float *X, int N, float *B, float *C, double *xsq,
+                cudaStream_t st);
+int launch_lipschitz_from_D(const float *D, int n, int m, double *L, cudaStream_t st);
+int launch_lipschitz_from_B(const float *B, int m, double *L, cudaStream_t st);
+}  // namespace gram
+
+namespace tc {
+// tcgen05 forward (SLISTA_PREC_BF16 / SLISTA_PREC_BF16X3).
+bool supported(int m);
+size_t forward_ws_bytes(int m);
+int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st);
+}  // namespace tc
+
+// Device-side error flag (set by bounded waits that expire).
+int read_and_clear_device_flag(cudaStream_t st);
+
+}  // namespace slista

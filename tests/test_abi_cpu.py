@@ -1,0 +1,96 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every function include/slista.h declares, sizes its
+buffers as documented, and rejects bad arguments before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1905_11071_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def _declared():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"SLISTA_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt)
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(_lib.EXPORTS) <= set(names)
+
+
+def test_sizes(lib):
+    assert _lib.slista_mask_words(256, 10000, 40) == 40 * 10000 * 8
+    assert _lib.slista_mask_words(20, 7, 3) == 3 * 7 * 1
+    assert _lib.slista_mask_words(33, 7, 3) == 3 * 7 * 2
+    # ceil(40 / 7) - 1 = 5 checkpoints, each z and g
+    assert _lib.slista_ckpt_floats(256, 10000, 40, 7) == 2 * 10000 * 256 * 5
+    assert _lib.slista_ckpt_floats(256, 100, 40, 40) == 0
+    assert _lib.slista_ckpt_floats(256, 100, 40, 50) == 0
+    assert _lib.slista_workspace_bytes(_lib.FN_SLISTA_FWD, 256, 1000, 40, _lib.PREC_FP32) == 0
+    ws = _lib.slista_workspace_bytes(_lib.FN_SLISTA_BWD, 256, 1000, 40, _lib.PREC_FP32, 7)
+    assert ws >= 4 * 7 * 1000 * 256
+    assert _lib.slista_workspace_bytes(_lib.FN_OBJECTIVE, 256, 1000, 40, 0) == 0
+
+
+def _err(lib):
+    return lib.slista_last_error().decode()
+
+
+def test_argument_validation_without_gpu(lib):
+    vp = ctypes.c_void_p(1)  # never dereferenced: validation fails first
+    # null dictionary
+    assert lib.lasso_gram(None, 4, 8, vp, 3, vp, vp, vp, None, None) == _lib.SLISTA_ERR_ARG
+    assert "D and B" in _err(lib)
+    # bad sizes
+    assert lib.lasso_gram(vp, 0, 8, vp, 3, vp, vp, vp, None, None) == _lib.SLISTA_ERR_ARG
+    # negative / NaN lambda
+    for lam in (-1.0, float("nan"), float("inf")):
+        rc = lib.slista_forward(vp, vp, 8, 4, lam, vp, 3, 0, vp, None, None, 1, None, 0, None)
+        assert rc == _lib.SLISTA_ERR_ARG, lam
+        assert "lam" in _err(lib)
+    # unknown precision and unbuilt TF32
+    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, 9, vp, None, None, 1, None, 0, None) == _lib.SLISTA_ERR_ARG
+    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_TF32, vp, None, None, 1, None, 0,
+                              None) == _lib.SLISTA_ERR_UNSUPPORTED
+    # FP32 path limit
+    assert lib.slista_forward(vp, vp, 300, 4, 0.1, vp, 3, 0, vp, None, None, 1, None, 0,
+                              None) == _lib.SLISTA_ERR_UNSUPPORTED
+    # checkpoint spacing
+    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, 0, vp, vp, vp, 0, None, 0, None) == _lib.SLISTA_ERR_ARG
+    # backward: workspace too small, missing checkpoints, precision
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, 0, vp, vp, 3, None, vp, None, 0,
+                               None) == _lib.SLISTA_ERR_WORKSPACE
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, 0, vp, None, 3, None, vp, vp, 1 << 30,
+                               None) == _lib.SLISTA_ERR_ARG
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_BF16X3, vp, vp, 3, None, vp, vp, 1 << 30,
+                               None) == _lib.SLISTA_ERR_UNSUPPORTED
+    # OISTA and objective null pointers
+    assert lib.oista_forward(vp, vp, 8, 4, 0.1, None, 3, 0, vp, None, None, None, 0, None) == _lib.SLISTA_ERR_ARG
+    assert lib.lasso_objective(vp, vp, None, vp, 8, 4, 0.1, vp, None, None) == _lib.SLISTA_ERR_ARG
+    assert lib.lasso_lipschitz(vp, 0, vp, None) == _lib.SLISTA_ERR_ARG
+    assert lib.ista_forward(vp, vp, 8, 4, 0.1, None, 3, 0, vp, None, 0, None) == _lib.SLISTA_ERR_ARG
+
+
+def test_python_binding_rejects_cpu_tensors(lib):
+    torch = pytest.importorskip("torch")
+    D = torch.zeros(4, 8)
+    X = torch.zeros(3, 4)
+    with pytest.raises(ValueError):
+        _lib.lasso_gram(D, X, torch.zeros(8, 8), torch.zeros(3, 8), torch.zeros(3, dtype=torch.float64))
