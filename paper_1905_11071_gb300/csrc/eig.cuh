@@ -30,6 +30,7 @@ struct WarpGroup {
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         return v;
     }
+    __device__ static bool any(bool p) { return __any_sync(0xffffffffu, p); }
     // smallest rank whose predicate is true (size if none)
     __device__ static int first_true(bool p, int *) {
         const unsigned b = __ballot_sync(0xffffffffu, p);
@@ -54,6 +55,7 @@ struct CtaGroup {
         for (int w = 0; w < NT / 32; ++w) s += scratch[w];
         return s;
     }
+    __device__ static bool any(bool p) { return __syncthreads_or(p) != 0; }
     __device__ static int first_true(bool p, int *scratch) {
         const unsigned b = __ballot_sync(0xffffffffu, p);
         __syncthreads();
@@ -76,7 +78,7 @@ __device__ inline int sturm_count(const float *d, const float *e2, int k, float 
     if (fabsf(q) < pivmin) q = -pivmin;
     int c = q < 0.0f;
     for (int i = 1; i < k; ++i) {
-        q = d[i] - x - e2[i - 1] / q;
+        q = d[i] - x - __fdividef(e2[i - 1], q);
         if (fabsf(q) < pivmin) q = -pivmin;
         c += q < 0.0f;
     }
@@ -115,9 +117,16 @@ __device__ double max_eig_sym(float *A, int lda, int k, float *v, float *p, floa
         float pv = 0.0f;
         for (int i = j + 1 + r0; i < k; i += G::size) {
             const float *row = A + i * lda;
-            float acc = 0.0f;
-            for (int l = j + 1; l < k; ++l) acc = fmaf(row[l], v[l], acc);
-            acc *= beta;
+            float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+            int l = j + 1;
+            for (; l + 3 < k; l += 4) {
+                a0 = fmaf(row[l], v[l], a0);
+                a1 = fmaf(row[l + 1], v[l + 1], a1);
+                a2 = fmaf(row[l + 2], v[l + 2], a2);
+                a3 = fmaf(row[l + 3], v[l + 3], a3);
+            }
+            for (; l < k; ++l) a0 = fmaf(row[l], v[l], a0);
+            const float acc = beta * ((a0 + a1) + (a2 + a3));
             p[i] = acc;
             pv = fmaf(acc, v[i], pv);
         }
@@ -128,7 +137,8 @@ __device__ double max_eig_sym(float *A, int lda, int k, float *v, float *p, floa
         for (int i = j + 1 + r0; i < k; i += G::size) {
             float *row = A + i * lda;
             const float vi = v[i], qi = p[i];
-            for (int l = j + 1; l < k; ++l) row[l] = row[l] - vi * p[l] - qi * v[l];
+#pragma unroll 4
+            for (int l = j + 1; l < k; ++l) row[l] = fmaf(-vi, p[l], fmaf(-qi, v[l], row[l]));
         }
         if (r0 == 0) e[j] = alpha;
         G::sync();
@@ -160,6 +170,264 @@ __device__ double max_eig_sym(float *A, int lda, int k, float *v, float *p, floa
         hi = nhi;
     }
     return (double)hi;
+}
+
+
+// Entry a of the start vector of the Krylov / power iterations: the
+// golden-ratio sequence 0.5 + frac((a + 1) * 0.618...), in [0.5, 1.5).
+__host__ __device__ inline float start_vector(int a)
+{
+    const float x = (float)(a + 1) * 0.6180339887f;
+    return 0.5f + (x - floorf(x));
+}
+
+// Upper end of a bracket of the largest eigenvalue of the symmetric
+// tridiagonal matrix (d[0..k-1], e[0..k-2]) by Sturm multisection over one
+// warp (33 trial points per round).  e2 receives e^2.
+__device__ inline float tridiag_max_eig_warp(const float *d, const float *e, float *e2, int k)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i + 1 < k; i += 32) e2[i] = e[i] * e[i];
+    __syncwarp();
+    float lo = -INFINITY, hi = -INFINITY, scale = 0.0f;
+    for (int i = 0; i < k; ++i) {
+        const float r = (i > 0 ? fabsf(e[i - 1]) : 0.0f) + (i + 1 < k ? fabsf(e[i]) : 0.0f);
+        lo = fmaxf(lo, d[i]);
+        hi = fmaxf(hi, d[i] + r);
+        scale = fmaxf(scale, fabsf(d[i]) + r);
+    }
+    const float pivmin = fmaxf(scale * 1e-30f, 1e-37f);
+    hi = hi + 2e-7f * scale;
+    for (int round = 0; round < 8 && hi - lo > 1.2e-7f * scale; ++round) {
+        const float x = lo + (hi - lo) * (float)(lane + 1) / 33.0f;
+        const bool above_all = sturm_count(d, e2, k, x, pivmin) == k;
+        const unsigned b = __ballot_sync(0xffffffffu, above_all);
+        const int f = b ? __ffs(b) - 1 : 32;
+        const float nhi = f < 32 ? lo + (hi - lo) * (float)(f + 1) / 33.0f : hi;
+        const float nlo = f > 0 ? lo + (hi - lo) * (float)f / 33.0f : lo;
+        lo = nlo;
+        hi = nhi;
+    }
+    return hi;
+}
+
+// Largest eigenvalue of a k x k symmetric matrix by Lanczos (one warp).
+// The three-term recurrence  beta_j q_{j+1} = A q_j - alpha_j q_j - beta_{j-1} q_{j-1}
+// builds the tridiagonal T_J whose largest eigenvalue (the top Ritz value)
+// converges to that of A from below; in finite precision the extreme Ritz
+// values stay accurate without reorthogonalisation (Paige).  J = k steps are
+// run when k <= 32 (T_k is then similar to A); otherwise steps are added in
+// blocks of 16, up to LANCZOS_JMAX, until the top Ritz value moves by less
+// than 2e-7 (relative).  A is in shared memory with leading dimension lda.
+// q, qp: k floats; al, be, e2: LANCZOS_JMAX floats of warp scratch.
+// RPL = rows per lane (>= ceil(k / 32)).
+constexpr int LANCZOS_JMAX = 64;
+
+template <int RPL>
+__device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q, float *qp, float *al, float *be,
+                                       float *e2)
+{
+    constexpr int JMAX = LANCZOS_JMAX;
+    const int lane = threadIdx.x & 31;
+    // generic start vector (a structured one such as all-ones can be exactly
+    // orthogonal to the top eigenvector, e.g. [[1, c], [c, 1]] with c < 0)
+    float nrm0 = 0.0f;
+    for (int a = lane; a < k; a += 32) {
+        const float v = start_vector(a);
+        nrm0 = fmaf(v, v, nrm0);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm0 += __shfl_xor_sync(0xffffffffu, nrm0, o);
+    const float inv = rsqrtf(nrm0);
+    for (int a = lane; a < k; a += 32) {
+        q[a] = start_vector(a) * inv;
+        qp[a] = 0.0f;
+    }
+    __syncwarp();
+    float beta_prev = 0.0f;
+    float theta_prev = -INFINITY, theta = 0.0f;
+    int j = 0;
+    int target = k <= 32 ? k : 32;
+    bool done = false;
+#pragma unroll 1
+    for (;;) {
+#pragma unroll 1
+        for (; j < target; ++j) {
+            float w[RPL];
+            float dot = 0.0f;
+#pragma unroll
+            for (int rr = 0; rr < RPL; ++rr) {
+                const int a = lane + 32 * rr;
+                float s = 0.0f;
+                if (a < k) {
+                    const float *row = A + a * lda;
+                    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+                    int b = 0;
+                    for (; b + 3 < k; b += 4) {
+                        s0 = fmaf(row[b], q[b], s0);
+                        s1 = fmaf(row[b + 1], q[b + 1], s1);
+                        s2 = fmaf(row[b + 2], q[b + 2], s2);
+                        s3 = fmaf(row[b + 3], q[b + 3], s3);
+                    }
+                    for (; b < k; ++b) s0 = fmaf(row[b], q[b], s0);
+                    s = (s0 + s1) + (s2 + s3);
+                    dot = fmaf(s, q[a], dot);
+                }
+                w[rr] = s;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            const float alpha = dot;
+            float nrm = 0.0f;
+#pragma unroll
+            for (int rr = 0; rr < RPL; ++rr) {
+                const int a = lane + 32 * rr;
+                if (a < k) {
+                    w[rr] = w[rr] - alpha * q[a] - beta_prev * qp[a];
+                    nrm = fmaf(w[rr], w[rr], nrm);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+            const float beta = sqrtf(nrm);
+            if (lane == 0) {
+                al[j] = alpha;
+                be[j] = beta;
+            }
+            __syncwarp();
+            if (beta <= 1e-6f * fabsf(alpha) || j + 1 == k) {  // invariant subspace or full dimension
+                ++j;
+                done = true;
+                break;
+            }
+            const float ib = 1.0f / beta;
+#pragma unroll
+            for (int rr = 0; rr < RPL; ++rr) {
+                const int a = lane + 32 * rr;
+                if (a < k) {
+                    qp[a] = q[a];
+                    q[a] = w[rr] * ib;
+                }
+            }
+            __syncwarp();
+            beta_prev = beta;
+        }
+        theta = tridiag_max_eig_warp(al, be, e2, j);
+        if (done) break;                                        // exhausted
+        if (theta - theta_prev <= 2e-7f * fabsf(theta)) break;  // converged
+        if (j >= JMAX || j >= k) break;
+        theta_prev = theta;
+        target = min(min(j + 16, k), JMAX);
+    }
+    return (double)theta;
+}
+
+// Upper end of a bracket of the largest eigenvalue of the symmetric
+// tridiagonal (d, e) by Sturm multisection over a whole CTA (NT + 1 points
+// per round).  e2: k floats (written).  redi: NT/32 ints of scratch.
+template <int NT>
+__device__ float tridiag_max_eig_cta(const float *d, const float *e, float *e2, int k, int *redi)
+{
+    for (int i = threadIdx.x; i + 1 < k; i += NT) e2[i] = e[i] * e[i];
+    __syncthreads();
+    float lo = -INFINITY, hi = -INFINITY, scale = 0.0f;
+    for (int i = 0; i < k; ++i) {
+        const float r = (i > 0 ? fabsf(e[i - 1]) : 0.0f) + (i + 1 < k ? fabsf(e[i]) : 0.0f);
+        lo = fmaxf(lo, d[i]);
+        hi = fmaxf(hi, d[i] + r);
+        scale = fmaxf(scale, fabsf(d[i]) + r);
+    }
+    const float pivmin = fmaxf(scale * 1e-30f, 1e-37f);
+    hi = hi + 2e-7f * scale;
+    for (int round = 0; round < 6 && hi - lo > 1.2e-7f * scale; ++round) {
+        const float x = lo + (hi - lo) * (float)(threadIdx.x + 1) / (float)(NT + 1);
+        const bool above_all = sturm_count(d, e2, k, x, pivmin) == k;
+        const int f = CtaGroup<NT>::first_true(above_all, redi);
+        const float nhi = f < NT ? lo + (hi - lo) * (float)(f + 1) / (float)(NT + 1) : hi;
+        const float nlo = f > 0 ? lo + (hi - lo) * (float)f / (float)(NT + 1) : lo;
+        lo = nlo;
+        hi = nhi;
+    }
+    return hi;
+}
+
+// Lanczos as in lanczos_max_eig_warp, with every product spread over a CTA:
+// row a of the matrix-vector product is summed by TPR = 2^floor(log2(NT/k))
+// threads (strided columns, shuffle-combined).  q, qp, w: k floats; al, be,
+// e2: LANCZOS_JMAX floats; redf: NT/32 floats, redi: NT/32 ints (scratch).
+template <int NT>
+__device__ double lanczos_max_eig_cta(const float *A, int lda, int k, float *q, float *qp, float *w, float *al,
+                                      float *be, float *e2, float *redf, int *redi)
+{
+    constexpr int JMAX = LANCZOS_JMAX;
+    int tpr = 1;
+    while (tpr < 32 && tpr * 2 * k <= NT) tpr *= 2;
+    const int row = threadIdx.x / tpr, col0 = threadIdx.x % tpr;
+    const bool has_row = row < k;
+    float nrm0 = 0.0f;
+    for (int a = threadIdx.x; a < k; a += NT) {
+        const float v = start_vector(a);
+        nrm0 = fmaf(v, v, nrm0);
+    }
+    nrm0 = CtaGroup<NT>::sum(nrm0, redf);
+    const float inv = rsqrtf(nrm0);
+    for (int a = threadIdx.x; a < k; a += NT) {
+        q[a] = start_vector(a) * inv;
+        qp[a] = 0.0f;
+    }
+    __syncthreads();
+    float beta_prev = 0.0f, theta_prev = -INFINITY, theta = 0.0f;
+    int j = 0, target = k <= 32 ? k : 32;
+    bool done = false;
+#pragma unroll 1
+    for (;;) {
+#pragma unroll 1
+        for (; j < target; ++j) {
+            float s = 0.0f;
+            if (has_row) {
+                const float *r = A + row * lda;
+                float s0 = 0.0f, s1 = 0.0f;
+                int b = col0;
+                for (; b + tpr < k; b += 2 * tpr) {
+                    s0 = fmaf(r[b], q[b], s0);
+                    s1 = fmaf(r[b + tpr], q[b + tpr], s1);
+                }
+                if (b < k) s0 = fmaf(r[b], q[b], s0);
+                s = s0 + s1;
+            }
+            for (int o = tpr / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            const bool lead = has_row && col0 == 0;
+            const float alpha = CtaGroup<NT>::sum(lead ? s * q[row] : 0.0f, redf);
+            float wv = 0.0f;
+            if (lead) wv = s - alpha * q[row] - beta_prev * qp[row];
+            const float beta = sqrtf(CtaGroup<NT>::sum(lead ? wv * wv : 0.0f, redf));
+            if (threadIdx.x == 0) {
+                al[j] = alpha;
+                be[j] = beta;
+            }
+            if (beta <= 1e-6f * fabsf(alpha) || j + 1 == k) {
+                ++j;
+                done = true;
+                break;
+            }
+            if (lead) w[row] = wv / beta;
+            __syncthreads();
+            for (int a = threadIdx.x; a < k; a += NT) {
+                qp[a] = q[a];
+                q[a] = w[a];
+            }
+            __syncthreads();
+            beta_prev = beta;
+        }
+        __syncthreads();
+        theta = tridiag_max_eig_cta<NT>(al, be, e2, j, redi);
+        if (done) break;
+        if (theta - theta_prev <= 2e-7f * fabsf(theta)) break;
+        if (j >= JMAX || j >= k) break;
+        theta_prev = theta;
+        target = min(min(j + 16, k), JMAX);
+    }
+    return (double)theta;
 }
 
 }  // namespace eig

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(PI_NT) lipschitz_kernel(const float *__restric
     }
     // power iteration fallback (mode 0 only)
     float *v = sm;
-    for (int a = threadIdx.x; a < k; a += PI_NT) v[a] = 1.0f;
+    for (int a = threadIdx.x; a < k; a += PI_NT) v[a] = eig::start_vector(a);
     __syncthreads();
     double best = 0.0;
     int stall = 0;

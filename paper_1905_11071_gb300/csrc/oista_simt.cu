@@ -10,8 +10,9 @@
 //   L_S     Only samples whose step is accepted need L_S = lambda_max(B_SS)
 //           (Eq. spca); it is recomputed only when S differs from the support
 //           it was last computed for (L_empty = L, |S| = 1 gives B_jj).  One
-//           warp gathers B_SS into shared memory and runs the Householder /
-//           Sturm solver of eig.cuh; larger supports go to a block-wide buffer.
+//           warp gathers B_SS into shared memory and runs Lanczos with a Sturm
+//           multisection on the Lanczos tridiagonal (eig.cuh); larger
+//           supports are gathered by the whole block into a shared buffer.
 //   step    z^(t+1) = ST(z + a g, a lam) with a = 1/L_S if (star) holds,
 //           else a = 1/L (the ISTA fallback of Algorithm 1);
 //   update  g <- g + (z^(t) - z^(t+1)) B, as in the forward kernel.
@@ -29,22 +30,24 @@ namespace {
 
 constexpr int KMAX = 64;  // largest |S| solved by one warp in its own buffer
 
+constexpr int JM = eig::LANCZOS_JMAX;
+
 template <int MP>
 struct WarpEig {
     static constexpr int LDA = eig::odd_ld(KMAX);
     float A[KMAX * LDA];
-    float v[KMAX], p[KMAX], d[KMAX], e[KMAX], e2[KMAX];
+    float q[KMAX], qp[KMAX], al[JM], be[JM], e2[JM];
     int idx[MP];
 };
 
-// Largest k whose k x odd_ld(k) matrix, five k-vectors and MP indices fit in
-// the eight warps' buffers together.
+// Largest k whose k x odd_ld(k) matrix, three k-vectors, the Lanczos scratch
+// and MP indices fit in the eight warps' buffers together.
 template <int MP>
 __host__ __device__ constexpr int kbig()
 {
     constexpr int words = (int)(sizeof(WarpEig<MP>) / 4) * (NT / 32);
     int k = MP;
-    while (k > KMAX && k * eig::odd_ld(k) + 5 * k + MP > words) --k;
+    while (k > KMAX && k * eig::odd_ld(k) + 3 * k + 3 * JM + MP > words) --k;
     return k;
 }
 
@@ -60,14 +63,45 @@ struct OistaSmem {
 };
 
 // Gathers B_SS (k x k, indices idx) into A with leading dimension lda.
+// Returns whether B_SS has a non-zero off-diagonal entry (group-uniform).
 template <class G>
-__device__ void gather_bss(const float *__restrict__ B, int m, const int *idx, int k, float *A, int lda)
+__device__ bool gather_bss(const float *__restrict__ B, int m, const int *idx, int k, float *A, int lda)
 {
-    for (int e = G::rank(); e < k * k; e += G::size) {
+    const int kk = k * k;
+    bool off = false;
+    int e = G::rank();
+    for (; e + 3 * G::size < kk; e += 4 * G::size) {
+        float x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = e + u * G::size;
+            x[u] = __ldg(B + (size_t)idx[q / k] * m + idx[q % k]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = e + u * G::size;
+            const int a = q / k, b = q % k;
+            A[a * lda + b] = x[u];
+            off |= (a != b) && (x[u] != 0.0f);
+        }
+    }
+    for (; e < kk; e += G::size) {
         const int a = e / k, b = e % k;
-        A[a * lda + b] = __ldg(B + (size_t)idx[a] * m + idx[b]);
+        const float x = __ldg(B + (size_t)idx[a] * m + idx[b]);
+        A[a * lda + b] = x;
+        off |= (a != b) && (x != 0.0f);
     }
     G::sync();
+    return G::any(off);
+}
+
+// Largest diagonal entry of A (the largest eigenvalue when A is diagonal,
+// e.g. B_SS of an orthogonal D_S, where it is exact).
+__device__ inline float max_diag(const float *A, int lda, int k)
+{
+    float v = A[0];
+    for (int a = 1; a < k; ++a) v = fmaxf(v, A[a * lda + a]);
+    return v;
 }
 
 // Fallback for supports too large for shared memory: power iteration on B_SS
@@ -77,7 +111,7 @@ template <int MP>
 __device__ double power_iteration_global(const float *__restrict__ B, int m, const int *idx, int k, float *v)
 {
     const int lane = threadIdx.x & 31;
-    for (int a = lane; a < k; a += 32) v[a] = 1.0f;
+    for (int a = lane; a < k; a += 32) v[a] = eig::start_vector(a);
     __syncwarp();
     double best = 0.0;
     int stall = 0;
@@ -162,7 +196,9 @@ __global__ void __launch_bounds__(NT) oista_kernel(
     int *flag = reinterpret_cast<int *>(LSrow + NB);  // 1: condition (star) fails
     int *valid = flag + NB;                           // LSrow[r] holds L_{Sprev[r]}
     int *deferred = valid + NB;                       // rows whose support is too large for a warp
-    int *ctr = deferred + NB;                         // [0] queue, [1] accepted, [2] #deferred
+    int *ctr = deferred + NB;                         // [0] queue, [1] accepted, [2] #deferred, [4] |S|
+    __shared__ float redf[NT / 32];
+    __shared__ int redi[NT / 32];
 
     const Idx<TL> ix;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -217,9 +253,12 @@ __global__ void __launch_bounds__(NT) oista_kernel(
             } else if (k == 1) {
                 LS = (double)__ldg(B + (size_t)we.idx[0] * m + we.idx[0]);
             } else if (k <= KMAX) {
-                gather_bss<eig::WarpGroup>(B, m, we.idx, k, we.A, eig::odd_ld(k));
-                LS = eig::max_eig_sym<eig::WarpGroup>(we.A, eig::odd_ld(k), k, we.v, we.p, we.d, we.e, we.e2,
-                                                      nullptr, nullptr);
+                const int lda = eig::odd_ld(k);
+                if (gather_bss<eig::WarpGroup>(B, m, we.idx, k, we.A, lda))
+                    LS = eig::lanczos_max_eig_warp<(KMAX + 31) / 32>(we.A, lda, k, we.q, we.qp, we.al, we.be,
+                                                                     we.e2);
+                else
+                    LS = (double)max_diag(we.A, lda, k);
             } else {
                 if (lane == 0) deferred[atomicAdd(&ctr[2], 1)] = lr;
                 continue;
@@ -232,34 +271,37 @@ __global__ void __launch_bounds__(NT) oista_kernel(
             for (int w = lane; w < WP; w += 32) Sprev[lr * WP + w] = Scur[lr * WP + w];
         }
         __syncthreads();
-        // 3. large supports: warp 0 with every warp's buffer
+        // 3. large supports: the whole block on every warp's buffer, one at a time
         const int ndef = ctr[2];
-        if (ndef > 0) {
+#pragma unroll 1
+        for (int q = 0; q < ndef; ++q) {
+            const int lr = deferred[q];
+            int *idx = reinterpret_cast<int *>(big);
+            int *kp = ctr + 4;
             if (warp == 0) {
-                for (int q = 0; q < ndef; ++q) {
-                    const int lr = deferred[q];
-                    int *idx = reinterpret_cast<int *>(big);
-                    const int k = support_indices(Scur + lr * WP, WP, idx);
-                    double LS;
-                    if (k <= KBIG) {
-                        const int lda = eig::odd_ld(k);
-                        float *A = big + MP;
-                        float *vv = A + k * lda;
-                        gather_bss<eig::WarpGroup>(B, m, idx, k, A, lda);
-                        LS = eig::max_eig_sym<eig::WarpGroup>(A, lda, k, vv, vv + k, vv + 2 * k, vv + 3 * k,
-                                                              vv + 4 * k, nullptr, nullptr);
-                    } else {
-                        LS = power_iteration_global<MP>(B, m, idx, k, big + MP);
-                    }
-                    __syncwarp();
-                    if (lane == 0) {
-                        LSrow[lr] = LS;
-                        valid[lr] = 1;
-                    }
-                    for (int w = lane; w < WP; w += 32) Sprev[lr * WP + w] = Scur[lr * WP + w];
-                    __syncwarp();
-                }
+                const int k = support_indices(Scur + lr * WP, WP, idx);
+                if (lane == 0) *kp = k;
             }
+            __syncthreads();
+            const int k = *kp;
+            double LS;
+            if (k <= KBIG) {
+                const int lda = eig::odd_ld(k);
+                float *A = big + MP;
+                float *vv = A + k * lda;
+                const bool off = gather_bss<eig::CtaGroup<NT>>(B, m, idx, k, A, lda);
+                LS = off ? eig::lanczos_max_eig_cta<NT>(A, lda, k, vv, vv + k, vv + 2 * k, vv + 3 * k,
+                                                        vv + 3 * k + JM, vv + 3 * k + 2 * JM, redf, redi)
+                         : (double)max_diag(A, lda, k);
+            } else {
+                LS = 0.0;
+                if (warp == 0) LS = power_iteration_global<MP>(B, m, idx, k, big + MP);
+            }
+            if (threadIdx.x == 0) {
+                LSrow[lr] = LS;
+                valid[lr] = 1;
+            }
+            for (int w = threadIdx.x; w < WP; w += NT) Sprev[lr * WP + w] = Scur[lr * WP + w];
             __syncthreads();
         }
         // 4. the step: 1/L_S if (star) holds, else the ISTA step 1/L
