@@ -1,0 +1,160 @@
+"""Parity of the tcgen05 tensor-core forward (SLISTA_PREC_BF16X3 and
+SLISTA_PREC_BF16) with the FP64 oracle, through the C ABI.
+
+Tolerances: relative objective error per sample <= 1e-5 for the split
+BF16X3 product and <= 1e-3 for plain BF16 (the two precision classes the
+method is held to); codes z elementwise <= 1e-4 * max(1, max|z|) (BF16X3) and
+<= 2e-2 * max(1, max|z|) (BF16); support masks bit-exact where the oracle's
+pre-threshold margin exceeds 1e-4 (BF16X3).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_11071_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16x3": {"F": 1e-5, "Z": 1e-4}, "bf16": {"F": 1e-3, "Z": 2e-2}}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1905_11071_gb300 import build, _lib
+    build.build()
+    _lib.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def api():
+    from paper_1905_11071_gb300 import api as A
+    return A
+
+
+def _check(prec, Zg, Fg, Zo, Fo):
+    zt = TOL[prec]["Z"] * max(1.0, float(np.abs(Zo).max()))
+    zerr = float(np.abs(Zg.astype(np.float64) - Zo).max())
+    ferr = float((np.abs(Fg - Fo) / np.abs(Fo)).max())
+    assert zerr <= zt, (prec, zerr, zt)
+    assert ferr <= TOL[prec]["F"], (prec, ferr)
+    return zerr, ferr
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("N", [1, 127, 128, 700])
+def test_slista_forward_tc_64x256(prec, N):
+    w = synth.slista_64x256(N=N, T=40)
+    Lo = oracle.lipschitz(w.D)
+    alpha = synth.step_sizes(w.T, 1.0 / Lo, 0.3, seed=5)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    Z = A.slista(g.B, g.C, w.lam, dev(alpha), prec=prec)
+    F = host(A.objective(g.B, g.C, g.xsq, Z, w.lam, with_gap=False))
+    Zo = oracle.pgd(w.D, w.X, w.lam, alpha)
+    Fo = oracle.objective(w.D, w.X, Zo, w.lam, with_gap=False)
+    _check(prec, host(Z), F, Zo, Fo)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("n,m", [(10, 20), (32, 64), (48, 100), (64, 128)])
+def test_slista_forward_tc_small_m(prec, n, m):
+    """m padded to 64 / 128 inside the kernel (B_lo resident)."""
+    rng = np.random.default_rng(n + m)
+    D = synth.gaussian_dictionary(n, m, rng)
+    X = synth.sparse_model_samples(D, 300, 0.1, 0.01, rng)
+    lam = synth.lam_fraction(D, X, 0.1)
+    T = 30
+    Lo = oracle.lipschitz(D)
+    alpha = synth.step_sizes(T, 1.0 / Lo, 0.3, seed=6)
+    A = api()
+    g = A.gram(dev(D), dev(X))
+    Z = A.slista(g.B, g.C, lam, dev(alpha), prec=prec)
+    F = host(A.objective(g.B, g.C, g.xsq, Z, lam, with_gap=False))
+    Zo = oracle.pgd(D, X, lam, alpha)
+    _check(prec, host(Z), F, Zo, oracle.objective(D, X, Zo, lam, with_gap=False))
+
+
+def test_tc_masks_bit_exact_where_safe():
+    w = synth.slista_64x256(N=300, T=40)
+    Lo = oracle.lipschitz(w.D)
+    alpha = synth.step_sizes(w.T, 1.0 / Lo, 0.3, seed=8)
+    A = api()
+    from paper_1905_11071_gb300 import _lib
+    g = A.gram(dev(w.D), dev(w.X))
+    Z = torch.empty((w.N, w.m), dtype=torch.float32, device="cuda")
+    masks = torch.zeros(_lib.slista_mask_words(w.m, w.N, w.T), dtype=torch.int32, device="cuda")
+    ws = A.workspace(_lib.slista_workspace_bytes(_lib.FN_SLISTA_FWD, w.m, w.N, w.T, _lib.PREC_BF16X3),
+                     Z.device, "t")
+    _lib.slista_forward(g.B, g.C, w.lam, dev(alpha), _lib.PREC_BF16X3, Z, masks=masks, ws=ws)
+    Zall = oracle.pgd(w.D, w.X, w.lam, alpha, keep_all=True)
+    words = host(masks).view(np.uint32).astype(np.uint64).reshape(w.T, w.N, 8, 1)
+    bits = ((words >> np.arange(32, dtype=np.uint64)) & np.uint64(1)).reshape(w.T, w.N, 256).astype(bool)
+    D = w.D.astype(np.float64)
+    X = w.X.astype(np.float64)
+    for t in range(w.T):
+        u = Zall[t] - float(alpha[t]) * ((Zall[t] @ D.T - X) @ D)
+        safe = np.abs(np.abs(u) - float(alpha[t]) * w.lam) > 1e-4
+        assert np.array_equal(bits[t][safe], (Zall[t + 1] != 0)[safe]), t
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_tc_ista_matches_slista_constant_step(prec):
+    w = synth.slista_64x256(N=260, T=25)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    a = (1.0 / g.L.double()).float().expand(w.T).contiguous()
+    assert torch.equal(A.ista(g.B, g.C, w.lam, g.L, w.T, prec=prec), A.slista(g.B, g.C, w.lam, a, prec=prec))
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_tc_identity_dictionary_one_layer_exact(prec):
+    """D = Id: the first layer reads g = c exactly, so z^(1) = ST(x, lam) bit for bit."""
+    rng = np.random.default_rng(9)
+    D = np.eye(128, dtype=np.float32)
+    X = rng.standard_normal((200, 128)).astype(np.float32)
+    A = api()
+    g = A.gram(dev(D), dev(X))
+    Z = host(A.ista(g.B, g.C, 0.5, g.L, 1, prec=prec))
+    want = np.sign(X) * np.maximum(np.abs(X) - np.float32(0.5), 0)
+    assert np.array_equal(Z, want)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_tc_zero_above_lambda_max(prec):
+    w = synth.slista_64x256(N=200, T=10)
+    lam = float(np.float32(np.abs(w.X.astype(np.float64) @ w.D.astype(np.float64)).max() * 1.001))
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    assert not A.ista(g.B, g.C, lam, g.L, 10, prec=prec).any()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_tc_full_size_sampled_rows(prec):
+    """The benchmark workload (64 x 256, N = 10000, T = 40), 64 sampled rows."""
+    w = synth.slista_64x256()
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    alpha = (1.0 / g.L.double()).float().expand(w.T).contiguous()
+    Z = A.slista(g.B, g.C, w.lam, alpha, prec=prec)
+    F = host(A.objective(g.B, g.C, g.xsq, Z, w.lam, with_gap=False))
+    assert np.isfinite(F).all()
+    rows = np.random.default_rng(1).choice(w.N, size=64, replace=False)
+    Lo = oracle.lipschitz(w.D)
+    Zo = oracle.ista(w.D, w.X[rows], w.lam, Lo, w.T)
+    Fo = oracle.objective(w.D, w.X[rows], Zo, w.lam, with_gap=False)
+    _check(prec, host(Z)[rows], F[rows], Zo, Fo)
+
+
+def test_tc_device_flag_clear_after_runs():
+    from paper_1905_11071_gb300 import _lib
+    _lib.slista_device_status()
