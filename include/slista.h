@@ -128,6 +128,28 @@ SLISTA_API int slista_forward(const float *B, const float *C, int m, int N, floa
                    uint32_t *masks, float *ckpt, int ckpt_every,
                    void *ws, size_t ws_bytes, void *stream);
 
+/* Step-LISTA forward on the tensor cores (SLISTA_PREC_BF16 or
+ * SLISTA_PREC_BF16X3) that allocates nothing and takes no workspace.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory when they call - code whose device memory is owned
+ * by another allocator or reserved in full at start-up (a framework's
+ * caching pool, a fixed arena, a per-process quota), and loops that cannot
+ * afford the device-wide synchronisation cudaMalloc / cudaFree imply.
+ * Arguments, results and arithmetic are those of slista_forward with
+ * ckpt = NULL (the same kernel runs).  Its only scratch, the split copy of B
+ * (256 KiB), lives in a static device array of the library, which every GPU
+ * that loads the library holds until the process exits; m is limited to
+ * m <= 256 by its size (larger m: SLISTA_ERR_UNSUPPORTED).
+ * The first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the array and each call rewrites it completely
+ * before use: calls whose work may overlap on the GPU (different streams
+ * without ordering between them) race on it and must be serialised by the
+ * caller. */
+SLISTA_API int slista_forward_noalloc(const float *B, const float *C, int m, int N, float lam,
+                                      const float *alpha, int T, int prec, float *Z, uint32_t *masks,
+                                      void *stream);
+
 /* Step-LISTA backward: the sub-gradient of sum_i F_{x_i}(z_i^(T)) (the
  * empirical form of Eq. unsupervised) with respect to alpha, obtained by the
  * chain rule on Eq. steprec, with derivative 0 at the kinks of ST and of |z|

@@ -37,7 +37,7 @@ FN_OBJECTIVE = 5
 EXPORTS = [
     "slista_last_error", "slista_device_status", "slista_workspace_bytes", "slista_ckpt_floats",
     "slista_mask_words", "lasso_gram", "lasso_lipschitz", "ista_forward", "slista_forward",
-    "slista_backward", "oista_forward", "lasso_objective",
+    "slista_backward", "oista_forward", "lasso_objective", "slista_forward_noalloc",
 ]
 
 
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
         lib.ista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, sz, vp]
         lib.slista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp, i, vp, sz, vp]
         lib.slista_backward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, i, vp, vp, vp, sz, vp]
+        lib.slista_forward_noalloc.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp]
         lib.oista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
         lib.lasso_objective.argtypes = [vp, vp, vp, vp, i, i, f, vp, vp, vp]
         for name in EXPORTS:
@@ -203,6 +204,21 @@ def slista_forward(B, C, lam, alpha, prec, Z, masks=None, ckpt=None, ckpt_every=
     _check(load().slista_forward(_ptr(B), _ptr(C), m, N, float(lam), _ptr(alpha), T, int(prec), _ptr(Z),
                                  _ptr(masks), _ptr(ckpt), int(ckpt_every), _ptr(ws), wsb, _stream(stream)),
            "slista_forward")
+
+
+def slista_forward_noalloc(B, C, lam, alpha, prec, Z, masks=None, stream=None) -> None:
+    """Tensor-core Step-LISTA forward without workspace (static device scratch)."""
+    import torch
+    m = B.shape[0]
+    N = C.shape[0]
+    T = alpha.shape[0]
+    _need(B, torch.float32, (m, m), "B")
+    _need(C, torch.float32, (N, m), "C")
+    _need(alpha, torch.float32, (T,), "alpha")
+    _need(Z, torch.float32, (N, m), "Z")
+    _opt(masks, torch.int32, None, "masks")
+    _check(load().slista_forward_noalloc(_ptr(B), _ptr(C), m, N, float(lam), _ptr(alpha), T, int(prec), _ptr(Z),
+                                         _ptr(masks), _stream(stream)), "slista_forward_noalloc")
 
 
 def slista_backward(B, C, lam, alpha, prec, masks, ckpt, ckpt_every, dalpha, gZ=None, ws=None,

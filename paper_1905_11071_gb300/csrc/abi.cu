@@ -184,6 +184,24 @@ int slista_forward(const float *B, const float *C, int m, int N, float lam, cons
     return forward_common(a, prec, ws, ws_bytes, as_stream(stream), "slista_forward");
 }
 
+int slista_forward_noalloc(const float *B, const float *C, int m, int N, float lam, const float *alpha, int T,
+                           int prec, float *Z, uint32_t *masks, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 0, SLISTA_ERR_ARG, "slista_forward_noalloc: bad sizes m=%d N=%d T=%d", m,
+                   N, T);
+    SLISTA_REQUIRE(B && (T == 0 || alpha), SLISTA_ERR_ARG, "slista_forward_noalloc: B and alpha must not be NULL");
+    SLISTA_REQUIRE(N == 0 || (C && Z), SLISTA_ERR_ARG, "slista_forward_noalloc: C and Z must not be NULL");
+    SLISTA_REQUIRE(prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3, SLISTA_ERR_UNSUPPORTED,
+                   "slista_forward_noalloc: precision must be SLISTA_PREC_BF16 or SLISTA_PREC_BF16X3 (got %d)", prec);
+    SLISTA_REQUIRE(m <= tc::noalloc_max_m(), SLISTA_ERR_UNSUPPORTED,
+                   "slista_forward_noalloc: m = %d exceeds the static scratch limit m <= %d", m, tc::noalloc_max_m());
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    PgdArgs a{B, C, m, N, lam, alpha, nullptr, T, Z, masks, nullptr, 1};
+    return tc::launch_forward_noalloc(a, prec, as_stream(stream));
+}
+
 int slista_backward(const float *B, const float *C, int m, int N, float lam, const float *alpha, int T, int prec,
                     const uint32_t *masks, const float *ckpt, int ckpt_every, const float *gZ, float *dalpha,
                     void *ws, size_t ws_bytes, void *stream)

@@ -76,6 +76,8 @@ namespace tc {
 bool supported(int m);
 size_t forward_ws_bytes(int m);
 int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st);
+int launch_forward_noalloc(const PgdArgs &a, int prec, cudaStream_t st);
+int noalloc_max_m();
 }  // namespace tc
 
 // Device-side error flag (set by bounded waits that expire).

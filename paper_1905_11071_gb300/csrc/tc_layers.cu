@@ -24,6 +24,8 @@
 // releasing its tensor memory.
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -505,6 +507,52 @@ int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st)
         case 256: return split ? launch_mp<256, true>(a, ws, st) : launch_mp<256, false>(a, ws, st);
     }
     return fail(SLISTA_ERR_UNSUPPORTED, "tensor-core path supports m <= 256 (got %d)", a.m);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant (slista_forward_noalloc): the only scratch of the
+// tensor-core forward is the split copy of B (B_hi and B_lo, BF16, swizzled),
+// held here in a file-scope device array sized for m <= NOALLOC_MAX_M.  The
+// array exists once per device for the life of the process; every call
+// rewrites all of it before the layer kernel reads it, so nothing needs
+// clearing, but two calls whose work overlaps on the GPU would race on it.
+// ---------------------------------------------------------------------------
+constexpr int NOALLOC_MAX_M = 256;
+constexpr size_t NOALLOC_BYTES = (size_t)NOALLOC_MAX_M * NOALLOC_MAX_M * 2 * 2;  // 256 KiB
+static __device__ __align__(256) uint8_t g_noalloc_bsplit[NOALLOC_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+int noalloc_max_m() { return NOALLOC_MAX_M; }
+
+int launch_forward_noalloc(const PgdArgs &a, int prec, cudaStream_t st)
+{
+    if (mp_for(a.m) == 0 || forward_ws_bytes(a.m) > NOALLOC_BYTES)
+        return fail(SLISTA_ERR_UNSUPPORTED, "slista_forward_noalloc: m = %d exceeds the static scratch limit m <= %d",
+                    a.m, NOALLOC_MAX_M);
+    int dev = 0;
+    SLISTA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return fail(SLISTA_ERR_UNSUPPORTED, "slista_forward_noalloc: device %d out of range", dev);
+    void *scratch = nullptr;
+    {
+        // once per device, with that device current: the device address of
+        // the array (its host-side name is not a device address)
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (g_noalloc_ptr[dev] == nullptr) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_bsplit);
+            if (e != cudaSuccess)
+                return fail(SLISTA_ERR_CUDA, "slista_forward_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    return launch_forward(a, prec, scratch, st);
 }
 
 }  // namespace tc
