@@ -160,10 +160,13 @@ SLISTA_API int slista_forward_noalloc(const float *B, const float *C, int m, int
  *                        dalpha_t = sum_i <h_i, g_i^(t) - lam sign(z_i^(t+1))>;
  *                        G = h - alpha_t B h
  * where g^(t) = c - B z^(t).  Iterates between checkpoints are recomputed
- * from `ckpt` with the same arithmetic as slista_forward, so masks, ckpt and
+ * from `ckpt` with the FP32 arithmetic of slista_forward, so masks, ckpt and
  * ckpt_every must come from a slista_forward call with the same B, C, lam,
- * alpha, T and prec.  gZ (nullable, N x m): upstream gradient dLoss/dz^(T).
- * dalpha (T, float32) receives the sub-gradient.  Only SLISTA_PREC_FP32. */
+ * alpha and T (any precision: after a tensor-core forward the recomputed
+ * segments follow the FP32 trajectory from each checkpoint).
+ * gZ (nullable, N x m): upstream gradient dLoss/dz^(T).  dalpha (T, float32)
+ * receives the sub-gradient.  prec selects the arithmetic of the adjoint;
+ * only SLISTA_PREC_FP32 is built. */
 SLISTA_API int slista_backward(const float *B, const float *C, int m, int N, float lam,
                     const float *alpha, int T, int prec,
                     const uint32_t *masks, const float *ckpt, int ckpt_every,

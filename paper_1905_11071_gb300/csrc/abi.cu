@@ -79,8 +79,6 @@ int forward_common(const PgdArgs &a, int prec, void *ws, size_t ws_bytes, cudaSt
     if (prec == SLISTA_PREC_TF32) return fail(SLISTA_ERR_UNSUPPORTED, "%s: TF32 is not built", name);
     SLISTA_REQUIRE(tc::supported(a.m), SLISTA_ERR_UNSUPPORTED, "%s: tensor-core path does not support m = %d", name,
                    a.m);
-    SLISTA_REQUIRE(a.ckpt == nullptr, SLISTA_ERR_UNSUPPORTED,
-                   "%s: checkpoints are produced by the FP32 path only", name);
     const size_t need = tc::forward_ws_bytes(a.m);
     SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws != nullptr), SLISTA_ERR_WORKSPACE,
                    "%s: workspace of %zu bytes needed, %zu given", name, need, ws_bytes);

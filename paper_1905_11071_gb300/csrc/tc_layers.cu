@@ -1,8 +1,8 @@
 // tcgen05 (sm_103a tensor core) forward kernel for the unfolded
 // proximal-gradient layers (Eq. pgd / Eq. steprec): ISTA and Step-LISTA.
 //
-// Per CTA: a tile of 128 samples (MMA M = 128), all T layers, persistent over
-// tiles.  The per-sample state is
+// Per CTA: a tile of up to 128 samples (MMA M = 128), all T layers, persistent
+// over tiles.  The per-sample state is
 //   g = c - B z   in tensor memory, as the FP32 accumulator of the MMA, and
 //   z             in registers (thread = one sample row, one half of the codes).
 // A layer is the epilogue
@@ -12,6 +12,9 @@
 // with a split into BF16 parts a = a_hi + a_lo and B = B_hi + B_lo:
 //   BF16   : a_hi B_hi
 //   BF16X3 : a_hi B_hi + a_lo B_hi + a_hi B_lo   (a_lo B_lo dropped)
+// Every REFRESH layers the same products rebuild g from scratch instead:
+// the accumulator is reloaded with c and the A operand is -z', so the MMAs
+// produce g = c - B z' (bounded rounding drift, same MMA count).
 // The epilogue writes a_hi / a_lo straight into tensor memory as the MMA's
 // A operand (tcgen05.st); B_hi (and B_lo for m <= 128) stay resident in
 // shared memory in the K-major 128-byte-swizzled layout; for m = 256 B_lo is
@@ -50,7 +53,34 @@ int read_and_clear_device_flag(cudaStream_t st)
 namespace tc {
 
 constexpr int NTHREADS = 256;   // warp w: TMEM lane quadrant (w & 3), code half (w >> 2)
+// Every REFRESH layers (at the checkpoint layers instead when checkpoints are
+// written) the accumulator is rebuilt as g = c - B z rather than updated by the
+// step, which bounds the drift the split products accumulate (about 2e-6
+// relative per layer, growing like t^0.8 without refreshes).
+constexpr int REFRESH = 8;
 constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
+
+// 16 consecutive entries of row `row` of C (columns col0..col0+15, zero
+// outside N x m), as four 16-byte loads when the rows are 16-byte aligned.
+__device__ __forceinline__ void load_c16(const float *__restrict__ C, int row, bool row_ok, int m, int col0,
+                                         uint32_t (&v)[16])
+{
+    if (row_ok && (m & 3) == 0) {
+        const float4 *src = reinterpret_cast<const float4 *>(C + (size_t)row * m + col0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 x = col0 + 4 * q < m ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[4 * q + 0] = __float_as_uint(x.x);
+            v[4 * q + 1] = __float_as_uint(x.y);
+            v[4 * q + 2] = __float_as_uint(x.z);
+            v[4 * q + 3] = __float_as_uint(x.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            v[j] = __float_as_uint((row_ok && col0 + j < m) ? __ldg(C + (size_t)row * m + col0 + j) : 0.0f);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -253,7 +283,7 @@ template <int MP, bool SPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_pgd_forward_kernel(
     const uint8_t *__restrict__ Bsplit, const float *__restrict__ C, int m, int N, float lam,
     const float *__restrict__ alpha, const double *__restrict__ Lp, int T, float *__restrict__ Z,
-    uint32_t *__restrict__ masks)
+    uint32_t *__restrict__ masks, float *__restrict__ ckpt, int K, int TR)
 {
     using CF = Cfg<MP, SPLIT>;
     extern __shared__ uint8_t smem_raw[];
@@ -268,7 +298,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pgd_forward_kernel(
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, half = warp >> 2;
-    const int ntiles = (N + 127) / 128;
+    const int ntiles = (N + TR - 1) / TR;  // TR <= 128 rows per tile (lanes >= TR idle)
     const int W = (m + 31) / 32;
     const uint8_t *gLo = Bsplit + CF::OPER;
 
@@ -319,21 +349,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pgd_forward_kernel(
 
 #pragma unroll 1
     for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-        const int row = tile * 128 + quad * 32 + lane;
-        const bool row_ok = row < N;
+        const int row = tile * TR + quad * 32 + lane;
+        const bool row_ok = (quad * 32 + lane < TR) && row < N;
         // g <- c, z <- 0
         float z[CF::HALF];
 #pragma unroll
         for (int ch = 0; ch < CF::NCH; ++ch) {
-            float v[32];
             const int col0 = half * CF::HALF + ch * 32;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int c = col0 + j;
-                v[j] = (row_ok && c < m) ? __ldg(C + (size_t)row * m + c) : 0.0f;
-                z[ch * 32 + j] = 0.0f;
+            for (int p = 0; p < 2; ++p) {
+                uint32_t v[16];
+                load_c16(C, row, row_ok, m, col0 + 16 * p, v);
+                tmem_st16(tmem + lane_base + CF::T_G + col0 + 16 * p, v);
             }
-            tmem_st32(tmem + lane_base + CF::T_G + col0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) z[ch * 32 + j] = 0.0f;
         }
         tmem_st_wait();
 
@@ -341,7 +371,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pgd_forward_kernel(
         for (int t = 0; t < T; ++t) {
             const float a = alpha ? __ldg(alpha + t) : a_const;
             const float thr = a * lam;
+            if (ckpt && t > 0 && t % K == 0) {
+                // checkpoint (z^(t), g^(t)) every K layers, layout of slista_forward
+                float *ck = ckpt + (size_t)(t / K - 1) * 2 * N * m;
+#pragma unroll
+                for (int ch = 0; ch < CF::NCH; ++ch) {
+                    const int col0 = half * CF::HALF + ch * 32;
+                    float gv[32];
+                    tmem_ld32(tmem + lane_base + CF::T_G + col0, gv);
+                    if (row_ok)
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (col0 + j < m) {
+                                ck[(size_t)row * m + col0 + j] = z[ch * 32 + j];
+                                ck[(size_t)N * m + (size_t)row * m + col0 + j] = gv[j];
+                            }
+                }
+            }
             // --- epilogue: z update and the split step a = z - z' into tensor memory
+            // (a = -z' on refresh layers, whose accumulator is reloaded with c)
+            const bool refresh = ckpt ? ((t + 1) % K == 0) : ((t + 1) % REFRESH == 0);
 #pragma unroll
             for (int ch = 0; ch < CF::NCH; ++ch) {
                 const int col0 = half * CF::HALF + ch * 32;
@@ -353,7 +402,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pgd_forward_kernel(
                     const float zo = z[ch * 32 + j];
                     const float u = fmaf(a, gv[j], zo);
                     const float zn = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
-                    gv[j] = zo - zn;  // the step a = z - z' (the MMA's A operand)
+                    gv[j] = refresh ? -zn : zo - zn;  // the MMA's A operand
                     z[ch * 32 + j] = zn;
                     word |= (uint32_t)(zn != 0.0f) << j;
                 }
@@ -375,6 +424,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_pgd_forward_kernel(
                     tmem_st16(tmem + lane_base + CF::T_ALO + col0 / 2, pk);
                 }
                 if (masks && row_ok && (col0 >> 5) < W) masks[((size_t)t * N + row) * W + (col0 >> 5)] = word;
+            }
+            if (refresh && t != T - 1) {
+#pragma unroll
+                for (int ch = 0; ch < CF::NCH; ++ch) {
+                    const int col0 = half * CF::HALF + ch * 32;
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        uint32_t cv[16];
+                        load_c16(C, row, row_ok, m, col0 + 16 * p, cv);
+                        tmem_st16(tmem + lane_base + CF::T_G + col0 + 16 * p, cv);
+                    }
+                }
             }
             tmem_st_wait();
             if (t == T - 1) break;
@@ -479,12 +540,19 @@ int launch_mp(const PgdArgs &a, void *ws, cudaStream_t st)
     split_b_kernel<<<ceil_div(MP * MP, 256), 256, 0, st>>>(a.B, a.m, MP, bsplit);
     int rc = check_launch("split_b_kernel");
     if (rc) return rc;
-    const int ntiles = ceil_div(a.N, 128);
-    if (ntiles == 0) return SLISTA_OK;
+    if (a.N == 0) return SLISTA_OK;
+    // A layer costs the same for a tile of 128 rows as for a partial one, so
+    // tiles are sized to keep every SM busy: rounds = tiles per SM with full
+    // tiles, then the rows are spread evenly over rounds x SMs tiles.
+    const int sms = num_sms();
+    const int rounds = ceil_div(ceil_div(a.N, 128), sms);
+    const int TR = ceil_div(a.N, (long long)rounds * sms);
+    const int ntiles = ceil_div(a.N, TR);
     auto k = tc_pgd_forward_kernel<MP, SPLIT>;
     SLISTA_CUDA_TRY(allow_smem(k, CF::SMEM));
-    const int grid = ntiles < num_sms() ? ntiles : num_sms();
-    k<<<grid, NTHREADS, CF::SMEM, st>>>(bsplit, a.C, a.m, a.N, a.lam, a.alpha, a.L, a.T, a.Z, a.masks);
+    const int grid = ntiles < sms ? ntiles : sms;
+    k<<<grid, NTHREADS, CF::SMEM, st>>>(bsplit, a.C, a.m, a.N, a.lam, a.alpha, a.L, a.T, a.Z, a.masks, a.ckpt,
+                                        a.ckpt_every, TR);
     return check_launch("tc_pgd_forward_kernel");
 }
 

@@ -158,3 +158,29 @@ def test_tc_full_size_sampled_rows(prec):
 def test_tc_device_flag_clear_after_runs():
     from paper_1905_11071_gb300 import _lib
     _lib.slista_device_status()
+
+
+@pytest.mark.parametrize("K", [1, 7, 40])
+def test_tc_forward_with_fp32_adjoint(K):
+    """Step-size sub-gradient when the forward (masks, checkpoints) runs on the
+    tensor cores (BF16X3) and the adjoint recomputes segments in FP32."""
+    w = synth.slista_64x256(N=300, T=40)
+    Lo = oracle.lipschitz(w.D)
+    alpha = synth.step_sizes(w.T, 1.0 / Lo, 0.3, seed=7)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    Z, st = A.slista(g.B, g.C, w.lam, dev(alpha), prec="bf16x3", keep_for_backward=True, ckpt_every=K)
+    dg = host(A.slista_grad(g.B, g.C, w.lam, dev(alpha), st)).astype(np.float64)
+    do, _ = oracle.slista_grad(w.D, w.X, w.lam, alpha)
+    assert np.linalg.norm(dg - do) <= 1e-4 * np.linalg.norm(do), (np.linalg.norm(dg - do) / np.linalg.norm(do))
+    # the tensor-core checkpoints hold z^(t) and g^(t) = c - B z^(t)
+    if st.ckpt is not None:
+        Zall = oracle.pgd(w.D, w.X, w.lam, alpha, keep_all=True)
+        Bo, Co, _ = oracle.gram(w.D, w.X)
+        ck = host(st.ckpt).reshape(-1, 2, w.N, w.m)
+        for s in range(ck.shape[0]):
+            t = (s + 1) * K
+            zt = TOL["bf16x3"]["Z"] * max(1.0, np.abs(Zall[t]).max())
+            assert np.abs(ck[s, 0] - Zall[t]).max() <= zt
+            g_or = Co - Zall[t] @ Bo
+            assert np.abs(ck[s, 1] - g_or).max() <= TOL["bf16x3"]["Z"] * max(1.0, np.abs(g_or).max())
