@@ -147,7 +147,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
 
     parts = ["gram", "slista_fwd", "objective", "slista_bwd", "oista_fwd"]
-    launches_per_step = {"gram": 3, "slista_fwd": 1, "objective": 1, "slista_bwd": 2, "oista_fwd": 1}
+    launches_per_step = {"gram": 3, "slista_fwd": 2, "objective": 1, "slista_bwd": 2, "oista_fwd": 1 + 2 * T}
 
     def step(evs=None):
         if evs is not None:
@@ -164,7 +164,7 @@ def run_ours(args, rank, world, local_rank):
         da = api.slista_grad(g.B, g.C, lam, alpha, st)
         if evs is not None:
             evs[4].record(stream)
-        Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T)
+        Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=D)
         if evs is not None:
             evs[5].record(stream)
         return Z, F, gap, da, Zo
@@ -228,7 +228,7 @@ def run_ours(args, rank, world, local_rank):
             Z, st = api.slista(g.B, g.C, lam, ad, prec=args.prec, keep_for_backward=True, ckpt_every=K)
             F, gap = api.objective(g.B, g.C, g.xsq, Z, lam)
             da = api.slista_grad(g.B, g.C, lam, ad, st)
-            Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T)
+            Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=Dd)
             Zh.copy_(Z, non_blocking=True)
             Fh.copy_(F, non_blocking=True)
             Gh.copy_(gap, non_blocking=True)

@@ -177,13 +177,18 @@ SLISTA_API int slista_backward(const float *B, const float *C, int m, int N, flo
  * L_S = largest eigenvalue of B_SS (Eq. spca; L_empty = L, recomputed only
  * when S changes), y = ST(z - (Bz - c)/L_S, lam/L_S); z^(t+1) = y when
  * supp(y) is inside S (condition (star)), else the ISTA step with 1/L.
- * L_S comes from a masked power iteration (FP32 products, FP64 Rayleigh
- * quotient).  Outputs: Z (N x m) = z^(T); LS (N, nullable) = the L_S used at
- * the last layer; accepted (T ints, nullable) = number of samples whose step
- * t met condition (star) (zeroed by the call).  Only SLISTA_PREC_FP32. */
-SLISTA_API int oista_forward(const float *B, const float *C, int m, int N, float lam, const double *L,
-                  int T, int prec, float *Z, double *LS, int *accepted,
-                  void *ws, size_t ws_bytes, void *stream);
+ * Condition (star) is decided before L_S (off S it reads |(c - Bz)_j| <= lam,
+ * independent of L_S), so L_S is computed only for accepted steps.  L_S comes
+ * from Lanczos in FP32 on B_SS, or, for |S| > 64 when D (n x m, nullable) is
+ * given, on D_S D_S^T (same non-zero spectrum, n <= 64); relative accuracy
+ * about 1e-6.  Outputs: Z (N x m) = z^(T); LS (N, nullable) = the L_S of
+ * supp(z^(T-1)), the support the last layer's candidate step used;
+ * accepted (T ints, nullable) = number of samples whose step t met condition
+ * (star) (zeroed by the call).  Workspace: the per-sample state of the layer
+ * loop (slista_workspace_bytes(SLISTA_FN_OISTA, ...)).  Only SLISTA_PREC_FP32. */
+SLISTA_API int oista_forward(const float *B, const float *C, const float *D, int n, int m, int N,
+                             float lam, const double *L, int T, int prec, float *Z, double *LS,
+                             int *accepted, void *ws, size_t ws_bytes, void *stream);
 
 /* Per-sample Lasso objective (Eq. lasso) evaluated from the Gram quantities,
  *     F_i = 1/2 xsq_i - c_i^T z_i + 1/2 z_i^T B z_i + lam ||z_i||_1,

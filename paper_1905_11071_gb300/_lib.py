@@ -80,7 +80,7 @@ def load(path: str = LIB_PATH):
         lib.slista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp, i, vp, sz, vp]
         lib.slista_backward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, i, vp, vp, vp, sz, vp]
         lib.slista_forward_noalloc.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp]
-        lib.oista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
+        lib.oista_forward.argtypes = [vp, vp, vp, i, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
         lib.lasso_objective.argtypes = [vp, vp, vp, vp, i, i, f, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("slista_last_error", "slista_workspace_bytes", "slista_ckpt_floats",
@@ -240,18 +240,20 @@ def slista_backward(B, C, lam, alpha, prec, masks, ckpt, ckpt_every, dalpha, gZ=
                                   _stream(stream)), "slista_backward")
 
 
-def oista_forward(B, C, lam, L, T, prec, Z, LS=None, accepted=None, ws=None, stream=None) -> None:
+def oista_forward(B, C, lam, L, T, prec, Z, LS=None, accepted=None, ws=None, D=None, stream=None) -> None:
     import torch
     m = B.shape[0]
     N = C.shape[0]
+    n = 0 if D is None else D.shape[0]
     _need(B, torch.float32, (m, m), "B")
+    _opt(D, torch.float32, (n, m), "D")
     _need(C, torch.float32, (N, m), "C")
     _need(L, torch.float64, (1,), "L")
     _need(Z, torch.float32, (N, m), "Z")
     _opt(LS, torch.float64, (N,), "LS")
     _opt(accepted, torch.int32, (T,), "accepted")
     wsb = 0 if ws is None else ws.numel() * ws.element_size()
-    _check(load().oista_forward(_ptr(B), _ptr(C), m, N, float(lam), _ptr(L), int(T), int(prec), _ptr(Z),
+    _check(load().oista_forward(_ptr(B), _ptr(C), _ptr(D), n, m, N, float(lam), _ptr(L), int(T), int(prec), _ptr(Z),
                                 _ptr(LS), _ptr(accepted), _ptr(ws), wsb, _stream(stream)), "oista_forward")
 
 

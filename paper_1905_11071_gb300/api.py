@@ -116,8 +116,9 @@ def slista_grad(B, C, lam, alpha, state: ForwardState, gZ=None, prec="fp32", str
     return dalpha
 
 
-def oista(B, C, lam, L, T, stream=None):
-    """Oracle-ISTA (Algorithm 1).  Returns (Z, LS, accepted)."""
+def oista(B, C, lam, L, T, D=None, stream=None):
+    """Oracle-ISTA (Algorithm 1).  Returns (Z, LS, accepted).  D (optional)
+    lets supports larger than 64 be solved on the n x n matrix D_S D_S^T."""
     N, m = C.shape
     dev = C.device
     Z = torch.empty((N, m), dtype=torch.float32, device=dev)
@@ -125,7 +126,7 @@ def oista(B, C, lam, L, T, stream=None):
     acc = torch.empty((max(T, 1),), dtype=torch.int32, device=dev)
     ws = workspace(_lib.slista_workspace_bytes(_lib.FN_OISTA, m, N, T, 0), dev, "oista")
     _lib.oista_forward(B, C, lam, L, T, _lib.PREC_FP32, Z, LS=LS, accepted=acc[:T] if T > 0 else None,
-                       ws=ws, stream=stream)
+                       ws=ws, D=D, stream=stream)
     return Z, LS, acc[:T]
 
 

@@ -123,7 +123,7 @@ size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_ev
         case SLISTA_FN_SLISTA_BWD:
             if (ckpt_every <= 0 || T <= 0) return 0;
             return simt::backward_ws_bytes(m, N, T, ckpt_every < T ? ckpt_every : T);
-        case SLISTA_FN_OISTA: return simt::oista_ws_bytes(m, N);
+        case SLISTA_FN_OISTA: return simt::padded_mp(m) ? simt::oista_ws_bytes(m, N, T) : 0;
         default: return 0;
     }
 }
@@ -223,21 +223,22 @@ int slista_backward(const float *B, const float *C, int m, int N, float lam, con
     return simt::launch_backward(a, ws, as_stream(stream));
 }
 
-int oista_forward(const float *B, const float *C, int m, int N, float lam, const double *L, int T, int prec,
-                  float *Z, double *LS, int *accepted, void *ws, size_t ws_bytes, void *stream)
+int oista_forward(const float *B, const float *C, const float *D, int n, int m, int N, float lam, const double *L,
+                  int T, int prec, float *Z, double *LS, int *accepted, void *ws, size_t ws_bytes, void *stream)
 {
     clear_error();
     SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 0, SLISTA_ERR_ARG, "oista_forward: bad sizes m=%d N=%d T=%d", m, N, T);
     SLISTA_REQUIRE(prec == SLISTA_PREC_FP32, SLISTA_ERR_UNSUPPORTED, "oista_forward: only SLISTA_PREC_FP32");
     SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "oista_forward: m <= 256 supported");
     SLISTA_REQUIRE(B && L, SLISTA_ERR_ARG, "oista_forward: B and L must not be NULL");
+    SLISTA_REQUIRE(!D || n >= 1, SLISTA_ERR_ARG, "oista_forward: n must be >= 1 when D is given");
     SLISTA_REQUIRE(N == 0 || (C && Z), SLISTA_ERR_ARG, "oista_forward: C and Z must not be NULL");
     int rc = check_lam(lam);
     if (rc) return rc;
-    const size_t need = simt::oista_ws_bytes(m, N);
+    const size_t need = simt::oista_ws_bytes(m, N, T);
     SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
                    "oista_forward: workspace of %zu bytes needed, %zu given", need, ws_bytes);
-    OistaArgs a{B, C, m, N, lam, L, T, Z, LS, accepted};
+    OistaArgs a{B, C, D, D ? n : 0, m, N, lam, L, T, Z, LS, accepted};
     return simt::launch_oista(a, ws, as_stream(stream));
 }
 

@@ -8,7 +8,7 @@
 // C and xsq come from the SIMT tile engine (the sample tile X_b in shared
 // memory, D streamed through it); B from a direct per-entry kernel whose
 // summation order makes B exactly symmetric; L from the smaller of D D^T and
-// D^T D by a single-CTA Householder / Sturm eigen-solver (eig.cuh).
+// D^T D by a single-CTA Lanczos / Sturm eigen-solver (eig.cuh).
 #include "common.cuh"
 #include "eig.cuh"
 #include "kernels.h"
@@ -69,13 +69,15 @@ __global__ void dtd_kernel(const float *__restrict__ D, int n, int m, float *__r
 
 // ---------------------------------------------------------------------------
 // Largest eigenvalue of a k x k symmetric PSD matrix K.  For k <= KL_SMEM the
-// matrix is staged in shared memory and solved by the block-wide Householder /
-// Sturm solver (eig.cuh).  Larger matrices fall back to power iteration on K in
+// matrix is formed in shared memory (from a shared copy of D when it fits) and
+// solved by one warp with Lanczos run to the full dimension (T_k is then
+// similar to K) and a Sturm multisection on T_k (eig.cuh).  Larger matrices fall back to power iteration on K in
 // global memory (FP32 products, FP64 Rayleigh quotients), which keeps the
 // largest quotient seen and stops after 400 iterations without progress.
 // ---------------------------------------------------------------------------
 constexpr int KL_SMEM = 128;
 constexpr int PI_NT = 256;
+constexpr int L_STAGE_FLOATS = 32768;  // D (n x m) staged in shared memory up to 128 KiB
 
 // mode 0: K = Kg (k x k, global);  mode 1: K = D D^T (k = n);  mode 2: K = D^T D (k = m).
 __global__ void __launch_bounds__(PI_NT) lipschitz_kernel(const float *__restrict__ Kg,
@@ -84,13 +86,23 @@ __global__ void __launch_bounds__(PI_NT) lipschitz_kernel(const float *__restric
 {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
-    __shared__ float redf[PI_NT / 32];
-    __shared__ int redi[PI_NT / 32];
     __shared__ double redd[3][PI_NT / 32];
     if (k <= KL_SMEM) {
         const int lda = eig::odd_ld(k);
         float *Ks = sm;
-        float *vec = Ks + k * lda;
+        float *vec = Ks + k * lda;            // q, qp (k each), al, be, e2 (JMAX each)
+        float *Ds = vec + 2 * k + 3 * eig::LANCZOS_JMAX;
+        const int ldd_s = m | 1;  // odd row stride: lanes reading different rows hit different banks
+        const bool stage = mode != 0 && (size_t)n * ldd_s <= (size_t)L_STAGE_FLOATS;
+        const float *Dsrc = D;
+        int ldd = m;
+        if (stage) {  // coalesced copy of D; the Gram entries then read shared memory
+            for (int e = threadIdx.x; e < n * m; e += PI_NT) Ds[(e / m) * ldd_s + e % m] = __ldg(D + e);
+            __syncthreads();
+            Dsrc = Ds;
+            ldd = ldd_s;
+        }
+        bool off = false;
         for (int e = threadIdx.x; e < k * k; e += PI_NT) {
             const int a = e / k, b = e % k;
             float s;
@@ -98,17 +110,28 @@ __global__ void __launch_bounds__(PI_NT) lipschitz_kernel(const float *__restric
                 s = __ldg(Kg + (size_t)a * k + b);
             } else if (mode == 1) {  // (D D^T)_ab = sum_j D_aj D_bj
                 s = 0.0f;
-                for (int j = 0; j < m; ++j) s = fmaf(__ldg(D + (size_t)a * m + j), __ldg(D + (size_t)b * m + j), s);
+                for (int j = 0; j < m; ++j) s = fmaf(Dsrc[(size_t)a * ldd + j], Dsrc[(size_t)b * ldd + j], s);
             } else {  // (D^T D)_ab = sum_i D_ia D_ib
                 s = 0.0f;
-                for (int i = 0; i < n; ++i) s = fmaf(__ldg(D + (size_t)i * m + a), __ldg(D + (size_t)i * m + b), s);
+                for (int i = 0; i < n; ++i) s = fmaf(Dsrc[(size_t)i * ldd + a], Dsrc[(size_t)i * ldd + b], s);
             }
             Ks[a * lda + b] = s;
+            off |= (a != b) && (s != 0.0f);
         }
-        __syncthreads();
-        const double v = eig::max_eig_sym<eig::CtaGroup<PI_NT>>(Ks, lda, k, vec, vec + k, vec + 2 * k,
-                                                                 vec + 3 * k, vec + 4 * k, redf, redi);
-        if (threadIdx.x == 0) *L = v;
+        if (!__syncthreads_or(off)) {  // diagonal (orthonormal D): the largest entry, exactly
+            if (threadIdx.x == 0) {
+                float v = Ks[0];
+                for (int a = 1; a < k; ++a) v = fmaxf(v, Ks[a * lda + a]);
+                *L = (double)v;
+            }
+            return;
+        }
+        if (threadIdx.x < 32) {
+            const double v = eig::lanczos_max_eig_warp<(KL_SMEM + 31) / 32>(
+                Ks, lda, k, vec, vec + k, vec + 2 * k, vec + 2 * k + eig::LANCZOS_JMAX,
+                vec + 2 * k + 2 * eig::LANCZOS_JMAX);
+            if (threadIdx.x == 0) *L = v;
+        }
         return;
     }
     // power iteration fallback (mode 0 only)
@@ -195,7 +218,10 @@ int launch_xd(const float *D, int n, int m, const float *X, int N, float *C, dou
 int launch_power(const float *Kg, const float *D, int n, int m, int mode, int k, double *L, cudaStream_t st)
 {
     const bool staged = k <= KL_SMEM;
-    const size_t smem = sizeof(float) * (staged ? (size_t)k * eig::odd_ld(k) + 5 * (size_t)k : (size_t)k);
+    const bool stage_d = mode != 0 && (size_t)n * (m | 1) <= (size_t)L_STAGE_FLOATS;
+    const size_t smem = sizeof(float) * (staged ? (size_t)k * eig::odd_ld(k) + 2 * (size_t)k +
+                                                      3 * (size_t)eig::LANCZOS_JMAX + (stage_d ? (size_t)n * (m | 1) : 0)
+                                                : (size_t)k);
     if (!staged && (k > 4 * PI_NT || mode != 0))
         return fail(SLISTA_ERR_UNSUPPORTED, "Lipschitz kernel supports k <= %d (got %d)", 4 * PI_NT, k);
     SLISTA_CUDA_TRY(allow_smem(lipschitz_kernel, smem));

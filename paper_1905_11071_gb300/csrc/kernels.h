@@ -45,7 +45,8 @@ struct ObjArgs {
 
 struct OistaArgs {
     const float *B, *C;
-    int m, N;
+    const float *D;      // nullable: n x m dictionary, for supports larger than 64
+    int n, m, N;
     float lam;
     const double *L;
     int T;
@@ -61,7 +62,7 @@ int launch_backward(const BwdArgs &a, void *ws, cudaStream_t st);
 size_t backward_ws_bytes(int m, int N, int T, int K);
 int launch_objective(const ObjArgs &a, cudaStream_t st);
 int launch_oista(const OistaArgs &a, void *ws, cudaStream_t st);
-size_t oista_ws_bytes(int m, int N);
+size_t oista_ws_bytes(int m, int N, int T);
 }  // namespace simt
 
 namespace gram {

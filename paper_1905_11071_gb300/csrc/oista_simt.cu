@@ -1,23 +1,30 @@
-// Oracle-ISTA (Algorithm 1, Section 3) on the CUDA cores.
+// Oracle-ISTA (Algorithm 1, Section 3).
 //
-// One CTA owns NB samples for all T layers (state z and g = c - B z in
-// registers, as in the forward kernel).  Per layer t, with S = supp(z^(t)):
-//
-//   (star)  The candidate y = ST(z + g / L_S, lam / L_S) has y_j = 0 for
-//           every j outside S iff |g_j| <= lam there (z_j = 0 off S, so both
-//           the argument and the threshold scale with 1 / L_S).  Condition
-//           (star) is therefore decided first, without L_S.
+// Per layer t, with S = supp(z^(t)):
+//   (star)  The candidate y = ST(z + g / L_S, lam / L_S) has y_j = 0 for every
+//           j outside S iff |g_j| <= lam there (z_j = 0 off S, so argument and
+//           threshold both scale with 1 / L_S): condition (star) is decided
+//           without L_S.
 //   L_S     Only samples whose step is accepted need L_S = lambda_max(B_SS)
-//           (Eq. spca); it is recomputed only when S differs from the support
-//           it was last computed for (L_empty = L, |S| = 1 gives B_jj).  One
-//           warp gathers B_SS into shared memory and runs Lanczos with a Sturm
-//           multisection on the Lanczos tridiagonal (eig.cuh); larger
-//           supports are gathered by the whole block into a shared buffer.
-//   step    z^(t+1) = ST(z + a g, a lam) with a = 1/L_S if (star) holds,
-//           else a = 1/L (the ISTA fallback of Algorithm 1);
-//   update  g <- g + (z^(t) - z^(t+1)) B, as in the forward kernel.
-// The result is Algorithm 1 exactly (up to rounding); only the order in
-// which L_S and (star) are evaluated differs from the listing.
+//           (Eq. spca), and only when S differs from the support it was last
+//           computed for (L_empty = L; |S| = 1 gives B_jj).
+//   step    z^(t+1) = ST(z + a g, a lam), a = 1/L_S if (star) holds, else 1/L
+//           (the ISTA fallback); then g <- g + (z^(t) - z^(t+1)) B.
+// The result is Algorithm 1 (up to rounding); only the order in which L_S and
+// (star) are evaluated differs from the listing.
+//
+// The layers run as two kernels each, with the per-sample state (z, g, the
+// support words, the cached L_S) in the workspace:
+//   oista_solve_kernel  every warp of the grid takes samples from the layer's
+//                       list of required L_S and computes them by Lanczos on
+//                       B_SS gathered into its shared buffer (|S| <= 64), or on
+//                       the n x n matrix D_S D_S^T (same non-zero spectrum) for
+//                       larger supports when D is given;
+//   oista_step_kernel   the layer for a tile of samples (FP32, the tile engine
+//                       of the forward kernel), fused with the next layer's
+//                       preparation: S, condition (star) and the list of
+//                       samples that need a new L_S.
+// Splitting the eigen-solves from the layer balances them over the whole GPU.
 #include "common.cuh"
 #include "eig.cuh"
 #include "kernels.h"
@@ -28,142 +35,78 @@ namespace simt {
 
 namespace {
 
-constexpr int KMAX = 64;  // largest |S| solved by one warp in its own buffer
-
+constexpr int KMAX = 64;  // largest matrix a warp solves in its own buffer
 constexpr int JM = eig::LANCZOS_JMAX;
+constexpr int SOLVE_WARPS = 8;
+constexpr int STEP_NB = 32;
 
-template <int MP>
+constexpr int GCOLS = 8;  // D_S columns staged per round in gram_ds
+
 struct WarpEig {
     static constexpr int LDA = eig::odd_ld(KMAX);
     float A[KMAX * LDA];
-    float q[KMAX], qp[KMAX], al[JM], be[JM], e2[JM];
-    int idx[MP];
+    float q[256], qp[256], al[JM], be[JM], e2[JM];
+    float col[GCOLS * KMAX];
+    int idx[256];
 };
 
-// Largest k whose k x odd_ld(k) matrix, three k-vectors, the Lanczos scratch
-// and MP indices fit in the eight warps' buffers together.
-template <int MP>
-__host__ __device__ constexpr int kbig()
-{
-    constexpr int words = (int)(sizeof(WarpEig<MP>) / 4) * (NT / 32);
-    int k = MP;
-    while (k > KMAX && k * eig::odd_ld(k) + 3 * k + 3 * JM + MP > words) --k;
-    return k;
-}
+// Per-sample state of the layer loop, carved out of the workspace.
+struct OistaWs {
+    double *LSv;              // N: cached L_S
+    float *Zs, *Gs;           // N x m each: z^(t), g^(t) = c - B z^(t)
+    uint32_t *Scur, *Sprev;   // N x W: supp(z^(t)), support of the cached L_S
+    int *flag;                // N: 1 if condition (star) fails at the current layer
+    int *valid;               // N: LSv holds L_{Sprev}
+    int *list;                // 2 x 2 x N: samples needing L_S, [layer parity][|S| > 64 ? 0 : 1]
+    int *counter;             // 2 x 2: list lengths, same indexing
+    int *qpos;                // T x 2: queue positions of the solve kernels
+    float *Dt;                // m x n: D transposed (columns of D contiguous), when D is given
+    int N, W;
 
-template <int MP, int NB>
-struct OistaSmem {
-    static constexpr int WP = MP / 32;
-    static constexpr size_t tile_bytes = sizeof(float) * (size_t)Tile<MP, NB>::SMEM_FLOATS;
-    static constexpr size_t eig_bytes = sizeof(WarpEig<MP>) * (NT / 32);
-    static constexpr size_t words_bytes = sizeof(uint32_t) * 2 * NB * WP;
-    static constexpr size_t misc_bytes = sizeof(double) * NB + sizeof(int) * (3 * NB + 8);
-    static constexpr size_t total = tile_bytes + eig_bytes + words_bytes + misc_bytes;
-    static_assert(total <= 227 * 1024, "OISTA shared memory exceeds the per-CTA limit");
+    static size_t bytes(int m, int N, int T)
+    {
+        const size_t W = (size_t)(m + 31) / 32;
+        return sizeof(double) * (size_t)N + 2 * sizeof(float) * (size_t)N * m + 2 * sizeof(uint32_t) * N * W +
+               sizeof(int) * (6 * (size_t)N + 4 + 2 * (size_t)T) + sizeof(float) * (size_t)m * 256 + 16;
+    }
+    static OistaWs carve(void *ws, int m, int N, int T)
+    {
+        const size_t W = (size_t)(m + 31) / 32;
+        char *p = reinterpret_cast<char *>(ws);
+        OistaWs o;
+        o.LSv = reinterpret_cast<double *>(p);
+        p += sizeof(double) * (size_t)N;
+        o.Zs = reinterpret_cast<float *>(p);
+        p += sizeof(float) * (size_t)N * m;
+        o.Gs = reinterpret_cast<float *>(p);
+        p += sizeof(float) * (size_t)N * m;
+        o.Scur = reinterpret_cast<uint32_t *>(p);
+        p += sizeof(uint32_t) * (size_t)N * W;
+        o.Sprev = reinterpret_cast<uint32_t *>(p);
+        p += sizeof(uint32_t) * (size_t)N * W;
+        o.flag = reinterpret_cast<int *>(p);
+        p += sizeof(int) * (size_t)N;
+        o.valid = reinterpret_cast<int *>(p);
+        p += sizeof(int) * (size_t)N;
+        o.list = reinterpret_cast<int *>(p);
+        p += sizeof(int) * 4 * (size_t)N;
+        o.counter = reinterpret_cast<int *>(p);
+        p += sizeof(int) * 4;
+        o.qpos = reinterpret_cast<int *>(p);
+        p += sizeof(int) * 2 * (size_t)T;
+        o.Dt = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
+        o.N = N;
+        o.W = (int)W;
+        return o;
+    }
 };
 
-// Gathers B_SS (k x k, indices idx) into A with leading dimension lda.
-// Returns whether B_SS has a non-zero off-diagonal entry (group-uniform).
-template <class G>
-__device__ bool gather_bss(const float *__restrict__ B, int m, const int *idx, int k, float *A, int lda)
-{
-    const int kk = k * k;
-    bool off = false;
-    int e = G::rank();
-    for (; e + 3 * G::size < kk; e += 4 * G::size) {
-        float x[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int q = e + u * G::size;
-            x[u] = __ldg(B + (size_t)idx[q / k] * m + idx[q % k]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int q = e + u * G::size;
-            const int a = q / k, b = q % k;
-            A[a * lda + b] = x[u];
-            off |= (a != b) && (x[u] != 0.0f);
-        }
-    }
-    for (; e < kk; e += G::size) {
-        const int a = e / k, b = e % k;
-        const float x = __ldg(B + (size_t)idx[a] * m + idx[b]);
-        A[a * lda + b] = x;
-        off |= (a != b) && (x != 0.0f);
-    }
-    G::sync();
-    return G::any(off);
-}
-
-// Largest diagonal entry of A (the largest eigenvalue when A is diagonal,
-// e.g. B_SS of an orthogonal D_S, where it is exact).
-__device__ inline float max_diag(const float *A, int lda, int k)
-{
-    float v = A[0];
-    for (int a = 1; a < k; ++a) v = fmaxf(v, A[a * lda + a]);
-    return v;
-}
-
-// Fallback for supports too large for shared memory: power iteration on B_SS
-// read from global memory, FP32 products and FP64 Rayleigh quotients; keeps
-// the largest quotient seen and stops after 400 iterations without progress.
-template <int MP>
-__device__ double power_iteration_global(const float *__restrict__ B, int m, const int *idx, int k, float *v)
-{
-    const int lane = threadIdx.x & 31;
-    for (int a = lane; a < k; a += 32) v[a] = eig::start_vector(a);
-    __syncwarp();
-    double best = 0.0;
-    int stall = 0;
-#pragma unroll 1
-    for (int it = 0; it < 20000 && stall < 400; ++it) {
-        float wl[MP / 32];
-        double vw = 0.0, ww = 0.0, vv = 0.0;
-#pragma unroll
-        for (int rr = 0; rr < MP / 32; ++rr) {
-            const int a = lane + 32 * rr;
-            float s = 0.0f;
-            if (a < k) {
-                const float *row = B + (size_t)idx[a] * m;
-                for (int b = 0; b < k; ++b) s = fmaf(__ldg(row + idx[b]), v[b], s);
-                const double va = (double)v[a];
-                vw += va * (double)s;
-                vv += va * va;
-                ww += (double)s * (double)s;
-            }
-            wl[rr] = s;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vw += __shfl_xor_sync(0xffffffffu, vw, o);
-            vv += __shfl_xor_sync(0xffffffffu, vv, o);
-            ww += __shfl_xor_sync(0xffffffffu, ww, o);
-        }
-        const double rq = vw / vv;
-        if (rq > best * (1.0 + 1e-9)) {
-            best = rq;
-            stall = 0;
-        } else {
-            ++stall;
-        }
-        const float inv = (float)(1.0 / sqrt(ww));
-        __syncwarp();
-#pragma unroll
-        for (int rr = 0; rr < MP / 32; ++rr) {
-            const int a = lane + 32 * rr;
-            if (a < k) v[a] = wl[rr] * inv;
-        }
-        __syncwarp();
-    }
-    return best;
-}
-
-// Index list of the support words of one row (by one warp); returns |S|.
-__device__ int support_indices(const uint32_t *words, int WP, int *idx)
+// Index list of a support given by its words (one warp); returns |S|.
+__device__ int support_indices(const uint32_t *words, int W, int *idx)
 {
     const int lane = threadIdx.x & 31;
     int k = 0;
-    for (int w = 0; w < WP; ++w) {
+    for (int w = 0; w < W; ++w) {
         const uint32_t bits = words[w];
         const bool has = (bits >> lane) & 1u;
         const uint32_t bal = __ballot_sync(0xffffffffu, has);
@@ -174,79 +117,193 @@ __device__ int support_indices(const uint32_t *words, int WP, int *idx)
     return k;
 }
 
-template <int MP, int NB>
-__global__ void __launch_bounds__(NT) oista_kernel(
-    const float *__restrict__ B, const float *__restrict__ C, int m, int N, float lam,
-    const double *__restrict__ Lp, int T, float *__restrict__ Z, double *__restrict__ LS_out,
-    int *__restrict__ accepted)
+// B_SS into A (leading dimension lda); returns whether an off-diagonal entry is non-zero.
+__device__ bool gather_bss(const float *__restrict__ B, int m, const int *idx, int k, float *A, int lda)
 {
-    using TL = Tile<MP, NB>;
-    using SM = OistaSmem<MP, NB>;
-    constexpr int WP = SM::WP;
-    constexpr int KBIG = kbig<MP>();
-    extern __shared__ float4 smem4[];
-    char *base = reinterpret_cast<char *>(smem4);
-    float *A_s = reinterpret_cast<float *>(base);
-    float *B_s = A_s + TL::A_FLOATS;
-    WarpEig<MP> *eigw = reinterpret_cast<WarpEig<MP> *>(base + SM::tile_bytes);
-    float *big = reinterpret_cast<float *>(eigw);  // all warps' buffers, for one large support
-    uint32_t *Scur = reinterpret_cast<uint32_t *>(base + SM::tile_bytes + SM::eig_bytes);
-    uint32_t *Sprev = Scur + NB * WP;
-    double *LSrow = reinterpret_cast<double *>(Sprev + NB * WP);
-    int *flag = reinterpret_cast<int *>(LSrow + NB);  // 1: condition (star) fails
-    int *valid = flag + NB;                           // LSrow[r] holds L_{Sprev[r]}
-    int *deferred = valid + NB;                       // rows whose support is too large for a warp
-    int *ctr = deferred + NB;                         // [0] queue, [1] accepted, [2] #deferred, [4] |S|
-    __shared__ float redf[NT / 32];
-    __shared__ int redi[NT / 32];
-
-    const Idx<TL> ix;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int row0 = blockIdx.x * NB;
-    const double L = __ldg(Lp);
-    const float aL = (float)(1.0 / L);
-
-    float g[TL::RM][TL::RN], z[TL::RM][TL::RN], d[TL::RM][TL::RN];
-    load_rows<TL>(g, C, row0, N, m, m);
+    const int lane = threadIdx.x & 31;
+    const int kk = k * k;
+    bool off = false;
+    for (int e0 = 0; e0 < kk; e0 += 32 * 8) {  // eight independent loads in flight per lane
+        float x[8];
 #pragma unroll
-    for (int i = 0; i < TL::RM; ++i)
-#pragma unroll
-        for (int j = 0; j < TL::RN; ++j) z[i][j] = 0.0f;
-    for (int r = threadIdx.x; r < NB; r += NT) {
-        valid[r] = 0;
-        flag[r] = 0;
-        LSrow[r] = L;
-    }
-    if (threadIdx.x < 8) ctr[threadIdx.x] = 0;
-    __syncthreads();
-
-#pragma unroll 1
-    for (int t = 0; t < T; ++t) {
-        const bool want_ls_out = (LS_out != nullptr) && (t == T - 1);
-        // 1. S = supp(z^(t)) and condition (star): |g_j| <= lam wherever z_j = 0
-        store_support_words<TL>(Scur, z, 0, NB, WP);
-#pragma unroll
-        for (int i = 0; i < TL::RM; ++i) {
-            bool bad = false;
-#pragma unroll
-            for (int j = 0; j < TL::RN; ++j) bad |= (z[i][j] == 0.0f) && (fabsf(g[i][j]) > lam);
-            if (bad) flag[ix.row(i)] = 1;
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 32 + lane;
+            x[u] = e < kk ? __ldg(B + (size_t)idx[e / k] * m + idx[e % k]) : 0.0f;
         }
-        __syncthreads();
-        // 2. L_S for accepted samples whose support changed (dynamic row queue)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * 32 + lane;
+            if (e < kk) {
+                const int a = e / k, b = e % k;
+                A[a * lda + b] = x[u];
+                off |= (a != b) && (x[u] != 0.0f);
+            }
+        }
+    }
+    __syncwarp();
+    return __any_sync(0xffffffffu, off);
+}
+
+// G = D_S D_S^T (n x n, n <= KMAX) into A, accumulated over the k support
+// columns; Dt is D transposed, so column j of D is the contiguous row j of Dt.
+__device__ void gram_ds(const float *__restrict__ Dt, int n, const int *idx, int k, float *A, int lda, float *col)
+{
+    const int lane = threadIdx.x & 31;
+    float acc[KMAX / 32][KMAX];  // rows lane and lane + 32 of G
+#pragma unroll
+    for (int r = 0; r < KMAX / 32; ++r)
+#pragma unroll
+        for (int b = 0; b < KMAX; ++b) acc[r][b] = 0.0f;
+#pragma unroll 1
+    for (int s0 = 0; s0 < k; s0 += GCOLS) {
+        float x[GCOLS][KMAX / 32];
+#pragma unroll
+        for (int c = 0; c < GCOLS; ++c)
+#pragma unroll
+            for (int r = 0; r < KMAX / 32; ++r) {
+                const int a = lane + 32 * r;
+                x[c][r] = (s0 + c < k && a < n) ? __ldg(Dt + (size_t)idx[s0 + c] * n + a) : 0.0f;
+            }
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < GCOLS; ++c)
+#pragma unroll
+            for (int r = 0; r < KMAX / 32; ++r) col[c * KMAX + lane + 32 * r] = x[c][r];
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < GCOLS; ++c) {
+#pragma unroll
+            for (int r = 0; r < KMAX / 32; ++r) {
+                const float da = col[c * KMAX + lane + 32 * r];
+#pragma unroll
+                for (int b = 0; b < KMAX; ++b) acc[r][b] = fmaf(da, col[c * KMAX + b], acc[r][b]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < KMAX / 32; ++r) {
+        const int a = lane + 32 * r;
+        if (a < n)
+#pragma unroll
+            for (int b = 0; b < KMAX; ++b)
+                if (b < n) A[a * lda + b] = acc[r][b];
+    }
+    __syncwarp();
+}
+
+// Lanczos with the matrix-vector products read from global memory, for the
+// rare supports too large for the shared buffer when D is not given.
+__device__ double lanczos_global(const float *__restrict__ B, int m, const int *idx, int k, WarpEig &we)
+{
+    const int lane = threadIdx.x & 31;
+    float *q = we.q, *qp = we.qp;
+    float nrm0 = 0.0f;
+    for (int a = lane; a < k; a += 32) nrm0 = fmaf(eig::start_vector(a), eig::start_vector(a), nrm0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm0 += __shfl_xor_sync(0xffffffffu, nrm0, o);
+    const float inv = rsqrtf(nrm0);
+    for (int a = lane; a < k; a += 32) {
+        q[a] = eig::start_vector(a) * inv;
+        qp[a] = 0.0f;
+    }
+    __syncwarp();
+    float beta_prev = 0.0f, theta_prev = -INFINITY;
+    int j = 0;
+    const int J = k < JM ? k : JM;
+#pragma unroll 1
+    for (; j < J; ++j) {
+        float w[8];  // k <= 256 rows over 32 lanes
+        float dot = 0.0f;
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const int a = lane + 32 * rr;
+            float s = 0.0f;
+            if (a < k) {
+                const float *row = B + (size_t)idx[a] * m;
+                for (int b = 0; b < k; ++b) s = fmaf(__ldg(row + idx[b]), q[b], s);
+                dot = fmaf(s, q[a], dot);
+            }
+            w[rr] = s;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        float nrm = 0.0f;
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const int a = lane + 32 * rr;
+            if (a < k) {
+                w[rr] = w[rr] - dot * q[a] - beta_prev * qp[a];
+                nrm = fmaf(w[rr], w[rr], nrm);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        const float beta = sqrtf(nrm);
+        if (lane == 0) {
+            we.al[j] = dot;
+            we.be[j] = beta;
+        }
+        __syncwarp();
+        if (beta <= 1e-6f * fabsf(dot)) {
+            ++j;
+            break;
+        }
+        if ((j + 1) % 16 == 0) {
+            const float theta = eig::tridiag_max_eig_warp(we.al, we.be, we.e2, j + 1);
+            if (theta - theta_prev <= 2e-7f * fabsf(theta)) {
+                ++j;
+                break;
+            }
+            theta_prev = theta;
+        }
+        const float ib = 1.0f / beta;
+        __syncwarp();
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            const int a = lane + 32 * rr;
+            if (a < k) {
+                qp[a] = q[a];
+                q[a] = w[rr] * ib;
+            }
+        }
+        __syncwarp();
+        beta_prev = beta;
+    }
+    return (double)eig::tridiag_max_eig_warp(we.al, we.be, we.e2, j);
+}
+
+__device__ inline float max_diag(const float *A, int lda, int k)
+{
+    float v = A[0];
+    for (int a = 1; a < k; ++a) v = fmaxf(v, A[a * lda + a]);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// L_S for the samples listed for layer t.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SOLVE_WARPS * 32) oista_solve_kernel(
+    const float *__restrict__ B, bool have_D, int n, int m, const double *__restrict__ Lp, OistaWs ws, int t)
+{
+    extern __shared__ float4 smem4[];
+    WarpEig &we = reinterpret_cast<WarpEig *>(smem4)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int par = t & 1;
+    if (blockIdx.x == 0 && threadIdx.x < 2) ws.counter[2 * (par ^ 1) + threadIdx.x] = 0;  // next layer's lists
+    const double L = __ldg(Lp);
+#pragma unroll 1
+    for (int cls = 0; cls < 2; ++cls) {  // large supports first: they set the kernel's tail
+        const int count = ws.counter[2 * par + cls];
+        const int *list = ws.list + (size_t)(2 * par + cls) * ws.N;
 #pragma unroll 1
         for (;;) {
-            int lr = 0;
-            if (lane == 0) lr = atomicAdd(&ctr[0], 1);
-            lr = __shfl_sync(0xffffffffu, lr, 0);
-            if (lr >= NB) break;
-            if (row0 + lr >= N) continue;
-            if (flag[lr] && !want_ls_out) continue;
-            bool changed = valid[lr] == 0;
-            for (int w = 0; w < WP; ++w) changed |= (Scur[lr * WP + w] != Sprev[lr * WP + w]);
-            if (!changed) continue;
-            WarpEig<MP> &we = eigw[warp];
-            const int k = support_indices(Scur + lr * WP, WP, we.idx);
+            int q = 0;
+            if (lane == 0) q = atomicAdd(ws.qpos + 2 * t + cls, 1);
+            q = __shfl_sync(0xffffffffu, q, 0);
+            if (q >= count) break;
+            const int i = list[q];
+            const uint32_t *words = ws.Scur + (size_t)i * ws.W;
+            const int k = support_indices(words, ws.W, we.idx);
             double LS;
             if (k == 0) {
                 LS = L;
@@ -254,115 +311,226 @@ __global__ void __launch_bounds__(NT) oista_kernel(
                 LS = (double)__ldg(B + (size_t)we.idx[0] * m + we.idx[0]);
             } else if (k <= KMAX) {
                 const int lda = eig::odd_ld(k);
-                if (gather_bss<eig::WarpGroup>(B, m, we.idx, k, we.A, lda))
-                    LS = eig::lanczos_max_eig_warp<(KMAX + 31) / 32>(we.A, lda, k, we.q, we.qp, we.al, we.be,
-                                                                     we.e2);
+                if (gather_bss(B, m, we.idx, k, we.A, lda))
+                    LS = eig::lanczos_max_eig_warp<KMAX / 32>(we.A, lda, k, we.q, we.qp, we.al, we.be, we.e2);
                 else
                     LS = (double)max_diag(we.A, lda, k);
+            } else if (have_D && n <= KMAX) {
+                const int lda = eig::odd_ld(n);
+                gram_ds(ws.Dt, n, we.idx, k, we.A, lda, we.col);
+                LS = eig::lanczos_max_eig_warp<KMAX / 32>(we.A, lda, n, we.q, we.qp, we.al, we.be, we.e2);
             } else {
-                if (lane == 0) deferred[atomicAdd(&ctr[2], 1)] = lr;
-                continue;
+                LS = lanczos_global(B, m, we.idx, k, we);
             }
             __syncwarp();
             if (lane == 0) {
-                LSrow[lr] = LS;
-                valid[lr] = 1;
+                ws.LSv[i] = LS;
+                ws.valid[i] = 1;
             }
-            for (int w = lane; w < WP; w += 32) Sprev[lr * WP + w] = Scur[lr * WP + w];
+            for (int w = lane; w < ws.W; w += 32) ws.Sprev[(size_t)i * ws.W + w] = words[w];
+            __syncwarp();
         }
-        __syncthreads();
-        // 3. large supports: the whole block on every warp's buffer, one at a time
-        const int ndef = ctr[2];
-#pragma unroll 1
-        for (int q = 0; q < ndef; ++q) {
-            const int lr = deferred[q];
-            int *idx = reinterpret_cast<int *>(big);
-            int *kp = ctr + 4;
-            if (warp == 0) {
-                const int k = support_indices(Scur + lr * WP, WP, idx);
-                if (lane == 0) *kp = k;
-            }
-            __syncthreads();
-            const int k = *kp;
-            double LS;
-            if (k <= KBIG) {
-                const int lda = eig::odd_ld(k);
-                float *A = big + MP;
-                float *vv = A + k * lda;
-                const bool off = gather_bss<eig::CtaGroup<NT>>(B, m, idx, k, A, lda);
-                LS = off ? eig::lanczos_max_eig_cta<NT>(A, lda, k, vv, vv + k, vv + 2 * k, vv + 3 * k,
-                                                        vv + 3 * k + JM, vv + 3 * k + 2 * JM, redf, redi)
-                         : (double)max_diag(A, lda, k);
-            } else {
-                LS = 0.0;
-                if (warp == 0) LS = power_iteration_global<MP>(B, m, idx, k, big + MP);
-            }
-            if (threadIdx.x == 0) {
-                LSrow[lr] = LS;
-                valid[lr] = 1;
-            }
-            for (int w = threadIdx.x; w < WP; w += NT) Sprev[lr * WP + w] = Scur[lr * WP + w];
-            __syncthreads();
-        }
-        // 4. the step: 1/L_S if (star) holds, else the ISTA step 1/L
-#pragma unroll
-        for (int i = 0; i < TL::RM; ++i) {
-            const bool ok = flag[ix.row(i)] == 0;
-            const float a = ok ? (float)(1.0 / LSrow[ix.row(i)]) : aL;
-            const float thr = a * lam;
-#pragma unroll
-            for (int j = 0; j < TL::RN; ++j) {
-                const float zn = soft_threshold(fmaf(a, g[i][j], z[i][j]), thr);
-                d[i][j] = z[i][j] - zn;
-                z[i][j] = zn;
-            }
-            if (ix.tx == 0 && row0 + ix.row(i) < N && ok) atomicAdd(&ctr[1], 1);
-        }
-        if (want_ls_out)
-            for (int r = threadIdx.x; r < NB; r += NT)
-                if (row0 + r < N) LS_out[row0 + r] = LSrow[r];
-        store_tile<TL>(A_s, d);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (accepted) atomicAdd(accepted + t, ctr[1]);
-            ctr[0] = ctr[1] = ctr[2] = 0;
-        }
-        for (int r = threadIdx.x; r < NB; r += NT) flag[r] = 0;
-        if (t == T - 1) break;
-        // 5. g <- g + (z^(t) - z^(t+1)) B  (gemm_acc starts with a barrier)
-        gemm_acc<TL>(g, A_s, TL::LDA, B, m, m, m, B_s);
     }
-    store_rows<TL>(Z, z, row0, N, m, m);
+}
+
+// Dt = D^T (m x n).
+__global__ void transpose_kernel(const float *__restrict__ D, int n, int m, float *__restrict__ Dt)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n * m) {
+        const int i = e / m, j = e % m;
+        Dt[(size_t)j * n + i] = __ldg(D + e);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shared preparation of layer t+1 for one tile: S, condition (star), the list.
+// ---------------------------------------------------------------------------
+template <class TL>
+__device__ void prepare_next(const float (&z)[TL::RM][TL::RN], const float (&g)[TL::RM][TL::RN], float lam,
+                             int row0, int N, OistaWs ws, int next, bool want_ls, uint32_t *Sw, int *rowflag)
+{
+    const Idx<TL> ix;
+    for (int r = threadIdx.x; r < TL::NB; r += NT) rowflag[r] = 0;
+    __syncthreads();
+    store_support_words<TL>(Sw, z, 0, TL::NB, ws.W);
+#pragma unroll
+    for (int i = 0; i < TL::RM; ++i) {
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < TL::RN; ++j) bad |= (z[i][j] == 0.0f) && (fabsf(g[i][j]) > lam);
+        if (bad) rowflag[ix.row(i)] = 1;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < TL::NB; r += NT) {
+        const int gr = row0 + r;
+        if (gr >= N) continue;
+        const int f = rowflag[r];
+        ws.flag[gr] = f;
+        bool changed = ws.valid[gr] == 0;
+        for (int w = 0; w < ws.W; ++w) {
+            const uint32_t s = Sw[r * ws.W + w];
+            ws.Scur[(size_t)gr * ws.W + w] = s;
+            changed |= s != ws.Sprev[(size_t)gr * ws.W + w];
+        }
+        if ((f == 0 || want_ls) && changed) {
+            int k = 0;
+            for (int w = 0; w < ws.W; ++w) k += __popc(Sw[r * ws.W + w]);
+            const int cls = (k > KMAX) ? 0 : 1;
+            const int li = 2 * (next & 1) + cls;
+            const int pos = atomicAdd(ws.counter + li, 1);
+            ws.list[(size_t)li * ws.N + pos] = gr;
+        }
+    }
 }
 
 template <int MP>
-int launch_oista_mp(const OistaArgs &a, cudaStream_t st)
+struct StepSmem {
+    using TL = Tile<MP, STEP_NB>;
+    static constexpr size_t bytes =
+        sizeof(float) * TL::SMEM_FLOATS + sizeof(uint32_t) * STEP_NB * (MP / 32) + sizeof(int) * (STEP_NB + 4);
+};
+
+// z^(0) = 0, g^(0) = c, S = empty (L_S = L), and condition (star) for layer 0.
+template <int MP>
+__global__ void __launch_bounds__(NT) oista_init_kernel(const float *__restrict__ C, int m, int N, float lam,
+                                                        const double *__restrict__ Lp, OistaWs ws, bool want_ls)
 {
-    constexpr int NB = 32;
-    const size_t smem = OistaSmem<MP, NB>::total;
-    auto k = oista_kernel<MP, NB>;
-    SLISTA_CUDA_TRY(allow_smem(k, smem));
+    using TL = Tile<MP, STEP_NB>;
+    extern __shared__ float4 smem4[];
+    float *A_s = reinterpret_cast<float *>(smem4);
+    uint32_t *Sw = reinterpret_cast<uint32_t *>(A_s + TL::SMEM_FLOATS);
+    int *rowflag = reinterpret_cast<int *>(Sw + STEP_NB * (MP / 32));
+    const int row0 = blockIdx.x * STEP_NB;
+    float g[TL::RM][TL::RN], z[TL::RM][TL::RN];
+    load_rows<TL>(g, C, row0, N, m, m);
+#pragma unroll
+    for (int i = 0; i < TL::RM; ++i)
+#pragma unroll
+        for (int j = 0; j < TL::RN; ++j) z[i][j] = 0.0f;
+    store_rows<TL>(ws.Gs, g, row0, N, m, m);
+    store_rows<TL>(ws.Zs, z, row0, N, m, m);
+    const double L = __ldg(Lp);
+    for (int r = threadIdx.x; r < STEP_NB; r += NT) {
+        const int gr = row0 + r;
+        if (gr >= N) continue;
+        ws.LSv[gr] = L;  // L_empty = L
+        ws.valid[gr] = 1;
+        for (int w = 0; w < ws.W; ++w) ws.Sprev[(size_t)gr * ws.W + w] = 0u;
+    }
+    __syncthreads();
+    prepare_next<TL>(z, g, lam, row0, N, ws, 0, want_ls, Sw, rowflag);
+}
+
+// Layer t for one tile, then the preparation of layer t+1.
+template <int MP>
+__global__ void __launch_bounds__(NT) oista_step_kernel(const float *__restrict__ B, int m, int N, float lam,
+                                                        const double *__restrict__ Lp, OistaWs ws, int t, int T,
+                                                        bool want_ls_next, float *__restrict__ Z,
+                                                        double *__restrict__ LS_out, int *__restrict__ accepted)
+{
+    using TL = Tile<MP, STEP_NB>;
+    extern __shared__ float4 smem4[];
+    float *A_s = reinterpret_cast<float *>(smem4);
+    float *B_s = A_s + TL::A_FLOATS;
+    uint32_t *Sw = reinterpret_cast<uint32_t *>(A_s + TL::SMEM_FLOATS);
+    int *rowflag = reinterpret_cast<int *>(Sw + STEP_NB * (MP / 32));
+    int *cnt = rowflag + STEP_NB;
+    const Idx<TL> ix;
+    const int row0 = blockIdx.x * STEP_NB;
+    if (threadIdx.x == 0) *cnt = 0;
+    float g[TL::RM][TL::RN], z[TL::RM][TL::RN], d[TL::RM][TL::RN];
+    load_rows<TL>(z, ws.Zs, row0, N, m, m);
+    load_rows<TL>(g, ws.Gs, row0, N, m, m);
+    const float aL = (float)(1.0 / __ldg(Lp));
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TL::RM; ++i) {
+        const int r = row0 + ix.row(i);
+        const bool live = r < N;
+        const bool ok = live && ws.flag[r] == 0;
+        const float a = ok ? (float)(1.0 / ws.LSv[r]) : aL;
+        const float thr = a * lam;
+#pragma unroll
+        for (int j = 0; j < TL::RN; ++j) {
+            const float zn = soft_threshold(fmaf(a, g[i][j], z[i][j]), thr);
+            d[i][j] = z[i][j] - zn;
+            z[i][j] = zn;
+        }
+        if (ix.tx == 0 && ok) atomicAdd(cnt, 1);
+    }
+    if (t == T - 1) {
+        store_rows<TL>(Z, z, row0, N, m, m);
+        if (LS_out)
+            for (int r = threadIdx.x; r < STEP_NB; r += NT)
+                if (row0 + r < N) LS_out[row0 + r] = ws.LSv[row0 + r];
+    } else {
+        store_tile<TL>(A_s, d);
+        gemm_acc<TL>(g, A_s, TL::LDA, B, m, m, m, B_s);  // g <- g + (z^(t) - z^(t+1)) B
+        store_rows<TL>(ws.Zs, z, row0, N, m, m);
+        store_rows<TL>(ws.Gs, g, row0, N, m, m);
+        prepare_next<TL>(z, g, lam, row0, N, ws, t + 1, want_ls_next, Sw, rowflag);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && accepted && *cnt) atomicAdd(accepted + t, *cnt);
+}
+
+template <int MP>
+int launch_oista_mp(const OistaArgs &a, void *wsp, cudaStream_t st)
+{
+    const OistaWs ws = OistaWs::carve(wsp, a.m, a.N, a.T);
     if (a.accepted && a.T > 0) SLISTA_CUDA_TRY(cudaMemsetAsync(a.accepted, 0, sizeof(int) * a.T, st));
-    const int grid = ceil_div(a.N, NB);
-    if (grid == 0) return SLISTA_OK;
-    k<<<grid, NT, smem, st>>>(a.B, a.C, a.m, a.N, a.lam, a.L, a.T, a.Z, a.LS, a.accepted);
-    return check_launch("oista_kernel");
+    if (a.N == 0) return SLISTA_OK;
+    if (a.T == 0) {
+        SLISTA_CUDA_TRY(cudaMemsetAsync(a.Z, 0, sizeof(float) * (size_t)a.N * a.m, st));
+        return SLISTA_OK;
+    }
+    SLISTA_CUDA_TRY(cudaMemsetAsync(ws.counter, 0, sizeof(int) * (4 + 2 * (size_t)a.T), st));  // counters, qpos
+    const bool have_D = a.D != nullptr && a.n >= 1 && a.n <= KMAX;
+    if (have_D) {
+        transpose_kernel<<<ceil_div((long long)a.n * a.m, 256), 256, 0, st>>>(a.D, a.n, a.m, ws.Dt);
+        int rc0 = check_launch("transpose_kernel");
+        if (rc0) return rc0;
+    }
+    const size_t step_smem = StepSmem<MP>::bytes;
+    const size_t solve_smem = sizeof(WarpEig) * SOLVE_WARPS;
+    auto kinit = oista_init_kernel<MP>;
+    auto kstep = oista_step_kernel<MP>;
+    SLISTA_CUDA_TRY(allow_smem(kinit, step_smem));
+    SLISTA_CUDA_TRY(allow_smem(kstep, step_smem));
+    SLISTA_CUDA_TRY(allow_smem(oista_solve_kernel, solve_smem));
+    const int grid = ceil_div(a.N, STEP_NB);
+    const bool want_ls = a.LS != nullptr;
+    kinit<<<grid, NT, step_smem, st>>>(a.C, a.m, a.N, a.lam, a.L, ws, want_ls && a.T == 1);
+    int rc = check_launch("oista_init_kernel");
+    if (rc) return rc;
+    const int solve_grid = num_sms();
+    for (int t = 0; t < a.T; ++t) {
+        oista_solve_kernel<<<solve_grid, SOLVE_WARPS * 32, solve_smem, st>>>(a.B, have_D, a.n, a.m, a.L, ws, t);
+        rc = check_launch("oista_solve_kernel");
+        if (rc) return rc;
+        kstep<<<grid, NT, step_smem, st>>>(a.B, a.m, a.N, a.lam, a.L, ws, t, a.T, want_ls && t + 2 == a.T, a.Z,
+                                           a.LS, a.accepted);
+        rc = check_launch("oista_step_kernel");
+        if (rc) return rc;
+    }
+    return SLISTA_OK;
 }
 
 }  // namespace
 
-int launch_oista(const OistaArgs &a, void *, cudaStream_t st)
+int launch_oista(const OistaArgs &a, void *ws, cudaStream_t st)
 {
     switch (padded_mp(a.m)) {
-        case 32: return launch_oista_mp<32>(a, st);
-        case 64: return launch_oista_mp<64>(a, st);
-        case 128: return launch_oista_mp<128>(a, st);
-        case 256: return launch_oista_mp<256>(a, st);
+        case 32: return launch_oista_mp<32>(a, ws, st);
+        case 64: return launch_oista_mp<64>(a, ws, st);
+        case 128: return launch_oista_mp<128>(a, ws, st);
+        case 256: return launch_oista_mp<256>(a, ws, st);
     }
     return fail(SLISTA_ERR_UNSUPPORTED, "OISTA kernel supports m <= 256 (got %d)", a.m);
 }
 
-size_t oista_ws_bytes(int, int) { return 0; }
+size_t oista_ws_bytes(int m, int N, int T) { return OistaWs::bytes(m, N, T) + 64; }
 
 }  // namespace simt
 }  // namespace slista

@@ -82,7 +82,9 @@ def test_argument_validation_without_gpu(lib):
     assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_BF16X3, vp, vp, 3, None, vp, vp, 1 << 30,
                                None) == _lib.SLISTA_ERR_UNSUPPORTED
     # OISTA and objective null pointers
-    assert lib.oista_forward(vp, vp, 8, 4, 0.1, None, 3, 0, vp, None, None, None, 0, None) == _lib.SLISTA_ERR_ARG
+    assert lib.oista_forward(vp, vp, None, 0, 8, 4, 0.1, None, 3, 0, vp, None, None, None, 0, None) == _lib.SLISTA_ERR_ARG
+    assert lib.oista_forward(vp, vp, vp, 4, 8, 4, 0.1, vp, 3, 0, vp, None, None, None, 0,
+                             None) == _lib.SLISTA_ERR_WORKSPACE
     assert lib.lasso_objective(vp, vp, None, vp, 8, 4, 0.1, vp, None, None) == _lib.SLISTA_ERR_ARG
     assert lib.lasso_lipschitz(vp, 0, vp, None) == _lib.SLISTA_ERR_ARG
     assert lib.ista_forward(vp, vp, 8, 4, 0.1, None, 3, 0, vp, None, 0, None) == _lib.SLISTA_ERR_ARG

@@ -215,11 +215,14 @@ def test_oista_parity_fig3_setup():
     assert np.abs(host(accg) - acco).max() <= (~safe).sum()
 
 
-def test_oista_parity_64x256():
+@pytest.mark.parametrize("with_D", [True, False])
+def test_oista_parity_64x256(with_D):
+    """Supports larger than 64 are solved on D_S D_S^T when D is given, else by
+    Lanczos with the products read from global memory."""
     w = synth.slista_64x256(N=48, T=40)
     A = api()
     g = A.gram(dev(w.D), dev(w.X))
-    Zg, LSg, accg = A.oista(g.B, g.C, w.lam, g.L, w.T)
+    Zg, LSg, accg = A.oista(g.B, g.C, w.lam, g.L, w.T, D=dev(w.D) if with_D else None)
     Lo = oracle.lipschitz(w.D)
     Zo, LSo, acco, deco, marg = oracle.oista(w.D, w.X, w.lam, Lo, w.T, with_margin=True)
     safe = marg > OISTA_MARGIN
