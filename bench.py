@@ -147,7 +147,15 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
 
     parts = ["gram", "slista_fwd", "objective", "slista_bwd", "oista_fwd"]
-    launches_per_step = {"gram": 3, "slista_fwd": 2, "objective": 1, "slista_bwd": 2, "oista_fwd": 1 + 2 * T}
+    tc = args.prec in ("bf16", "bf16x3")
+    nseg = -(-T // K)
+    launches_per_step = {
+        "gram": 3,                                            # D^T D, X D (+ ||x||^2), L
+        "slista_fwd": 2 if tc else 1,                         # (B split) + layer kernel
+        "objective": 1,
+        "slista_bwd": (1 + 2 * nseg + 1) if tc else 2,        # (B split) + recompute/adjoint per segment + reduce
+        "oista_fwd": 1 + 1 + 2 * T,                           # transpose D, init, solve + step per layer
+    }
 
     def step(evs=None):
         if evs is not None:
@@ -161,7 +169,7 @@ def run_ours(args, rank, world, local_rank):
         F, gap = api.objective(g.B, g.C, g.xsq, Z, lam)
         if evs is not None:
             evs[3].record(stream)
-        da = api.slista_grad(g.B, g.C, lam, alpha, st)
+        da = api.slista_grad(g.B, g.C, lam, alpha, st, prec=args.prec)
         if evs is not None:
             evs[4].record(stream)
         Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=D)
@@ -227,7 +235,7 @@ def run_ours(args, rank, world, local_rank):
             g = api.gram(Dd, Xd)
             Z, st = api.slista(g.B, g.C, lam, ad, prec=args.prec, keep_for_backward=True, ckpt_every=K)
             F, gap = api.objective(g.B, g.C, g.xsq, Z, lam)
-            da = api.slista_grad(g.B, g.C, lam, ad, st)
+            da = api.slista_grad(g.B, g.C, lam, ad, st, prec=args.prec)
             Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=Dd)
             Zh.copy_(Z, non_blocking=True)
             Fh.copy_(F, non_blocking=True)
@@ -262,32 +270,42 @@ def run_ours(args, rank, world, local_rank):
     pk, pk_kind = peaks()
     fp32_peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
     mm = float(m)
+    # Layer kernels on the tensor cores: the peak of their own arithmetic is
+    # the measured dense BF16 rate (burst: the kernels are timed one launch at
+    # a time), divided by 3 for the split product hi*hi + hi*lo + lo*hi.
+    if tc:
+        nprod = 3 if args.prec == "bf16x3" else 1
+        layer_peak = pk["bf16_tflops"] / nprod
+        layer_bound, layer_src = "tensor", "%s bf16_tflops (burst) / %d products" % (pk_kind, nprod)
+    else:
+        layer_peak = fp32_peak
+        layer_bound, layer_src = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
     algo = {
-        # useful B z products: 2 m^2 per sample per layer
-        "slista_fwd": ("alu", 2 * mm * mm * T * N / 1e12, "TFLOP/s", fp32_peak),
-        # adjoint: the forward product plus B h, 4 m^2 per sample per layer
-        "slista_bwd": ("alu", 4 * mm * mm * T * N / 1e12, "TFLOP/s", fp32_peak),
-        # Oracle-ISTA: the layer products only (power iterations not counted)
-        "oista_fwd": ("alu", 2 * mm * mm * T * N / 1e12, "TFLOP/s", fp32_peak),
+        # useful B z products: 2 m^2 per sample per layer (T - 1 contractions)
+        "slista_fwd": (layer_bound, 2 * mm * mm * (T - 1) * N / 1e12, "TFLOP/s", layer_peak, layer_src),
+        # adjoint: recompute (K - 1 contractions per segment, + 1 for g^(T)) and B h (T - 1)
+        "slista_bwd": (layer_bound, 2 * mm * mm * (2 * T - nseg) * N / 1e12, "TFLOP/s", layer_peak,
+                       layer_src),
+        # Oracle-ISTA: the layer products only (eigen-solves not counted), FP32 CUDA cores
+        "oista_fwd": ("alu", 2 * mm * mm * (T - 1) * N / 1e12, "TFLOP/s", fp32_peak,
+                      "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"),
         # Gram: read D, X, write B, C, xsq
-        "gram": ("hbm", (4.0 * (n * m + N * n + N * m + m * m) + 8.0 * N) / 1e9, "GB/s", pk["hbm_gbs"]),
+        "gram": ("hbm", (4.0 * (n * m + N * n + N * m + m * m) + 8.0 * N) / 1e9, "GB/s", pk["hbm_gbs"], pk_kind),
         # objective: read Z, C, xsq, B, write F, gap
-        "objective": ("hbm", (4.0 * (2 * N * m + m * m) + 24.0 * N) / 1e9, "GB/s", pk["hbm_gbs"]),
+        "objective": ("hbm", (4.0 * (2 * N * m + m * m) + 24.0 * N) / 1e9, "GB/s", pk["hbm_gbs"], pk_kind),
     }
     rooflines = {}
     for p in parts:
-        bound, amount, unit, peak = algo[p]
+        bound, amount, unit, peak, src = algo[p]
         secs = per_part[p] / 1e3
         ach = amount / secs if secs > 0 else 0.0
         rooflines[p] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                         "frac": ach / peak if peak else None, "ms": per_part[p],
-                        "share": per_part[p] / sum(per_part.values())}
+                        "share": per_part[p] / sum(per_part.values()), "peak_source": src}
     dom = max(parts, key=lambda p: per_part[p])
     r = rooflines[dom]
     roofline = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
-                "unit": r["unit"], "frac": r["frac"], "traffic": None,
-                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if r["bound"] == "alu"
-                                else pk_kind)}
+                "unit": r["unit"], "frac": r["frac"], "traffic": None, "peak_source": r["peak_source"]}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

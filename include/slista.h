@@ -98,15 +98,18 @@ SLISTA_API size_t slista_mask_words(int m, int N, int T);
 /* Gram quantities of the Lasso: B = D^T D (the matrix behind W_z = Id - D^T D / L,
  * Section 4), C = X D (the D^T x term of the gradient D^T(Dz - x), Eq. ista),
  * xsq_i = ||x_i||^2, and optionally L = largest eigenvalue of D^T D (Section 1,
- * after Eq. ista) by power iteration (FP32 products, FP64 Rayleigh quotient,
- * relative accuracy about 1e-7).
+ * after Eq. ista).  L is taken from the smaller of D^T D and D D^T when that
+ * side is <= 128 (Lanczos with full reorthogonalisation on FP32 products,
+ * then bisection on the tridiagonal matrix; relative accuracy about 1e-6),
+ * else by power iteration on B; a diagonal B gives its largest entry exactly.
  * D: n x m, X: N x n (inputs).  B: m x m, C: N x m, xsq: N, L: 1 (outputs;
  * L may be NULL to skip it).  n, m >= 1, N >= 0. */
 SLISTA_API int lasso_gram(const float *D, int n, int m, const float *X, int N,
                float *B, float *C, double *xsq, double *L, void *stream);
 
-/* L = largest eigenvalue of the symmetric PSD matrix B (m x m) by power
- * iteration (Section 1: L is the largest eigenvalue of D^T D). */
+/* L = largest eigenvalue of the symmetric PSD matrix B (m x m) (Section 1:
+ * L is the largest eigenvalue of D^T D), by the method of lasso_gram applied
+ * to B itself. */
 SLISTA_API int lasso_lipschitz(const float *B, int m, double *L, void *stream);
 
 /* ISTA, Eq. ista: T layers with the constant step 1/L from z^(0) = 0.
@@ -160,13 +163,21 @@ SLISTA_API int slista_forward_noalloc(const float *B, const float *C, int m, int
  *                        dalpha_t = sum_i <h_i, g_i^(t) - lam sign(z_i^(t+1))>;
  *                        G = h - alpha_t B h
  * where g^(t) = c - B z^(t).  Iterates between checkpoints are recomputed
- * from `ckpt` with the FP32 arithmetic of slista_forward, so masks, ckpt and
- * ckpt_every must come from a slista_forward call with the same B, C, lam,
- * alpha and T (any precision: after a tensor-core forward the recomputed
- * segments follow the FP32 trajectory from each checkpoint).
+ * from `ckpt`, so masks, ckpt and ckpt_every must come from a slista_forward
+ * call with the same B, C, lam, alpha and T.
+ * prec selects the arithmetic of the recompute and of B h:
+ *   SLISTA_PREC_FP32: CUDA cores, FP32.  After a tensor-core forward the
+ *     recomputed segments follow the FP32 trajectory from each checkpoint.
+ *   SLISTA_PREC_BF16 / SLISTA_PREC_BF16X3: tcgen05 tensor cores with the
+ *     products of slista_forward at that precision; with masks and ckpt from
+ *     a forward at the same precision the recompute reproduces the forward's
+ *     iterates bit for bit.  At most 256 layers between checkpoints
+ *     (min(ckpt_every, T) <= 256, else SLISTA_ERR_UNSUPPORTED).
  * gZ (nullable, N x m): upstream gradient dLoss/dz^(T).  dalpha (T, float32)
- * receives the sub-gradient.  prec selects the arithmetic of the adjoint;
- * only SLISTA_PREC_FP32 is built. */
+ * receives the sub-gradient; the per-layer sums are reduced in FP64 in a
+ * fixed order, so repeated calls give identical results.
+ * ws: at least slista_workspace_bytes(SLISTA_FN_SLISTA_BWD, m, N, T, prec,
+ * ckpt_every) bytes (else SLISTA_ERR_WORKSPACE). */
 SLISTA_API int slista_backward(const float *B, const float *C, int m, int N, float lam,
                     const float *alpha, int T, int prec,
                     const uint32_t *masks, const float *ckpt, int ckpt_every,

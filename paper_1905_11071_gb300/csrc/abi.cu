@@ -122,6 +122,8 @@ size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_ev
             return 0;
         case SLISTA_FN_SLISTA_BWD:
             if (ckpt_every <= 0 || T <= 0) return 0;
+            if (prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3)
+                return tc::backward_ws_bytes(m, N, T, ckpt_every < T ? ckpt_every : T);
             return simt::backward_ws_bytes(m, N, T, ckpt_every < T ? ckpt_every : T);
         case SLISTA_FN_OISTA: return simt::padded_mp(m) ? simt::oista_ws_bytes(m, N, T) : 0;
         default: return 0;
@@ -207,19 +209,24 @@ int slista_backward(const float *B, const float *C, int m, int N, float lam, con
     clear_error();
     SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 1, SLISTA_ERR_ARG, "slista_backward: bad sizes m=%d N=%d T=%d", m, N,
                    T);
-    SLISTA_REQUIRE(prec == SLISTA_PREC_FP32, SLISTA_ERR_UNSUPPORTED, "slista_backward: only SLISTA_PREC_FP32");
+    const bool tcp = prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3;
+    SLISTA_REQUIRE(prec == SLISTA_PREC_FP32 || tcp, prec == SLISTA_PREC_TF32 ? SLISTA_ERR_UNSUPPORTED : SLISTA_ERR_ARG,
+                   "slista_backward: precision %d not supported", prec);
     SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "slista_backward: m <= 256 supported");
     SLISTA_REQUIRE(B && alpha && dalpha, SLISTA_ERR_ARG, "slista_backward: B, alpha, dalpha must not be NULL");
     SLISTA_REQUIRE(ckpt_every >= 1, SLISTA_ERR_ARG, "slista_backward: ckpt_every must be >= 1");
     const int K = ckpt_every < T ? ckpt_every : T;
+    SLISTA_REQUIRE(!tcp || K <= 256, SLISTA_ERR_UNSUPPORTED,
+                   "slista_backward: tensor-core adjoint needs at most 256 layers between checkpoints (got %d)", K);
     SLISTA_REQUIRE(N == 0 || (C && masks), SLISTA_ERR_ARG, "slista_backward: C and masks must not be NULL");
     SLISTA_REQUIRE(N == 0 || K >= T || ckpt, SLISTA_ERR_ARG, "slista_backward: ckpt must not be NULL");
     int rc = check_lam(lam);
     if (rc) return rc;
-    const size_t need = simt::backward_ws_bytes(m, N, T, K);
+    const size_t need = tcp ? tc::backward_ws_bytes(m, N, T, K) : simt::backward_ws_bytes(m, N, T, K);
     SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
                    "slista_backward: workspace of %zu bytes needed, %zu given", need, ws_bytes);
     BwdArgs a{B, C, m, N, lam, alpha, T, masks, ckpt, K, gZ, dalpha};
+    if (tcp) return tc::launch_backward(a, prec, ws, as_stream(stream));
     return simt::launch_backward(a, ws, as_stream(stream));
 }
 

@@ -77,6 +77,9 @@ namespace tc {
 bool supported(int m);
 size_t forward_ws_bytes(int m);
 int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st);
+// tcgen05 adjoint (recompute of each segment + reverse sweep); K <= 256.
+size_t backward_ws_bytes(int m, int N, int T, int K);
+int launch_backward(const BwdArgs &a, int prec, void *ws, cudaStream_t st);
 int launch_forward_noalloc(const PgdArgs &a, int prec, cudaStream_t st);
 int noalloc_max_m();
 }  // namespace tc

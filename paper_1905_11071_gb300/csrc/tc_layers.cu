@@ -52,7 +52,6 @@ int read_and_clear_device_flag(cudaStream_t st)
 
 namespace tc {
 
-constexpr int NTHREADS = 256;   // warp w: TMEM lane quadrant (w & 3), code half (w >> 2)
 // Every REFRESH layers (at the checkpoint layers instead when checkpoints are
 // written) the accumulator is rebuilt as g = c - B z rather than updated by the
 // step, which bounds the drift the split products accumulate (about 2e-6
@@ -87,12 +86,12 @@ __device__ __forceinline__ void load_c16(const float *__restrict__ C, int row, b
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
@@ -100,14 +99,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.b32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
 }
 
 // Bounded wait for the completion of phase `parity`; false (and the device
 // flag raised) if it does not complete within WAIT_LIMIT_CYCLES.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int code)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int code)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
@@ -120,17 +119,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int co
     return true;
 }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
 {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
 
@@ -164,9 +161,9 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
         : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t *bar)
+__device__ __forceinline__ void mma_commit(uint32_t bar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
 
@@ -184,6 +181,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
           "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
         : "r"(taddr)
         : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (ld + wait in one asm).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
+          "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
@@ -257,269 +274,531 @@ __global__ void split_b_kernel(const float *__restrict__ B, int m, int MP, uint8
 }
 
 // ---------------------------------------------------------------------------
-// The layer kernel
+// Engine shared by the layer kernels: resident operands, tensor memory, the
+// contraction D (+)= A x B over all K with B_lo streamed when it does not
+// fit, and the bounded waits.
 // ---------------------------------------------------------------------------
 template <int MP, bool SPLIT>
 struct Cfg {
-    static constexpr int KB = MP / 16;                // MMA K-steps per layer
+    static constexpr int KB = MP / 16;                // MMA K-steps per contraction
     static constexpr int CHUNK = MP * 128;            // bytes of one 64-wide K chunk of an operand
     static constexpr int OPER = MP * MP * 2;          // bytes of one BF16 operand
     static constexpr bool LO_RES = SPLIT && MP <= 128;
     static constexpr bool LO_STREAM = SPLIT && MP > 128;
     static constexpr int SMEM_OPER = OPER + (LO_RES ? OPER : 0) + (LO_STREAM ? 2 * CHUNK : 0);
-    static constexpr int SMEM = SMEM_OPER + 1024 /*align*/ + 64 /*barriers*/;
+    static constexpr int SMEM = SMEM_OPER + 1024 /*align*/ + 64 /*barriers, tmem slot, B_lo address*/;
     static constexpr int T_G = 0, T_AHI = MP, T_ALO = MP + MP / 2;
     static constexpr int COLS_USED = SPLIT ? 2 * MP : MP + MP / 2;
     static constexpr int TMEM_COLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128
                                      : COLS_USED <= 256 ? 256 : 512;
-    static constexpr int HALF = MP / 2;               // code columns per thread
-    static constexpr int NCH = HALF / 32;             // 32-column chunks per thread
+    // Thread layout: warp w owns TMEM lanes 32*(w%4).. (tile rows) and the
+    // column group w/4 of NG groups of CW code columns, worked in 16-column
+    // pieces (NPC per thread).
+    static constexpr int NG = MP / 32 < 4 ? MP / 32 : 4;
+    static constexpr int NT = 128 * NG;               // threads per CTA
+    static constexpr int CW = MP / NG;                // code columns per thread (>= 32)
+    static constexpr int NPC = CW / 16;
     static constexpr uint32_t IDESC = idesc_bf16(128, MP);
     static_assert(MP % 64 == 0 && MP <= 256, "MP must be 64, 128 or 256");
     static_assert(COLS_USED <= 512, "tensor memory");
 };
 
+constexpr int ADJ_KMAX = 256;  // layers per recompute segment of the adjoint
+
 template <int MP, bool SPLIT>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_pgd_forward_kernel(
-    const uint8_t *__restrict__ Bsplit, const float *__restrict__ C, int m, int N, float lam,
-    const float *__restrict__ alpha, const double *__restrict__ Lp, int T, float *__restrict__ Z,
-    uint32_t *__restrict__ masks, float *__restrict__ ckpt, int K, int TR)
+struct TcEngine {
+    using CF = Cfg<MP, SPLIT>;
+    uint32_t tmem, lane_base, sB_u;  // sB_u: shared address of the operand area (1024-aligned)
+    // producer state, one bit each: phase of bar_mma (0), of bar_full[s]
+    // (1 + s) and bar_empty[s] (3 + s); a bulk copy into stage s not yet
+    // waited for (5 + s)
+    uint32_t bits;
+    bool failed;
+
+    __device__ __forceinline__ uint32_t bit(int i) const { return (bits >> i) & 1u; }
+    __device__ __forceinline__ void flip(int i) { bits ^= 1u << i; }
+    // global address of B_lo (read by thread 0 only; kept in shared memory)
+    __device__ __forceinline__ const uint8_t *lo_src() const
+    {
+        const uint8_t *g;
+        asm volatile("ld.shared.u64 %0, [%1];" : "=l"(g) : "r"(bar(6)));
+        return g;
+    }
+
+    __device__ __forceinline__ uint32_t sL_u() const { return sB_u + CF::OPER; }
+    __device__ __forceinline__ uint32_t bar(int i) const { return sB_u + CF::SMEM_OPER + 8 * i; }
+    __device__ __forceinline__ uint32_t bar_mma() const { return bar(0); }
+    __device__ __forceinline__ uint32_t bar_full(int s) const { return bar(1 + s); }
+    __device__ __forceinline__ uint32_t bar_empty(int s) const { return bar(3 + s); }
+
+    // Barriers, tensor memory, resident operands; prefetch of the streamed
+    // B_lo chunks 0 and 1 when `work` (the CTA has at least one tile).
+    __device__ __forceinline__ void init(uint8_t *smem_raw, const uint8_t *Bsplit, bool work)
+    {
+        uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+        uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + CF::SMEM_OPER + 5 * 8);
+        sB_u = smem_u32(smem);
+        const int tid = threadIdx.x;
+        if (tid == 0) {
+            for (int i = 0; i < 5; ++i) mbar_init(bar(i), 1);
+            fence_mbar_init();
+            const uint8_t *g = Bsplit + CF::OPER;
+            asm volatile("st.shared.u64 [%0], %1;" ::"r"(bar(6)), "l"(g) : "memory");
+        }
+        if ((tid >> 5) == 0) tmem_alloc(tmem_slot, CF::TMEM_COLS);
+        {
+            const uint4 *src = reinterpret_cast<const uint4 *>(Bsplit);
+            uint4 *dst = reinterpret_cast<uint4 *>(smem);
+            constexpr int n16 = (CF::OPER + (CF::LO_RES ? CF::OPER : 0)) / 16;
+            for (int i = tid; i < n16; i += CF::NT) dst[i] = __ldg(src + i);
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        tmem = *tmem_slot;
+        lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
+        bits = 0u;
+        failed = false;
+        if (CF::LO_STREAM && tid == 0 && work) {
+            load_stage(0, 0);
+            load_stage(1, 1);
+        }
+    }
+
+    __device__ __forceinline__ uint32_t taddr(int col) const { return tmem + lane_base + (uint32_t)col; }
+
+    __device__ __forceinline__ void load_stage(int s, int chunk)
+    {
+        mbar_arrive_expect_tx(bar_full(s), CF::CHUNK);
+        bulk_g2s(sL_u() + s * CF::CHUNK, lo_src() + chunk * CF::CHUNK, CF::CHUNK, bar_full(s));
+        bits |= 1u << (5 + s);
+    }
+
+    __device__ __forceinline__ void wait_stage(int s, int code)
+    {
+        failed |= !mbar_wait(bar_full(s), bit(1 + s), code);
+        flip(1 + s);
+        bits &= ~(1u << (5 + s));
+    }
+
+    // Every thread: publish the A operand written to tensor memory, then
+    // thread 0 issues D = [D +] A x B over all K (fresh: the first product
+    // overwrites D) and every thread waits for it.  Returns false, uniformly,
+    // if a bounded wait expired.
+    __device__ __forceinline__ bool contract(bool fresh)
+    {
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t dG = tmem + CF::T_G;
+            uint32_t acc = fresh ? 0u : 1u;
+            if (CF::LO_STREAM) {
+                // a_hi x B_lo on chunks 0 and 1 (prefetched)
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    wait_stage(s, 2);
+#pragma unroll
+                    for (int sub = 0; sub < 4; ++sub) {
+                        mma_ts(dG, tmem + CF::T_AHI + (s * 4 + sub) * 8, sdesc_sw128(sL_u() + s * CF::CHUNK + sub * 32),
+                               CF::IDESC, acc);
+                        acc = 1u;
+                    }
+                    mma_commit(bar_empty(s));
+                }
+            }
+#pragma unroll 1
+            for (int kb = 0; kb < CF::KB; ++kb) {
+                const uint64_t bd = sdesc_sw128(sB_u + (kb >> 2) * CF::CHUNK + (kb & 3) * 32);
+                mma_ts(dG, tmem + CF::T_AHI + kb * 8, bd, CF::IDESC, acc);
+                acc = 1u;
+                if (SPLIT) mma_ts(dG, tmem + CF::T_ALO + kb * 8, bd, CF::IDESC, 1u);
+                if (CF::LO_RES) {
+                    const uint64_t ld = sdesc_sw128(sL_u() + (kb >> 2) * CF::CHUNK + (kb & 3) * 32);
+                    mma_ts(dG, tmem + CF::T_AHI + kb * 8, ld, CF::IDESC, 1u);
+                }
+            }
+            if (CF::LO_STREAM) {
+                // refill both stages with chunks 2 and 3, then a_hi x B_lo on them
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    failed |= !mbar_wait(bar_empty(s), bit(3 + s), 3);
+                    flip(3 + s);
+                    load_stage(s, 2 + s);
+                }
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    wait_stage(s, 4);
+#pragma unroll
+                    for (int sub = 0; sub < 4; ++sub)
+                        mma_ts(dG, tmem + CF::T_AHI + ((2 + s) * 4 + sub) * 8,
+                               sdesc_sw128(sL_u() + s * CF::CHUNK + sub * 32), CF::IDESC, 1u);
+                }
+            }
+            mma_commit(bar_mma());
+        }
+        const bool ok = mbar_wait(bar_mma(), bit(0), 1);
+        flip(0);
+        tc_fence_after();
+        if (CF::LO_STREAM && threadIdx.x == 0 && ok && !failed) {
+            // every product is done: both stages are free, prefetch chunks 0 and 1
+            load_stage(0, 0);
+            load_stage(1, 1);
+        }
+        failed = __syncthreads_or(!ok || failed) != 0;
+        return !failed;
+    }
+
+    // Tensor memory of the tile is no longer read.
+    __device__ __forceinline__ void tile_done()
+    {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+
+    // Drain outstanding bulk copies, release tensor memory.
+    __device__ __forceinline__ void finish()
+    {
+        if (CF::LO_STREAM && threadIdx.x == 0)
+            for (int s = 0; s < 2; ++s)
+                if (bit(5 + s)) wait_stage(s, 5);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, CF::TMEM_COLS);
+    }
+};
+
+// Writes the BF16 split of v (16 values of this thread's row, code columns
+// col0..col0+15) as the A operand: 8 packed pairs per operand.
+template <int MP, bool SPLIT>
+__device__ __forceinline__ void store_split16(const TcEngine<MP, SPLIT> &E, int col0, const float (&v)[16])
+{
+    using CF = Cfg<MP, SPLIT>;
+    uint32_t pk[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
+    }
+    tmem_st8(E.taddr(CF::T_AHI + col0 / 2), pk);
+    if (SPLIT) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162 *>(&pk[j]);
+            const float2 hf = __bfloat1622float2(h2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+            pk[j] = *reinterpret_cast<const uint32_t *>(&l2);
+        }
+        tmem_st8(E.taddr(CF::T_ALO + col0 / 2), pk);
+    }
+}
+
+// Loads 16 consecutive columns (col0..) of row `row` of a row-major N x m
+// FP32 matrix into this thread's tensor-memory lane at column tcol.
+template <int MP, bool SPLIT>
+__device__ __forceinline__ void row16_to_tmem(const TcEngine<MP, SPLIT> &E, const float *__restrict__ G, int row,
+                                              bool row_ok, int m, int col0, int tcol)
+{
+    uint32_t v[16];
+    load_c16(G, row, row_ok, m, col0, v);
+    tmem_st16(E.taddr(tcol), v);
+}
+
+struct TcParams {
+    const uint8_t *Bsplit;
+    const float *C;
+    int m, N;
+    float lam;
+    const float *alpha;   // T steps, or nullptr: 1/L
+    const double *Lp;
+    int T;
+    float *Z;
+    uint32_t *masks;
+    float *ckpt;          // forward: written; recompute / adjoint: read (const)
+    int K;                // checkpoint spacing
+    int TR;               // rows per tile
+    // recompute and adjoint
+    int t0, t1;           // layer range [t0, t1)
+    float *qbuf;          // (t1 - t0) x N x m: g^(t) - lam sign(z^(t+1))
+    float *Gbuf;          // N x m: adjoint state G
+    const float *gZ;      // nullable upstream gradient
+    int want_gT;          // recompute: form G_T after the last layer
+    float *partial;       // T x gridDim.x per-CTA sums of dalpha
+};
+
+// ---------------------------------------------------------------------------
+// Forward (RECOMP = false): T layers from z = 0, g = c, writing Z, masks and
+// checkpoints.  Recompute (RECOMP = true): layers [t0, t1) from the
+// checkpoint at t0 with the forward's arithmetic, writing q_t per layer and,
+// for the last segment, G_T = gZ or dF/dz^(T) = -g^(T) + lam sign(z^(T)).
+// Thread (warp w, lane l): tile row 32*(w%4) + l, code columns
+// [CW*(w/4), CW*(w/4) + CW), z of those columns in registers.
+// ---------------------------------------------------------------------------
+template <int MP, bool SPLIT, bool RECOMP>
+__global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(const TcParams p)
 {
     using CF = Cfg<MP, SPLIT>;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sB = smem;                                 // B_hi (resident)
-    uint8_t *sL = smem + CF::OPER;                      // B_lo: resident, or two streamed chunks
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + CF::SMEM_OPER);
-    uint64_t *bar_mma = bars + 0;
-    uint64_t *bar_full = bars + 1;                      // [2]
-    uint64_t *bar_empty = bars + 3;                     // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 5);
-
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, half = warp >> 2;
+    const int quad = warp & 3, cbase = (warp >> 2) * CF::CW;
+    const int N = p.N, m = p.m, TR = p.TR;
     const int ntiles = (N + TR - 1) / TR;  // TR <= 128 rows per tile (lanes >= TR idle)
     const int W = (m + 31) / 32;
-    const uint8_t *gLo = Bsplit + CF::OPER;
-
-    // --- set-up: barriers, tensor memory, resident operands
-    if (tid == 0) {
-        mbar_init(bar_mma, 1);
-        mbar_init(bar_full + 0, 1);
-        mbar_init(bar_full + 1, 1);
-        mbar_init(bar_empty + 0, 1);
-        mbar_init(bar_empty + 1, 1);
-        fence_mbar_init();
-    }
-    if (warp == 0) tmem_alloc(tmem_slot, CF::TMEM_COLS);
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(Bsplit);
-        uint4 *dst = reinterpret_cast<uint4 *>(sB);
-        constexpr int n16 = (CF::OPER + (CF::LO_RES ? CF::OPER : 0)) / 16;
-        for (int i = tid; i < n16; i += NTHREADS) dst[i] = __ldg(src + i);
-    }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-
-    // producer state (thread 0)
-    uint32_t ph_full[2] = {0u, 0u}, ph_empty[2] = {0u, 0u}, ph_mma = 0u;
-    bool pending[2] = {false, false};  // a bulk copy into stage s has not been waited for
-    bool failed = false;
-    auto load_stage = [&](int s, int chunk) {
-        mbar_arrive_expect_tx(bar_full + s, CF::CHUNK);
-        bulk_g2s(sL + s * CF::CHUNK, gLo + chunk * CF::CHUNK, CF::CHUNK, bar_full + s);
-        pending[s] = true;
-    };
-    auto wait_stage = [&](int s, int code) {
-        failed |= !mbar_wait(bar_full + s, ph_full[s], code);
-        ph_full[s] ^= 1u;
-        pending[s] = false;
-    };
-    if (CF::LO_STREAM && tid == 0 && blockIdx.x < ntiles) {
-        load_stage(0, 0);
-        load_stage(1, 1);
-    }
-
-    const float a_const = alpha ? 0.0f : (float)(1.0 / __ldg(Lp));
-    const uint32_t sB_u = smem_u32(sB), sL_u = smem_u32(sL);
+    const float lam = p.lam;
+    const float *__restrict__ Cg = p.C;
+    const float *__restrict__ alpha = p.alpha;
+    float *__restrict__ ckpt = p.ckpt;
+    TcEngine<MP, SPLIT> E;
+    E.init(smem_raw, p.Bsplit, blockIdx.x < ntiles);
+    const float a_const = alpha ? 0.0f : (float)(1.0 / __ldg(p.Lp));
+    const int tb = RECOMP ? p.t0 : 0, te = RECOMP ? p.t1 : p.T;
 
 #pragma unroll 1
-    for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    for (int tile = blockIdx.x; tile < ntiles && !E.failed; tile += gridDim.x) {
         const int row = tile * TR + quad * 32 + lane;
         const bool row_ok = (quad * 32 + lane < TR) && row < N;
-        // g <- c, z <- 0
-        float z[CF::HALF];
+        float z[CF::CW];
+        if (!RECOMP || tb == 0) {  // g <- c, z <- 0
+#pragma unroll 1
+            for (int pc = 0; pc < CF::NPC; ++pc)
+                row16_to_tmem(E, Cg, row, row_ok, m, cbase + 16 * pc, CF::T_G + cbase + 16 * pc);
 #pragma unroll
-        for (int ch = 0; ch < CF::NCH; ++ch) {
-            const int col0 = half * CF::HALF + ch * 32;
+            for (int j = 0; j < CF::CW; ++j) z[j] = 0.0f;
+        } else {  // (z, g) from the checkpoint at layer tb
+            const float *ck = ckpt + (size_t)(tb / p.K - 1) * 2 * N * m;
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                uint32_t v[16];
-                load_c16(C, row, row_ok, m, col0 + 16 * p, v);
-                tmem_st16(tmem + lane_base + CF::T_G + col0 + 16 * p, v);
+            for (int pc = 0; pc < CF::NPC; ++pc) {
+                const int col0 = cbase + 16 * pc;
+                row16_to_tmem(E, ck + (size_t)N * m, row, row_ok, m, col0, CF::T_G + col0);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    z[16 * pc + j] = (row_ok && col0 + j < m) ? __ldg(ck + (size_t)row * m + col0 + j) : 0.0f;
             }
-#pragma unroll
-            for (int j = 0; j < 32; ++j) z[ch * 32 + j] = 0.0f;
         }
         tmem_st_wait();
 
 #pragma unroll 1
-        for (int t = 0; t < T; ++t) {
+        for (int t = tb; t < te; ++t) {
             const float a = alpha ? __ldg(alpha + t) : a_const;
             const float thr = a * lam;
-            if (ckpt && t > 0 && t % K == 0) {
-                // checkpoint (z^(t), g^(t)) every K layers, layout of slista_forward
-                float *ck = ckpt + (size_t)(t / K - 1) * 2 * N * m;
+            if constexpr (!RECOMP) {
+                if (ckpt && t > 0 && t % p.K == 0) {
+                    // checkpoint (z^(t), g^(t)) every K layers, layout of slista_forward
+                    float *ck = ckpt + (size_t)(t / p.K - 1) * 2 * N * m;
 #pragma unroll
-                for (int ch = 0; ch < CF::NCH; ++ch) {
-                    const int col0 = half * CF::HALF + ch * 32;
-                    float gv[32];
-                    tmem_ld32(tmem + lane_base + CF::T_G + col0, gv);
-                    if (row_ok)
+                    for (int pc = 0; pc < CF::NPC; ++pc) {
+                        const int col0 = cbase + 16 * pc;
+                        float gv[16];
+                        tmem_ld16(E.taddr(CF::T_G + col0), gv);
+                        if (row_ok)
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (col0 + j < m) {
-                                ck[(size_t)row * m + col0 + j] = z[ch * 32 + j];
-                                ck[(size_t)N * m + (size_t)row * m + col0 + j] = gv[j];
-                            }
+                            for (int j = 0; j < 16; ++j)
+                                if (col0 + j < m) {
+                                    ck[(size_t)row * m + col0 + j] = z[16 * pc + j];
+                                    ck[(size_t)N * m + (size_t)row * m + col0 + j] = gv[j];
+                                }
+                    }
                 }
             }
+            const bool last = (t == te - 1);
+            const bool contract_after = !last || (RECOMP && p.want_gT);
             // --- epilogue: z update and the split step a = z - z' into tensor memory
             // (a = -z' on refresh layers, whose accumulator is reloaded with c)
-            const bool refresh = ckpt ? ((t + 1) % K == 0) : ((t + 1) % REFRESH == 0);
+            const bool refresh = ckpt ? ((t + 1) % p.K == 0) : ((t + 1) % REFRESH == 0);
+            uint32_t word = 0u;
 #pragma unroll
-            for (int ch = 0; ch < CF::NCH; ++ch) {
-                const int col0 = half * CF::HALF + ch * 32;
-                float gv[32];
-                tmem_ld32(tmem + lane_base + CF::T_G + col0, gv);
-                uint32_t word = 0u;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float zo = z[ch * 32 + j];
-                    const float u = fmaf(a, gv[j], zo);
-                    const float zn = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
-                    gv[j] = refresh ? -zn : zo - zn;  // the MMA's A operand
-                    z[ch * 32 + j] = zn;
-                    word |= (uint32_t)(zn != 0.0f) << j;
-                }
-                uint32_t pk[16];
+            for (int pc = 0; pc < CF::NPC; ++pc) {
+                const int col0 = cbase + 16 * pc;
+                float gv[16];
+                tmem_ld16(E.taddr(CF::T_G + col0), gv);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(gv[2 * j], gv[2 * j + 1]);
-                    pk[j] = *reinterpret_cast<const uint32_t *>(&h2);
-                }
-                tmem_st16(tmem + lane_base + CF::T_AHI + col0 / 2, pk);
-                if (SPLIT) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162 *>(&pk[j]);
-                        const float2 hf = __bfloat1622float2(h2);
-                        const __nv_bfloat162 l2 = __floats2bfloat162_rn(gv[2 * j] - hf.x, gv[2 * j + 1] - hf.y);
-                        pk[j] = *reinterpret_cast<const uint32_t *>(&l2);
+                    const float zo = z[16 * pc + j];
+                    const float u = fmaf(a, gv[j], zo);
+                    const float zn = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
+                    if constexpr (RECOMP) {
+                        if (row_ok && col0 + j < m)
+                            p.qbuf[((size_t)(t - tb) * N + row) * m + col0 + j] =
+                                gv[j] - lam * (float)((zn > 0.0f) - (zn < 0.0f));
                     }
-                    tmem_st16(tmem + lane_base + CF::T_ALO + col0 / 2, pk);
+                    gv[j] = refresh ? -zn : zo - zn;  // the MMA's A operand
+                    z[16 * pc + j] = zn;
+                    word |= (uint32_t)(zn != 0.0f) << (16 * (pc & 1) + j);
                 }
-                if (masks && row_ok && (col0 >> 5) < W) masks[((size_t)t * N + row) * W + (col0 >> 5)] = word;
+                store_split16(E, col0, gv);
+                if constexpr (!RECOMP) {
+                    if ((pc & 1) && p.masks && row_ok && ((col0 - 16) >> 5) < W)
+                        p.masks[((size_t)t * N + row) * W + ((col0 - 16) >> 5)] = word;
+                }
+                if (pc & 1) word = 0u;
             }
-            if (refresh && t != T - 1) {
-#pragma unroll
-                for (int ch = 0; ch < CF::NCH; ++ch) {
-                    const int col0 = half * CF::HALF + ch * 32;
-#pragma unroll
-                    for (int p = 0; p < 2; ++p) {
-                        uint32_t cv[16];
-                        load_c16(C, row, row_ok, m, col0 + 16 * p, cv);
-                        tmem_st16(tmem + lane_base + CF::T_G + col0 + 16 * p, cv);
-                    }
-                }
+            if (refresh && contract_after) {
+#pragma unroll 1
+                for (int pc = 0; pc < CF::NPC; ++pc)
+                    row16_to_tmem(E, Cg, row, row_ok, m, cbase + 16 * pc, CF::T_G + cbase + 16 * pc);
             }
             tmem_st_wait();
-            if (t == T - 1) break;
-            tc_fence_before();
-            __syncthreads();
-            // --- contraction g += a B on the tensor cores (one thread issues)
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t dG = tmem + CF::T_G;
-                if (CF::LO_STREAM) {
-                    // a_hi x B_lo, chunks 0 and 1 (prefetched)
+            if (!contract_after) break;
+            // --- contraction g += a B on the tensor cores
+            if (!E.contract(false)) break;
+            if constexpr (RECOMP) {
+                if (last) {
+                    // G_T = gZ, or dF/dz^(T) = B z - c + lam sign(z) = -g + lam sign(z)
 #pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        wait_stage(s, 2);
+                    for (int pc = 0; pc < CF::NPC; ++pc) {
+                        const int col0 = cbase + 16 * pc;
+                        float gv[16];
+                        tmem_ld16(E.taddr(CF::T_G + col0), gv);
+                        if (row_ok)
 #pragma unroll
-                        for (int sub = 0; sub < 4; ++sub)
-                            mma_ts(dG, tmem + CF::T_AHI + (s * 4 + sub) * 8, sdesc_sw128(sL_u + s * CF::CHUNK + sub * 32),
-                                   CF::IDESC, 1u);
-                        mma_commit(bar_empty + s);
+                            for (int j = 0; j < 16; ++j)
+                                if (col0 + j < m) {
+                                    const size_t o = (size_t)row * m + col0 + j;
+                                    const float zj = z[16 * pc + j];
+                                    p.Gbuf[o] = p.gZ ? __ldg(p.gZ + o)
+                                                     : -gv[j] + lam * (float)((zj > 0.0f) - (zj < 0.0f));
+                                }
                     }
                 }
-#pragma unroll 1
-                for (int kb = 0; kb < CF::KB; ++kb) {
-                    const uint64_t bd = sdesc_sw128(sB_u + (kb >> 2) * CF::CHUNK + (kb & 3) * 32);
-                    mma_ts(dG, tmem + CF::T_AHI + kb * 8, bd, CF::IDESC, 1u);
-                    if (SPLIT) mma_ts(dG, tmem + CF::T_ALO + kb * 8, bd, CF::IDESC, 1u);
-                    if (CF::LO_RES) {
-                        const uint64_t ld = sdesc_sw128(sL_u + (kb >> 2) * CF::CHUNK + (kb & 3) * 32);
-                        mma_ts(dG, tmem + CF::T_AHI + kb * 8, ld, CF::IDESC, 1u);
-                    }
-                }
-                if (CF::LO_STREAM) {
-                    // refill the two stages with chunks 2 and 3, then a_hi x B_lo on them
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        failed |= !mbar_wait(bar_empty + s, ph_empty[s], 3);
-                        ph_empty[s] ^= 1u;
-                        load_stage(s, 2 + s);
-                    }
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        wait_stage(s, 4);
-#pragma unroll
-                        for (int sub = 0; sub < 4; ++sub)
-                            mma_ts(dG, tmem + CF::T_AHI + ((2 + s) * 4 + sub) * 8,
-                                   sdesc_sw128(sL_u + s * CF::CHUNK + sub * 32), CF::IDESC, 1u);
-                    }
-                }
-                mma_commit(bar_mma);
             }
-            // --- wait for the contraction (every thread, bounded)
-            bool ok = mbar_wait(bar_mma, ph_mma, 1);
-            ph_mma ^= 1u;
-            tc_fence_after();
-            if (CF::LO_STREAM && tid == 0 && ok && !failed) {
-                // all MMAs done: both stages are free, prefetch chunks 0 and 1 for the next layer
-                load_stage(0, 0);
-                load_stage(1, 1);
-            }
-            failed = __syncthreads_or(!ok || failed) != 0;
-            if (failed) break;
         }
-        if (failed) break;
-        // z^(T) out
-#pragma unroll
-        for (int ch = 0; ch < CF::NCH; ++ch) {
-            const int col0 = half * CF::HALF + ch * 32;
+        if (E.failed) break;
+        if constexpr (!RECOMP) {
             if (row_ok)
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (col0 + j < m) Z[(size_t)row * m + col0 + j] = z[ch * 32 + j];
+                for (int j = 0; j < CF::CW; ++j)
+                    if (cbase + j < m) p.Z[(size_t)row * m + cbase + j] = z[j];
         }
-        tc_fence_before();
-        __syncthreads();  // tensor memory of this tile is no longer read
-        tc_fence_after();
+        E.tile_done();
     }
-    // drain outstanding bulk copies before the shared memory goes away
-    if (CF::LO_STREAM && tid == 0)
-        for (int s = 0; s < 2; ++s)
-            if (pending[s]) wait_stage(s, 5);
-    tc_fence_before();
+    E.finish();
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of Eq. steprec over the layers [t0, t1), walked backwards, for the
+// state G in Gbuf (updated in place):
+//   h = G * mask_t;  dalpha_t += <h, q_t>;  G = h - alpha_t B h
+// with B h on the tensor cores (split products into a fresh accumulator).
+// Per-CTA sums of dalpha_t go to partial[t * gridDim.x + block].
+// ---------------------------------------------------------------------------
+template <int MP, bool SPLIT>
+__global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const TcParams p)
+{
+    using CF = Cfg<MP, SPLIT>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ float part_s[ADJ_KMAX];
+    __shared__ float red[CF::NT / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, cbase = (warp >> 2) * CF::CW;
+    const int N = p.N, m = p.m, TR = p.TR;
+    const int ntiles = (N + TR - 1) / TR;
+    const int W = (m + 31) / 32;
+    const float *__restrict__ alpha = p.alpha;
+    const uint32_t *__restrict__ masks = p.masks;
+    const float *__restrict__ qbuf = p.qbuf;
+    float *__restrict__ Gbuf = p.Gbuf;
+    TcEngine<MP, SPLIT> E;
+    E.init(smem_raw, p.Bsplit, blockIdx.x < ntiles);
+    for (int i = tid; i < ADJ_KMAX; i += CF::NT) part_s[i] = 0.0f;
     __syncthreads();
-    tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, CF::TMEM_COLS);
+
+#pragma unroll 1
+    for (int tile = blockIdx.x; tile < ntiles && !E.failed; tile += gridDim.x) {
+        const int row = tile * TR + quad * 32 + lane;
+        const bool row_ok = (quad * 32 + lane < TR) && row < N;
+        float G[CF::CW];
+#pragma unroll
+        for (int j = 0; j < CF::CW; ++j) G[j] = (row_ok && cbase + j < m) ? Gbuf[(size_t)row * m + cbase + j] : 0.0f;
+#pragma unroll 1
+        for (int t = p.t1 - 1; t >= p.t0; --t) {
+            const float a = __ldg(alpha + t);
+            const float *qrow = qbuf + ((size_t)(t - p.t0) * N + row) * m;
+            float part = 0.0f;
+#pragma unroll
+            for (int pc = 0; pc < CF::NPC; ++pc) {
+                const int col0 = cbase + 16 * pc;
+                if ((pc & 1) == 0) {
+                    // mask bits of code columns col0 .. col0+31 (zero past m)
+                    const uint32_t valid = col0 + 32 <= m ? 0xffffffffu : col0 < m ? (1u << (m - col0)) - 1u : 0u;
+                    const uint32_t word =
+                        (row_ok && valid) ? __ldg(masks + ((size_t)t * N + row) * W + (col0 >> 5)) & valid : 0u;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) G[16 * pc + j] = ((word >> j) & 1u) ? G[16 * pc + j] : 0.0f;  // h
+                    if (row_ok) {
+                        // <h, q_t> over these 32 columns (h = 0 off the support and past m)
+                        if ((m & 3) == 0) {
+                            const float4 *q4 = reinterpret_cast<const float4 *>(qrow + col0);
+#pragma unroll
+                            for (int v = 0; v < 8; ++v)
+                                if (col0 + 4 * v < m) {
+                                    const float4 q = __ldg(q4 + v);
+                                    part = fmaf(G[16 * pc + 4 * v + 0], q.x, part);
+                                    part = fmaf(G[16 * pc + 4 * v + 1], q.y, part);
+                                    part = fmaf(G[16 * pc + 4 * v + 2], q.z, part);
+                                    part = fmaf(G[16 * pc + 4 * v + 3], q.w, part);
+                                }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if ((word >> j) & 1u) part = fmaf(G[16 * pc + j], __ldg(qrow + col0 + j), part);
+                        }
+                    }
+                }
+                float hv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) hv[j] = G[16 * pc + j];
+                store_split16(E, col0, hv);
+            }
+            tmem_st_wait();
+            // dalpha_t partial: block sum
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) red[warp] = part;
+            __syncthreads();
+            if (tid == 0) {
+                float sum = 0.0f;
+#pragma unroll
+                for (int w = 0; w < CF::NT / 32; ++w) sum += red[w];
+                part_s[t - p.t0] += sum;
+            }
+            if (t == 0) break;  // G^(0) is not needed
+            // --- B h on the tensor cores, then G = h - alpha_t B h
+            if (!E.contract(true)) break;
+#pragma unroll
+            for (int pc = 0; pc < CF::NPC; ++pc) {
+                float bh[16];
+                tmem_ld16(E.taddr(CF::T_G + cbase + 16 * pc), bh);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) G[16 * pc + j] = fmaf(-a, bh[j], G[16 * pc + j]);
+            }
+        }
+        if (E.failed) break;
+        if (p.t0 > 0 && row_ok) {
+#pragma unroll
+            for (int j = 0; j < CF::CW; ++j)
+                if (cbase + j < m) Gbuf[(size_t)row * m + cbase + j] = G[j];
+        }
+        E.tile_done();
+    }
+    __syncthreads();
+    for (int t = p.t0 + tid; t < p.t1; t += CF::NT) p.partial[(size_t)t * gridDim.x + blockIdx.x] = part_s[t - p.t0];
+    E.finish();
+}
+
+// dalpha[t] = sum over blocks of partial[t][b], in FP64, fixed order.
+__global__ void tc_reduce_partials_kernel(const float *__restrict__ partial, int nblk, int T, float *__restrict__ dalpha)
+{
+    const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (t >= T) return;
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += (double)partial[(size_t)t * nblk + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) dalpha[t] = (float)s;
 }
 
 namespace {
@@ -532,28 +811,120 @@ int mp_for(int m)
     return 0;
 }
 
+// Tiles sized to keep every SM busy: a layer costs the same for a partial
+// tile as for 128 rows, so rows are spread evenly over rounds x SMs tiles.
+void tiling(int N, int *TR, int *grid)
+{
+    const int sms = num_sms();
+    const int rounds = ceil_div(ceil_div(N, 128), sms);
+    *TR = N > 0 ? ceil_div(N, (long long)rounds * sms) : 128;
+    const int ntiles = N > 0 ? ceil_div(N, *TR) : 0;
+    *grid = ntiles < sms ? ntiles : sms;
+}
+
+template <int MP, bool SPLIT>
+int split_b(const float *B, int m, uint8_t *bsplit, cudaStream_t st)
+{
+    split_b_kernel<<<ceil_div(MP * MP, 256), 256, 0, st>>>(B, m, MP, bsplit);
+    return check_launch("split_b_kernel");
+}
+
 template <int MP, bool SPLIT>
 int launch_mp(const PgdArgs &a, void *ws, cudaStream_t st)
 {
     using CF = Cfg<MP, SPLIT>;
     uint8_t *bsplit = reinterpret_cast<uint8_t *>(ws);
-    split_b_kernel<<<ceil_div(MP * MP, 256), 256, 0, st>>>(a.B, a.m, MP, bsplit);
-    int rc = check_launch("split_b_kernel");
+    int rc = split_b<MP, SPLIT>(a.B, a.m, bsplit, st);
     if (rc) return rc;
     if (a.N == 0) return SLISTA_OK;
-    // A layer costs the same for a tile of 128 rows as for a partial one, so
-    // tiles are sized to keep every SM busy: rounds = tiles per SM with full
-    // tiles, then the rows are spread evenly over rounds x SMs tiles.
-    const int sms = num_sms();
-    const int rounds = ceil_div(ceil_div(a.N, 128), sms);
-    const int TR = ceil_div(a.N, (long long)rounds * sms);
-    const int ntiles = ceil_div(a.N, TR);
-    auto k = tc_pgd_forward_kernel<MP, SPLIT>;
+    TcParams p{};
+    p.Bsplit = bsplit;
+    p.C = a.C;
+    p.m = a.m;
+    p.N = a.N;
+    p.lam = a.lam;
+    p.alpha = a.alpha;
+    p.Lp = a.L;
+    p.T = a.T;
+    p.Z = a.Z;
+    p.masks = a.masks;
+    // A checkpoint buffer is only written when ckpt_every < T; the layers
+    // then refresh the accumulator at every checkpoint, else every REFRESH.
+    p.ckpt = a.ckpt_every < a.T ? a.ckpt : nullptr;
+    p.K = a.ckpt_every;
+    int grid = 0;
+    tiling(a.N, &p.TR, &grid);
+    auto k = tc_pgd_forward_kernel<MP, SPLIT, false>;
     SLISTA_CUDA_TRY(allow_smem(k, CF::SMEM));
-    const int grid = ntiles < sms ? ntiles : sms;
-    k<<<grid, NTHREADS, CF::SMEM, st>>>(bsplit, a.C, a.m, a.N, a.lam, a.alpha, a.L, a.T, a.Z, a.masks, a.ckpt,
-                                        a.ckpt_every, TR);
+    k<<<grid, CF::NT, CF::SMEM, st>>>(p);
     return check_launch("tc_pgd_forward_kernel");
+}
+
+size_t backward_ws_mp(int MP, int m, int N, int T, int K)
+{
+    int TR = 0, grid = 0;
+    tiling(N, &TR, &grid);
+    (void)TR;
+    const size_t bsplit = (size_t)MP * MP * 4;
+    const size_t q = sizeof(float) * (size_t)K * N * m;
+    const size_t G = sizeof(float) * (size_t)N * m;
+    const size_t part = sizeof(float) * (size_t)T * (grid > 0 ? grid : 1);
+    return bsplit + q + G + part + 256;
+}
+
+template <int MP, bool SPLIT>
+int launch_backward_mp(const BwdArgs &a, void *ws, cudaStream_t st)
+{
+    using CF = Cfg<MP, SPLIT>;
+    uint8_t *base = reinterpret_cast<uint8_t *>(ws);
+    uint8_t *bsplit = base;
+    float *qbuf = reinterpret_cast<float *>(base + (size_t)MP * MP * 4);
+    float *Gbuf = qbuf + (size_t)a.ckpt_every * a.N * a.m;
+    float *partial = Gbuf + (size_t)a.N * a.m;
+    int rc = split_b<MP, SPLIT>(a.B, a.m, bsplit, st);
+    if (rc) return rc;
+    if (a.N == 0) {
+        SLISTA_CUDA_TRY(cudaMemsetAsync(a.dalpha, 0, sizeof(float) * a.T, st));
+        return SLISTA_OK;
+    }
+    TcParams p{};
+    p.Bsplit = bsplit;
+    p.C = a.C;
+    p.m = a.m;
+    p.N = a.N;
+    p.lam = a.lam;
+    p.alpha = a.alpha;
+    p.Lp = nullptr;
+    p.T = a.T;
+    p.masks = const_cast<uint32_t *>(a.masks);
+    // the forward's refresh schedule: at checkpoints when there are any
+    p.ckpt = a.ckpt_every < a.T ? const_cast<float *>(a.ckpt) : nullptr;
+    p.K = a.ckpt_every;
+    p.qbuf = qbuf;
+    p.Gbuf = Gbuf;
+    p.gZ = a.gZ;
+    p.partial = partial;
+    int grid = 0;
+    tiling(a.N, &p.TR, &grid);
+    auto kr = tc_pgd_forward_kernel<MP, SPLIT, true>;
+    auto ka = tc_adjoint_kernel<MP, SPLIT>;
+    SLISTA_CUDA_TRY(allow_smem(kr, CF::SMEM));
+    SLISTA_CUDA_TRY(allow_smem(ka, CF::SMEM));
+    const int K = a.ckpt_every;
+    const int nseg = ceil_div(a.T, K);
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        p.t0 = seg * K;
+        p.t1 = p.t0 + K < a.T ? p.t0 + K : a.T;
+        p.want_gT = (seg == nseg - 1);
+        kr<<<grid, CF::NT, CF::SMEM, st>>>(p);
+        rc = check_launch("tc_pgd_forward_kernel (recompute)");
+        if (rc) return rc;
+        ka<<<grid, CF::NT, CF::SMEM, st>>>(p);
+        rc = check_launch("tc_adjoint_kernel");
+        if (rc) return rc;
+    }
+    tc_reduce_partials_kernel<<<ceil_div(a.T, 8), 256, 0, st>>>(partial, grid, a.T, a.dalpha);
+    return check_launch("tc_reduce_partials_kernel");
 }
 
 }  // namespace
@@ -566,6 +937,13 @@ size_t forward_ws_bytes(int m)
     return (size_t)MP * MP * 2 * 2;
 }
 
+size_t backward_ws_bytes(int m, int N, int T, int K)
+{
+    const int MP = mp_for(m);
+    if (MP == 0) return 0;
+    return backward_ws_mp(MP, m, N, T, K);
+}
+
 int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st)
 {
     const bool split = prec == SLISTA_PREC_BF16X3;
@@ -573,6 +951,19 @@ int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st)
         case 64: return split ? launch_mp<64, true>(a, ws, st) : launch_mp<64, false>(a, ws, st);
         case 128: return split ? launch_mp<128, true>(a, ws, st) : launch_mp<128, false>(a, ws, st);
         case 256: return split ? launch_mp<256, true>(a, ws, st) : launch_mp<256, false>(a, ws, st);
+    }
+    return fail(SLISTA_ERR_UNSUPPORTED, "tensor-core path supports m <= 256 (got %d)", a.m);
+}
+
+int launch_backward(const BwdArgs &a, int prec, void *ws, cudaStream_t st)
+{
+    if (a.ckpt_every > ADJ_KMAX)
+        return fail(SLISTA_ERR_UNSUPPORTED, "tensor-core adjoint: at most %d layers between checkpoints", ADJ_KMAX);
+    const bool split = prec == SLISTA_PREC_BF16X3;
+    switch (mp_for(a.m)) {
+        case 64: return split ? launch_backward_mp<64, true>(a, ws, st) : launch_backward_mp<64, false>(a, ws, st);
+        case 128: return split ? launch_backward_mp<128, true>(a, ws, st) : launch_backward_mp<128, false>(a, ws, st);
+        case 256: return split ? launch_backward_mp<256, true>(a, ws, st) : launch_backward_mp<256, false>(a, ws, st);
     }
     return fail(SLISTA_ERR_UNSUPPORTED, "tensor-core path supports m <= 256 (got %d)", a.m);
 }

@@ -79,8 +79,18 @@ def test_argument_validation_without_gpu(lib):
                                None) == _lib.SLISTA_ERR_WORKSPACE
     assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, 0, vp, None, 3, None, vp, vp, 1 << 30,
                                None) == _lib.SLISTA_ERR_ARG
-    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_BF16X3, vp, vp, 3, None, vp, vp, 1 << 30,
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_TF32, vp, vp, 3, None, vp, vp, 1 << 30,
                                None) == _lib.SLISTA_ERR_UNSUPPORTED
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, 9, vp, vp, 3, None, vp, vp, 1 << 30,
+                               None) == _lib.SLISTA_ERR_ARG
+    # tensor-core adjoint: at most 256 layers per recompute segment, and its own workspace size
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 300, _lib.PREC_BF16X3, vp, None, 300, None, vp, vp, 1 << 30,
+                               None) == _lib.SLISTA_ERR_UNSUPPORTED
+    assert "256" in _err(lib)
+    need = _lib.slista_workspace_bytes(_lib.FN_SLISTA_BWD, 8, 4, 10, _lib.PREC_BF16X3, 3)
+    assert need >= 64 * 64 * 4 + 4 * 3 * 4 * 8
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_BF16X3, vp, vp, 3, None, vp, vp, need - 1,
+                               None) == _lib.SLISTA_ERR_WORKSPACE
     # OISTA and objective null pointers
     assert lib.oista_forward(vp, vp, None, 0, 8, 4, 0.1, None, 3, 0, vp, None, None, None, 0, None) == _lib.SLISTA_ERR_ARG
     assert lib.oista_forward(vp, vp, vp, 4, 8, 4, 0.1, vp, 3, 0, vp, None, None, None, 0,

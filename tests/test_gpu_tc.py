@@ -184,3 +184,115 @@ def test_tc_forward_with_fp32_adjoint(K):
             assert np.abs(ck[s, 0] - Zall[t]).max() <= zt
             g_or = Co - Zall[t] @ Bo
             assert np.abs(ck[s, 1] - g_or).max() <= TOL["bf16x3"]["Z"] * max(1.0, np.abs(g_or).max())
+
+
+# --------------------------------------------------------------------------- tensor-core adjoint
+
+GRAD_TOL = {"bf16x3": 1e-4, "bf16": 3e-2}
+
+
+def _grad_case(N=300, T=40, seed=7):
+    w = synth.slista_64x256(N=N, T=T)
+    Lo = oracle.lipschitz(w.D)
+    alpha = synth.step_sizes(w.T, 1.0 / Lo, 0.3, seed=seed)
+    return w, alpha
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("K", [1, 3, 7, 40])
+def test_tc_backward_matches_oracle_gradient(prec, K):
+    """Forward and adjoint both on the tensor cores (Eq. steprec and its
+    chain rule); the sub-gradient of sum_i F(z_i^(T)) against the FP64 oracle."""
+    w, alpha = _grad_case()
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    _, st = A.slista(g.B, g.C, w.lam, dev(alpha), prec=prec, keep_for_backward=True, ckpt_every=K)
+    dg = host(A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, prec=prec)).astype(np.float64)
+    do, _ = oracle.slista_grad(w.D, w.X, w.lam, alpha)
+    rel = np.linalg.norm(dg - do) / np.linalg.norm(do)
+    assert rel <= GRAD_TOL[prec], (prec, K, rel)
+
+
+def test_tc_backward_deterministic():
+    w, alpha = _grad_case(N=500, T=20, seed=3)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    _, st = A.slista(g.B, g.C, w.lam, dev(alpha), prec="bf16x3", keep_for_backward=True, ckpt_every=5)
+    d1 = A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, prec="bf16x3")
+    d2 = A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, prec="bf16x3")
+    assert torch.equal(d1, d2)
+
+
+def test_tc_backward_upstream_gradient():
+    """gZ = dF/dz^(T) formed on the host in FP64 from the returned codes gives
+    the default gradient; gZ = 0 gives 0; the map gZ -> dalpha is linear."""
+    w, alpha = _grad_case(N=256, T=12, seed=11)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    Z, st = A.slista(g.B, g.C, w.lam, dev(alpha), prec="bf16x3", keep_for_backward=True, ckpt_every=4)
+    d_default = host(A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, prec="bf16x3")).astype(np.float64)
+    Bo, Co, _ = oracle.gram(w.D, w.X)
+    Zh = host(Z).astype(np.float64)
+    GT = Zh @ Bo - Co + w.lam * np.sign(Zh)
+    d_gz = host(A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, gZ=dev(GT.astype(np.float32)),
+                              prec="bf16x3")).astype(np.float64)
+    assert np.linalg.norm(d_gz - d_default) <= 1e-4 * np.linalg.norm(d_default)
+    zero = torch.zeros_like(Z)
+    assert not A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, gZ=zero, prec="bf16x3").any()
+    rng = np.random.default_rng(3)
+    G1 = dev(rng.standard_normal(Z.shape).astype(np.float32))
+    d1 = A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, gZ=G1, prec="bf16x3")
+    d2 = A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, gZ=2 * G1, prec="bf16x3")
+    torch.testing.assert_close(d2, 2 * d1, rtol=1e-5, atol=1e-5 * float(d1.abs().max()))
+
+
+@pytest.mark.parametrize("N", [1, 127, 129])
+def test_tc_backward_small_and_ragged_batches(N):
+    w, alpha = _grad_case(N=N, T=15, seed=13)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    _, st = A.slista(g.B, g.C, w.lam, dev(alpha), prec="bf16x3", keep_for_backward=True, ckpt_every=4)
+    dg = host(A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, prec="bf16x3")).astype(np.float64)
+    do, _ = oracle.slista_grad(w.D, w.X, w.lam, alpha)
+    assert np.linalg.norm(dg - do) <= GRAD_TOL["bf16x3"] * max(np.linalg.norm(do), 1e-12), (dg, do)
+
+
+@pytest.mark.parametrize("n,m", [(10, 20), (48, 100), (64, 128)])
+def test_tc_backward_small_m(n, m):
+    """m padded to 64 / 128 inside the kernels (B_lo resident)."""
+    rng = np.random.default_rng(n + m)
+    D = synth.gaussian_dictionary(n, m, rng)
+    X = synth.sparse_model_samples(D, 300, 0.1, 0.01, rng)
+    lam = synth.lam_fraction(D, X, 0.1)
+    T = 30
+    alpha = synth.step_sizes(T, 1.0 / oracle.lipschitz(D), 0.3, seed=6)
+    A = api()
+    g = A.gram(dev(D), dev(X))
+    _, st = A.slista(g.B, g.C, lam, dev(alpha), prec="bf16x3", keep_for_backward=True, ckpt_every=6)
+    dg = host(A.slista_grad(g.B, g.C, lam, dev(alpha), st, prec="bf16x3")).astype(np.float64)
+    do, _ = oracle.slista_grad(D, X, lam, alpha)
+    assert np.linalg.norm(dg - do) <= GRAD_TOL["bf16x3"] * np.linalg.norm(do), (np.linalg.norm(dg - do) / np.linalg.norm(do))
+
+
+def test_tc_backward_full_size_split_batch():
+    """The benchmark workload (64 x 256, N = 10000, T = 40, checkpoints every
+    7 layers): the sub-gradient is a sum over samples, so the full batch
+    equals the sum over two halves; 256 sampled rows against the oracle."""
+    w = synth.slista_64x256()
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    alpha = (1.0 / g.L.double()).float().expand(w.T).contiguous()
+    _, st = A.slista(g.B, g.C, w.lam, alpha, prec="bf16x3", keep_for_backward=True)
+    da = A.slista_grad(g.B, g.C, w.lam, alpha, st, prec="bf16x3").double()
+    parts = []
+    for sl in (slice(0, 4000), slice(4000, w.N)):
+        C = g.C[sl].contiguous()
+        _, s2 = A.slista(g.B, C, w.lam, alpha, prec="bf16x3", keep_for_backward=True)
+        parts.append(A.slista_grad(g.B, C, w.lam, alpha, s2, prec="bf16x3").double())
+    torch.testing.assert_close(da, parts[0] + parts[1], rtol=1e-4, atol=1e-4 * float(da.abs().max()))
+    rows = np.random.default_rng(2).choice(w.N, size=256, replace=False)
+    C = g.C[torch.from_numpy(rows).cuda()].contiguous()
+    _, s3 = A.slista(g.B, C, w.lam, alpha, prec="bf16x3", keep_for_backward=True)
+    dg = host(A.slista_grad(g.B, C, w.lam, alpha, s3, prec="bf16x3")).astype(np.float64)
+    do, _ = oracle.slista_grad(w.D, w.X[rows], w.lam, host(alpha).astype(np.float32))
+    assert np.linalg.norm(dg - do) <= GRAD_TOL["bf16x3"] * np.linalg.norm(do)
