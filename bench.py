@@ -124,6 +124,24 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- ours
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time: every rank contributes x, all get the maximum
+    (a collective on the timing only; the data path has none)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank: int, world: int, ms: float) -> float:
+    """Samples per second of the whole job: every rank processed n_per_rank
+    samples (weak scaling) within the slowest rank's ms."""
+    return n_per_rank * world / (ms / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -210,11 +228,8 @@ def run_ours(args, rank, world, local_rank):
         total += e[0].elapsed_time(e[5])
     ms_step = total / args.steps
     per_part = {p: v / args.steps for p, v in per_part.items()}
-    if world > 1:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = N * world / (ms_step / 1e3)
+    ms_step = max_over_ranks(ms_step, world, dev)
+    value = job_throughput(N, world, ms_step)
 
     # ---- end to end through the public API, host buffers, copies timed
     e2e = None
@@ -257,13 +272,10 @@ def run_ours(args, rank, world, local_rank):
             a1.synchronize()
             tot += a0.elapsed_time(a1)
         e_ms = tot / args.steps
-        if world > 1:
-            t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(e_ms, world, dev)
         h2d = Dh.numel() * 4 + Xh.numel() * 4 + Ah.numel() * 4
         d2h = Zh.numel() * 4 + Fh.numel() * 8 + Gh.numel() * 8 + dah.numel() * 4 + Zoh.numel() * 4
-        e2e = {"value": N * world / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
+        e2e = {"value": job_throughput(N, world, e_ms), "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # ---- roofline of the dominant kernel (per-launch figures)

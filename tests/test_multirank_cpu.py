@@ -1,0 +1,64 @@
+"""The multi-rank logic of bench.py on CPU: two gloo ranks (world_size 2)
+combine their step times by the maximum and report the whole job's samples/s
+(weak scaling: each rank works on its own samples, no data-path collective);
+each rank draws its own seeded samples; the reference arm runs on rank 0 only."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_1905_11071_gb300 import synth
+    ms = [3.0, 5.0][rank]
+    got = bench.max_over_ranks(ms, world, "cpu")
+    val = bench.job_throughput(10000, world, got)
+    w = synth.slista_64x256(seed=rank, N=16, T=2)
+    ref = bench.run_reference(type("A", (), {"N": 16, "T": 2, "cpu_samples": 1, "warmup": 0, "steps": 1})(),
+                              rank, world)
+    out[rank] = (got, val, float(w.X[0, 0]), ref is None)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_combine_by_max():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as man:
+        out = man.dict()
+        mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    for r in range(world):
+        got, val, x00, ref_none = res[r]
+        assert got == 5.0
+        assert val == pytest.approx(10000 * 2 / 5e-3)
+        assert ref_none == (r != 0)
+    # weak scaling: the ranks draw different samples
+    assert res[0][2] != res[1][2]
+
+
+def test_single_rank_needs_no_process_group():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(2.5, 1, "cpu") == 2.5
+    assert bench.job_throughput(100, 1, 1000.0) == pytest.approx(100.0)
+    assert np.isfinite(bench.job_throughput(1, 8, 1e-3))
