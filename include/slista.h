@@ -184,6 +184,52 @@ SLISTA_API int slista_backward(const float *B, const float *C, int m, int N, flo
                     const float *gZ, float *dalpha,
                     void *ws, size_t ws_bytes, void *stream);
 
+/* ---- ragged batches (many independent problems in one launch per layer) ----
+ *
+ * Each problem has its own dictionary width m, batch size N, lam, step sizes
+ * and buffers; T, ckpt_every and the precision are shared.  The layers of
+ * all problems run as one launch per layer (up to 64 problems per launch),
+ * on the tensor-core layer kernel for wide dictionaries (any 1 <= m <= 1024):
+ * the state (z, g) of every problem lives in the workspace between layers
+ * and each launch computes, for every 128-sample x 256-code block of every
+ * problem, the block of (z - z') B and the block's z', g' (Eq. steprec).
+ * `problems` is a HOST array of `count` descriptors holding device pointers;
+ * it is read during the call only.  prec: SLISTA_PREC_BF16 or
+ * SLISTA_PREC_BF16X3 (else SLISTA_ERR_UNSUPPORTED).  The paper has no
+ * batched entry point: it trains one problem at a time. */
+typedef struct slista_problem {
+    const float *B;      /* m x m, B = D^T D */
+    const float *C;      /* N x m, row i = (D^T x_i)^T */
+    int m;               /* 1 <= m <= 1024 */
+    int N;               /* >= 0 */
+    float lam;           /* >= 0 */
+    const float *alpha;  /* T step sizes (> 0) */
+    float *Z;            /* forward: N x m codes z^(T) (out) */
+    uint32_t *masks;     /* T x N x ceil(m/32) support words: written by the forward
+                          * (nullable there), read by the backward */
+    float *ckpt;         /* slista_ckpt_floats(m, N, T, ckpt_every) floats: written by
+                          * the forward, read by the backward; may be NULL when
+                          * ckpt_every >= T */
+    const float *gZ;     /* backward: upstream gradient dLoss/dz^(T) (N x m), nullable */
+    float *dalpha;       /* backward: T floats (out) */
+} slista_problem_t;
+
+/* Workspace of slista_forward_batched (fn = SLISTA_FN_SLISTA_FWD) or
+ * slista_backward_batched (fn = SLISTA_FN_SLISTA_BWD) for these problems. */
+SLISTA_API size_t slista_batched_workspace_bytes(int fn, const slista_problem_t *problems, int count, int T,
+                                                 int prec, int ckpt_every);
+
+/* Step-LISTA forward (Eq. steprec) of every problem: Z, and masks / ckpt where
+ * given (checkpoint layout of slista_forward, every ckpt_every layers). */
+SLISTA_API int slista_forward_batched(const slista_problem_t *problems, int count, int T, int prec,
+                                      int ckpt_every, void *ws, size_t ws_bytes, void *stream);
+
+/* Step-size sub-gradient of every problem (the adjoint of slista_backward),
+ * from the masks and checkpoints of a slista_forward_batched call with the
+ * same problems, T, prec and ckpt_every; dalpha per problem. */
+SLISTA_API int slista_backward_batched(const slista_problem_t *problems, int count, int T, int prec,
+                                       int ckpt_every, void *ws, size_t ws_bytes, void *stream);
+
 /* Oracle-ISTA, Algorithm 1 (Section 3): at every layer, S = supp(z^(t)),
  * L_S = largest eigenvalue of B_SS (Eq. spca; L_empty = L, recomputed only
  * when S changes), y = ST(z - (Bz - c)/L_S, lam/L_S); z^(t+1) = y when

@@ -38,7 +38,16 @@ EXPORTS = [
     "slista_last_error", "slista_device_status", "slista_workspace_bytes", "slista_ckpt_floats",
     "slista_mask_words", "lasso_gram", "lasso_lipschitz", "ista_forward", "slista_forward",
     "slista_backward", "oista_forward", "lasso_objective", "slista_forward_noalloc",
+    "slista_batched_workspace_bytes", "slista_forward_batched", "slista_backward_batched",
 ]
+
+
+class Problem(ctypes.Structure):
+    """slista_problem_t: one problem of a ragged batch (device pointers)."""
+    _fields_ = [("B", ctypes.c_void_p), ("C", ctypes.c_void_p), ("m", ctypes.c_int), ("N", ctypes.c_int),
+                ("lam", ctypes.c_float), ("alpha", ctypes.c_void_p), ("Z", ctypes.c_void_p),
+                ("masks", ctypes.c_void_p), ("ckpt", ctypes.c_void_p), ("gZ", ctypes.c_void_p),
+                ("dalpha", ctypes.c_void_p)]
 
 
 class SlistaError(RuntimeError):
@@ -82,9 +91,14 @@ def load(path: str = LIB_PATH):
         lib.slista_forward_noalloc.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp]
         lib.oista_forward.argtypes = [vp, vp, vp, i, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
         lib.lasso_objective.argtypes = [vp, vp, vp, vp, i, i, f, vp, vp, vp]
+        pp = ctypes.POINTER(Problem)
+        lib.slista_batched_workspace_bytes.restype = sz
+        lib.slista_batched_workspace_bytes.argtypes = [i, pp, i, i, i, i]
+        lib.slista_forward_batched.argtypes = [pp, i, i, i, i, vp, sz, vp]
+        lib.slista_backward_batched.argtypes = [pp, i, i, i, i, vp, sz, vp]
         for name in EXPORTS:
             if name not in ("slista_last_error", "slista_workspace_bytes", "slista_ckpt_floats",
-                            "slista_mask_words"):
+                            "slista_mask_words", "slista_batched_workspace_bytes"):
                 getattr(lib, name).restype = i
         _lib = lib
         return lib
@@ -269,3 +283,55 @@ def lasso_objective(B, C, xsq, Z, lam, F, gap=None, stream=None) -> None:
     _opt(gap, torch.float64, (N,), "gap")
     _check(load().lasso_objective(_ptr(B), _ptr(C), _ptr(xsq), _ptr(Z), m, N, float(lam), _ptr(F), _ptr(gap),
                                   _stream(stream)), "lasso_objective")
+
+
+def _problems(probs, T, backward):
+    """ctypes array of slista_problem_t from dicts of tensors (keys B, C, lam,
+    alpha, Z, masks, ckpt, gZ, dalpha; m and N from C)."""
+    import torch
+    arr = (Problem * max(len(probs), 1))()
+    for i, q in enumerate(probs):
+        C = q["C"]
+        N, m = C.shape
+        _need(q["B"], torch.float32, (m, m), "B")
+        _need(C, torch.float32, (N, m), "C")
+        _need(q["alpha"], torch.float32, (T,), "alpha")
+        _opt(q.get("masks"), torch.int32, None, "masks")
+        _opt(q.get("ckpt"), torch.float32, None, "ckpt")
+        if backward:
+            _opt(q.get("gZ"), torch.float32, (N, m), "gZ")
+            _need(q["dalpha"], torch.float32, (T,), "dalpha")
+        else:
+            _need(q["Z"], torch.float32, (N, m), "Z")
+        p = arr[i]
+        p.B = q["B"].data_ptr()
+        p.C = C.data_ptr()
+        p.m = m
+        p.N = N
+        p.lam = float(q["lam"])
+        p.alpha = q["alpha"].data_ptr()
+        for k in ("Z", "masks", "ckpt", "gZ", "dalpha"):
+            t = q.get(k)
+            setattr(p, k, None if t is None else t.data_ptr())
+    return arr
+
+
+def slista_batched_workspace_bytes(fn: int, probs, T: int, prec: int, ckpt_every: int) -> int:
+    arr = (Problem * max(len(probs), 1))()
+    for i, q in enumerate(probs):
+        arr[i].m, arr[i].N = int(q["m"]), int(q["N"])
+    return int(load().slista_batched_workspace_bytes(fn, arr, len(probs), T, prec, ckpt_every))
+
+
+def slista_forward_batched(probs, T, prec, ckpt_every, ws=None, stream=None) -> None:
+    arr = _problems(probs, T, backward=False)
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().slista_forward_batched(arr, len(probs), T, int(prec), int(ckpt_every), _ptr(ws), wsb,
+                                         _stream(stream)), "slista_forward_batched")
+
+
+def slista_backward_batched(probs, T, prec, ckpt_every, ws=None, stream=None) -> None:
+    arr = _problems(probs, T, backward=True)
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().slista_backward_batched(arr, len(probs), T, int(prec), int(ckpt_every), _ptr(ws), wsb,
+                                          _stream(stream)), "slista_backward_batched")

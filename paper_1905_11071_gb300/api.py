@@ -116,6 +116,56 @@ def slista_grad(B, C, lam, alpha, state: ForwardState, gZ=None, prec="fp32", str
     return dalpha
 
 
+def slista_batched(problems, prec="bf16x3", keep_for_backward: bool = False, ckpt_every: Optional[int] = None,
+                   stream=None):
+    """Step-LISTA forward of a ragged batch (one launch per layer for all
+    problems).  problems: list of dicts with B (m x m), C (N x m), lam and
+    alpha (T steps, the same T for all).  Returns the list of Z, and with
+    keep_for_backward the per-problem masks / checkpoints (added to the dicts
+    under "masks", "ckpt") and the checkpoint spacing."""
+    T = int(problems[0]["alpha"].shape[0]) if problems else 0
+    p = _prec(prec)
+    K = ckpt_every or default_ckpt_every(T)
+    dev = problems[0]["C"].device if problems else None
+    probs = []
+    for q in problems:
+        N, m = q["C"].shape
+        d = dict(q)
+        d["Z"] = torch.empty((N, m), dtype=torch.float32, device=dev)
+        if keep_for_backward:
+            d["masks"] = torch.empty((max(1, _lib.slista_mask_words(m, N, T)),), dtype=torch.int32, device=dev)
+            nck = _lib.slista_ckpt_floats(m, N, T, K)
+            d["ckpt"] = torch.empty((nck,), dtype=torch.float32, device=dev) if nck > 0 else None
+        else:
+            d.pop("masks", None)
+            d.pop("ckpt", None)
+        probs.append(d)
+    sizes = [{"m": int(q["C"].shape[1]), "N": int(q["C"].shape[0])} for q in problems]
+    ws = workspace(_lib.slista_batched_workspace_bytes(_lib.FN_SLISTA_FWD, sizes, T, p, K), dev, "bfwd") \
+        if problems else None
+    _lib.slista_forward_batched(probs, T, p, K, ws=ws, stream=stream)
+    Zs = [d["Z"] for d in probs]
+    return (Zs, probs, K) if keep_for_backward else Zs
+
+
+def slista_grad_batched(probs, ckpt_every: int, prec="bf16x3", gZs=None, stream=None):
+    """Step-size sub-gradients of a batch from slista_batched(...,
+    keep_for_backward=True)'s problem dicts.  Returns the list of dalpha."""
+    T = int(probs[0]["alpha"].shape[0])
+    p = _prec(prec)
+    dev = probs[0]["C"].device
+    qs = []
+    for i, d in enumerate(probs):
+        q = dict(d)
+        q["dalpha"] = torch.empty((T,), dtype=torch.float32, device=dev)
+        q["gZ"] = None if gZs is None else gZs[i]
+        qs.append(q)
+    sizes = [{"m": int(q["C"].shape[1]), "N": int(q["C"].shape[0])} for q in probs]
+    ws = workspace(_lib.slista_batched_workspace_bytes(_lib.FN_SLISTA_BWD, sizes, T, p, ckpt_every), dev, "bbwd")
+    _lib.slista_backward_batched(qs, T, p, ckpt_every, ws=ws, stream=stream)
+    return [q["dalpha"] for q in qs]
+
+
 def oista(B, C, lam, L, T, D=None, stream=None):
     """Oracle-ISTA (Algorithm 1).  Returns (Z, LS, accepted).  D (optional)
     lets supports larger than 64 be solved on the n x n matrix D_S D_S^T."""

@@ -4,6 +4,8 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -77,8 +79,14 @@ int forward_common(const PgdArgs &a, int prec, void *ws, size_t ws_bytes, cudaSt
         return simt::launch_forward(a, st);
     }
     if (prec == SLISTA_PREC_TF32) return fail(SLISTA_ERR_UNSUPPORTED, "%s: TF32 is not built", name);
-    SLISTA_REQUIRE(tc::supported(a.m), SLISTA_ERR_UNSUPPORTED, "%s: tensor-core path does not support m = %d", name,
-                   a.m);
+    SLISTA_REQUIRE(tc::supported(a.m) || tcw::supported(a.m), SLISTA_ERR_UNSUPPORTED,
+                   "%s: tensor-core path supports m <= 1024 (got %d)", name, a.m);
+    if (!tc::supported(a.m)) {  // m > 256: one launch per layer
+        const size_t need = tcw::forward_ws_bytes(a.m, a.N);
+        SLISTA_REQUIRE(ws_bytes >= need && ws != nullptr, SLISTA_ERR_WORKSPACE,
+                       "%s: workspace of %zu bytes needed, %zu given", name, need, ws_bytes);
+        return tcw::launch_forward(a, prec, ws, st);
+    }
     const size_t need = tc::forward_ws_bytes(a.m);
     SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws != nullptr), SLISTA_ERR_WORKSPACE,
                    "%s: workspace of %zu bytes needed, %zu given", name, need, ws_bytes);
@@ -118,12 +126,16 @@ size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_ev
     switch (fn) {
         case SLISTA_FN_ISTA:
         case SLISTA_FN_SLISTA_FWD:
-            if (prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3) return tc::forward_ws_bytes(m);
+            if (prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3)
+                return tc::supported(m) ? tc::forward_ws_bytes(m) : tcw::supported(m) ? tcw::forward_ws_bytes(m, N) : 0;
             return 0;
         case SLISTA_FN_SLISTA_BWD:
             if (ckpt_every <= 0 || T <= 0) return 0;
-            if (prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3)
-                return tc::backward_ws_bytes(m, N, T, ckpt_every < T ? ckpt_every : T);
+            if (prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3) {
+                const int K = ckpt_every < T ? ckpt_every : T;
+                return tc::supported(m) ? tc::backward_ws_bytes(m, N, T, K)
+                                        : tcw::supported(m) ? tcw::backward_ws_bytes(m, N, T, K) : 0;
+            }
             return simt::backward_ws_bytes(m, N, T, ckpt_every < T ? ckpt_every : T);
         case SLISTA_FN_OISTA: return simt::padded_mp(m) ? simt::oista_ws_bytes(m, N, T) : 0;
         default: return 0;
@@ -137,7 +149,7 @@ int lasso_gram(const float *D, int n, int m, const float *X, int N, float *B, fl
     SLISTA_REQUIRE(n >= 1 && m >= 1 && N >= 0, SLISTA_ERR_ARG, "lasso_gram: bad sizes n=%d m=%d N=%d", n, m, N);
     SLISTA_REQUIRE(D && B, SLISTA_ERR_ARG, "lasso_gram: D and B must not be NULL");
     SLISTA_REQUIRE(N == 0 || (X && C && xsq), SLISTA_ERR_ARG, "lasso_gram: X, C, xsq must not be NULL");
-    SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "lasso_gram: m <= 256 supported (got %d)", m);
+    SLISTA_REQUIRE(m <= 1024, SLISTA_ERR_UNSUPPORTED, "lasso_gram: m <= 1024 supported (got %d)", m);
     cudaStream_t st = as_stream(stream);
     int rc = gram::launch_gram(D, n, m, X, N, B, C, xsq, st);
     if (rc) return rc;
@@ -212,7 +224,8 @@ int slista_backward(const float *B, const float *C, int m, int N, float lam, con
     const bool tcp = prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3;
     SLISTA_REQUIRE(prec == SLISTA_PREC_FP32 || tcp, prec == SLISTA_PREC_TF32 ? SLISTA_ERR_UNSUPPORTED : SLISTA_ERR_ARG,
                    "slista_backward: precision %d not supported", prec);
-    SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "slista_backward: m <= 256 supported");
+    SLISTA_REQUIRE(tcp ? (tc::supported(m) || tcw::supported(m)) : simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED,
+                   "slista_backward: m <= %d supported with this precision (got %d)", tcp ? 1024 : 256, m);
     SLISTA_REQUIRE(B && alpha && dalpha, SLISTA_ERR_ARG, "slista_backward: B, alpha, dalpha must not be NULL");
     SLISTA_REQUIRE(ckpt_every >= 1, SLISTA_ERR_ARG, "slista_backward: ckpt_every must be >= 1");
     const int K = ckpt_every < T ? ckpt_every : T;
@@ -222,10 +235,14 @@ int slista_backward(const float *B, const float *C, int m, int N, float lam, con
     SLISTA_REQUIRE(N == 0 || K >= T || ckpt, SLISTA_ERR_ARG, "slista_backward: ckpt must not be NULL");
     int rc = check_lam(lam);
     if (rc) return rc;
-    const size_t need = tcp ? tc::backward_ws_bytes(m, N, T, K) : simt::backward_ws_bytes(m, N, T, K);
+    const bool wide = tcp && !tc::supported(m);
+    const size_t need = wide  ? tcw::backward_ws_bytes(m, N, T, K)
+                        : tcp ? tc::backward_ws_bytes(m, N, T, K)
+                              : simt::backward_ws_bytes(m, N, T, K);
     SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
                    "slista_backward: workspace of %zu bytes needed, %zu given", need, ws_bytes);
     BwdArgs a{B, C, m, N, lam, alpha, T, masks, ckpt, K, gZ, dalpha};
+    if (wide) return tcw::launch_backward(a, prec, ws, as_stream(stream));
     if (tcp) return tc::launch_backward(a, prec, ws, as_stream(stream));
     return simt::launch_backward(a, ws, as_stream(stream));
 }
@@ -257,11 +274,100 @@ int lasso_objective(const float *B, const float *C, const double *xsq, const flo
     SLISTA_REQUIRE(B, SLISTA_ERR_ARG, "lasso_objective: B must not be NULL");
     SLISTA_REQUIRE(N == 0 || (C && xsq && Z && F), SLISTA_ERR_ARG,
                    "lasso_objective: C, xsq, Z, F must not be NULL");
-    SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "lasso_objective: m <= 256 supported");
+    SLISTA_REQUIRE(m <= 1024, SLISTA_ERR_UNSUPPORTED, "lasso_objective: m <= 1024 supported (got %d)", m);
     int rc = check_lam(lam);
     if (rc) return rc;
     ObjArgs a{B, C, xsq, Z, m, N, lam, F, gap};
     return simt::launch_objective(a, as_stream(stream));
+}
+
+static int batch_args(const slista_problem_t *problems, int count, int T, int prec, int ckpt_every, bool bwd,
+                      std::vector<tcw::Problem> &out, const char *name)
+{
+    SLISTA_REQUIRE(count >= 0 && T >= 0 && (count == 0 || problems), SLISTA_ERR_ARG, "%s: bad batch (count=%d T=%d)",
+                   name, count, T);
+    SLISTA_REQUIRE(valid_prec(prec), SLISTA_ERR_ARG, "%s: unknown precision %d", name, prec);
+    SLISTA_REQUIRE(prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3, SLISTA_ERR_UNSUPPORTED,
+                   "%s: batches run on the tensor cores (SLISTA_PREC_BF16 or SLISTA_PREC_BF16X3)", name);
+    SLISTA_REQUIRE(ckpt_every >= 1, SLISTA_ERR_ARG, "%s: ckpt_every must be >= 1", name);
+    SLISTA_REQUIRE(!bwd || T >= 1, SLISTA_ERR_ARG, "%s: T must be >= 1", name);
+    out.resize(count);
+    for (int i = 0; i < count; ++i) {
+        const slista_problem_t &q = problems[i];
+        SLISTA_REQUIRE(q.m >= 1 && q.N >= 0, SLISTA_ERR_ARG, "%s: problem %d: bad sizes m=%d N=%d", name, i, q.m, q.N);
+        SLISTA_REQUIRE(tcw::supported(q.m), SLISTA_ERR_UNSUPPORTED, "%s: problem %d: m <= 1024 supported (got %d)",
+                       name, i, q.m);
+        SLISTA_REQUIRE(q.B && (T == 0 || q.alpha), SLISTA_ERR_ARG, "%s: problem %d: B and alpha must not be NULL",
+                       name, i);
+        SLISTA_REQUIRE(q.N == 0 || q.C, SLISTA_ERR_ARG, "%s: problem %d: C must not be NULL", name, i);
+        SLISTA_REQUIRE(!(q.lam < 0.0f) && !isnan(q.lam) && !isinf(q.lam), SLISTA_ERR_ARG,
+                       "%s: problem %d: lam must be finite and >= 0", name, i);
+        const bool needs_ck = ckpt_every < T;
+        if (bwd) {
+            SLISTA_REQUIRE(q.dalpha, SLISTA_ERR_ARG, "%s: problem %d: dalpha must not be NULL", name, i);
+            SLISTA_REQUIRE(q.N == 0 || (q.masks && (!needs_ck || q.ckpt)), SLISTA_ERR_ARG,
+                           "%s: problem %d: masks and ckpt must not be NULL", name, i);
+        } else {
+            SLISTA_REQUIRE(q.N == 0 || q.Z, SLISTA_ERR_ARG, "%s: problem %d: Z must not be NULL", name, i);
+        }
+        tcw::Problem &p = out[i];
+        p = tcw::Problem{};
+        p.B = q.B;
+        p.C = q.C;
+        p.m = q.m;
+        p.N = q.N;
+        p.lam = q.lam;
+        p.alpha = q.alpha;
+        p.Z = q.Z;
+        p.masks = q.masks;
+        p.ckpt = q.ckpt;
+        p.gZ = q.gZ;
+        p.dalpha = q.dalpha;
+    }
+    return SLISTA_OK;
+}
+
+size_t slista_batched_workspace_bytes(int fn, const slista_problem_t *problems, int count, int T, int prec,
+                                      int ckpt_every)
+{
+    if (count <= 0 || !problems || T < 0 || ckpt_every < 1) return 0;
+    (void)prec;
+    std::vector<tcw::Problem> v(count);
+    for (int i = 0; i < count; ++i) {
+        v[i] = tcw::Problem{};
+        v[i].m = problems[i].m;
+        v[i].N = problems[i].N;
+        if (!tcw::supported(v[i].m) || v[i].N < 0) return 0;
+    }
+    if (fn == SLISTA_FN_SLISTA_FWD) return tcw::forward_batch_ws_bytes(v.data(), count);
+    if (fn == SLISTA_FN_SLISTA_BWD && T >= 1) return tcw::backward_batch_ws_bytes(v.data(), count, T, ckpt_every);
+    return 0;
+}
+
+int slista_forward_batched(const slista_problem_t *problems, int count, int T, int prec, int ckpt_every, void *ws,
+                           size_t ws_bytes, void *stream)
+{
+    clear_error();
+    std::vector<tcw::Problem> v;
+    int rc = batch_args(problems, count, T, prec, ckpt_every, false, v, "slista_forward_batched");
+    if (rc) return rc;
+    const size_t need = tcw::forward_batch_ws_bytes(v.data(), count);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
+                   "slista_forward_batched: workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    return tcw::forward_batch(v.data(), count, T, ckpt_every, prec, ws, as_stream(stream));
+}
+
+int slista_backward_batched(const slista_problem_t *problems, int count, int T, int prec, int ckpt_every, void *ws,
+                            size_t ws_bytes, void *stream)
+{
+    clear_error();
+    std::vector<tcw::Problem> v;
+    int rc = batch_args(problems, count, T, prec, ckpt_every, true, v, "slista_backward_batched");
+    if (rc) return rc;
+    const size_t need = tcw::backward_batch_ws_bytes(v.data(), count, T, ckpt_every);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
+                   "slista_backward_batched: workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    return tcw::backward_batch(v.data(), count, T, ckpt_every, prec, ws, as_stream(stream));
 }
 
 }  // extern "C"

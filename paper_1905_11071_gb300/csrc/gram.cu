@@ -52,8 +52,19 @@ __global__ void __launch_bounds__(NT) xd_kernel(const float *__restrict__ X, con
     for (int i = 0; i < TL::RM; ++i)
 #pragma unroll
         for (int j = 0; j < TL::RN; ++j) acc[i][j] = 0.0f;
-    simt::gemm_acc<TL>(acc, A_s, lda, D, n, m, m, B_s);
-    simt::store_rows<TL>(C, acc, row0, N, m, m);
+    simt::gemm_acc<TL>(acc, A_s, lda, D, n, m < MP ? m : MP, m, B_s);
+    simt::store_rows<TL>(C, acc, row0, N, m < MP ? m : MP, m);
+    // wider dictionaries: the remaining column blocks of MP columns
+#pragma unroll 1
+    for (int c0 = MP; c0 < m; c0 += MP) {
+        const int nc = m - c0 < MP ? m - c0 : MP;
+#pragma unroll
+        for (int i = 0; i < TL::RM; ++i)
+#pragma unroll
+            for (int j = 0; j < TL::RN; ++j) acc[i][j] = 0.0f;
+        simt::gemm_acc<TL>(acc, A_s, lda, D + c0, n, nc, m, B_s);
+        simt::store_rows<TL>(C + c0, acc, row0, N, nc, m);
+    }
 }
 
 // B[a][b] = sum_i D[i][a] D[i][b]; identical arithmetic for (a,b) and (b,a).
@@ -245,7 +256,8 @@ int launch_gram(const float *D, int n, int m, const float *X, int N, float *B, f
         case 128: return launch_xd<128>(D, n, m, X, N, C, xsq, st);
         case 256: return launch_xd<256>(D, n, m, X, N, C, xsq, st);
     }
-    return fail(SLISTA_ERR_UNSUPPORTED, "lasso_gram supports m <= 256 (got %d)", m);
+    if (m <= 1024) return launch_xd<256>(D, n, m, X, N, C, xsq, st);  // column blocks of 256
+    return fail(SLISTA_ERR_UNSUPPORTED, "lasso_gram supports m <= 1024 (got %d)", m);
 }
 
 int launch_lipschitz_from_D(const float *D, int n, int m, double *L, cudaStream_t st)

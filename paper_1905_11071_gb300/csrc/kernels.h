@@ -84,6 +84,33 @@ int launch_forward_noalloc(const PgdArgs &a, int prec, cudaStream_t st);
 int noalloc_max_m();
 }  // namespace tc
 
+namespace tcw {
+// tcgen05 layers for 256 < m <= 1024 and for batches of problems: one launch
+// per layer, state in HBM.
+struct Problem {
+    const float *B, *C;
+    int m, N;
+    float lam;
+    const float *alpha;  // T steps, or nullptr: 1 / L
+    const double *L;
+    float *Z;
+    uint32_t *masks;
+    float *ckpt;
+    const float *gZ;
+    float *dalpha;
+};
+bool supported(int m);
+size_t forward_batch_ws_bytes(const Problem *P, int count);
+size_t backward_batch_ws_bytes(const Problem *P, int count, int T, int K);
+int forward_batch(const Problem *P, int count, int T, int K, int prec, void *ws, cudaStream_t st);
+int backward_batch(const Problem *P, int count, int T, int K, int prec, void *ws, cudaStream_t st);
+size_t forward_ws_bytes(int m, int N);
+int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st);
+size_t backward_ws_bytes(int m, int N, int T, int K);
+int launch_backward(const BwdArgs &a, int prec, void *ws, cudaStream_t st);
+int read_and_clear_flag(cudaStream_t st);
+}  // namespace tcw
+
 // Device-side error flag (set by bounded waits that expire).
 int read_and_clear_device_flag(cudaStream_t st);
 

@@ -282,6 +282,84 @@ __global__ void __launch_bounds__(NT) objective_kernel(
     }
 }
 
+// Objective and gap for wide dictionaries (256 < m <= 1024): the sample
+// rows z (all m codes) sit in A_s, w = z B is formed 256 columns at a time
+// by the tile engine, and the per-row sums of objective_kernel accumulate
+// over the column blocks in registers.
+template <int NB>
+__global__ void __launch_bounds__(NT) objective_wide_kernel(
+    const float *__restrict__ B, const float *__restrict__ C, const double *__restrict__ xsq,
+    const float *__restrict__ Z, int m, int N, int lda, float lam, double *__restrict__ F,
+    double *__restrict__ gap)
+{
+    using TL = Tile<256, NB>;
+    extern __shared__ float4 smem4[];
+    float *A_s = reinterpret_cast<float *>(smem4);
+    float *B_s = A_s + (size_t)NB * lda;
+    const Idx<TL> ix;
+    const int row0 = blockIdx.x * NB;
+    const int kp = lda - 4;  // m rounded up to 16
+    for (int e = threadIdx.x; e < NB * kp; e += NT) {
+        const int r = e / kp, k = e % kp;
+        A_s[r * lda + k] = (row0 + r < N && k < m) ? __ldg(Z + (size_t)(row0 + r) * m + k) : 0.0f;
+    }
+    double cz[TL::RM], zw[TL::RM], l1[TL::RM];
+    float cinf[TL::RM];
+#pragma unroll
+    for (int i = 0; i < TL::RM; ++i) {
+        cz[i] = zw[i] = l1[i] = 0.0;
+        cinf[i] = 0.0f;
+    }
+#pragma unroll 1
+    for (int c0 = 0; c0 < m; c0 += 256) {
+        const int nc = m - c0 < 256 ? m - c0 : 256;
+        float w[TL::RM][TL::RN], c[TL::RM][TL::RN];
+#pragma unroll
+        for (int i = 0; i < TL::RM; ++i)
+#pragma unroll
+            for (int j = 0; j < TL::RN; ++j) w[i][j] = 0.0f;
+        gemm_acc<TL>(w, A_s, lda, B + c0, m, nc, m, B_s);
+        load_rows<TL>(c, C + c0, row0, N, nc, m);
+#pragma unroll
+        for (int i = 0; i < TL::RM; ++i)
+#pragma unroll
+            for (int q = 0; q < TL::GPT; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int col = ix.col(q, e);
+                    if (col >= nc) continue;
+                    const float zv = A_s[ix.row(i) * lda + c0 + col];
+                    const float wv = w[i][q * 4 + e], cv = c[i][q * 4 + e];
+                    cz[i] = fma((double)cv, (double)zv, cz[i]);
+                    zw[i] = fma((double)zv, (double)wv, zw[i]);
+                    l1[i] += (double)fabsf(zv);
+                    cinf[i] = fmaxf(cinf[i], fabsf(cv - wv));
+                }
+    }
+#pragma unroll
+    for (int i = 0; i < TL::RM; ++i) {
+#pragma unroll
+        for (int o = TL::TXN / 2; o > 0; o >>= 1) {
+            cz[i] += __shfl_xor_sync(0xffffffffu, cz[i], o);
+            zw[i] += __shfl_xor_sync(0xffffffffu, zw[i], o);
+            l1[i] += __shfl_xor_sync(0xffffffffu, l1[i], o);
+            cinf[i] = fmaxf(cinf[i], __shfl_xor_sync(0xffffffffu, cinf[i], o));
+        }
+        const int r = row0 + ix.row(i);
+        if (ix.tx == 0 && r < N) {
+            const double xx = xsq[r];
+            const double Fv = 0.5 * xx - cz[i] + 0.5 * zw[i] + (double)lam * l1[i];
+            F[r] = Fv;
+            if (gap) {
+                const double r2 = xx - 2.0 * cz[i] + zw[i];
+                const double xr = xx - cz[i];
+                const double sc = (double)cinf[i] > (double)lam ? (double)lam / (double)cinf[i] : 1.0;
+                gap[r] = Fv - (sc * xr - 0.5 * sc * sc * r2);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
@@ -406,7 +484,18 @@ int launch_objective(const ObjArgs &a, cudaStream_t st)
         case 128: return launch_objective_mp<128>(a, st);
         case 256: return launch_objective_mp<256>(a, st);
     }
-    return fail(SLISTA_ERR_UNSUPPORTED, "objective kernel supports m <= 256 (got %d)", a.m);
+    if (a.m <= 1024) {
+        constexpr int NB = 32;
+        const int lda = ((a.m + 15) / 16) * 16 + 4;
+        const size_t smem = sizeof(float) * ((size_t)NB * lda + Tile<256, NB>::BS_FLOATS);
+        auto k = objective_wide_kernel<NB>;
+        SLISTA_CUDA_TRY(allow_smem(k, smem));
+        const int grid = ceil_div(a.N, NB);
+        if (grid == 0) return SLISTA_OK;
+        k<<<grid, NT, smem, st>>>(a.B, a.C, a.xsq, a.Z, a.m, a.N, lda, a.lam, a.F, a.gap);
+        return check_launch("objective_wide_kernel");
+    }
+    return fail(SLISTA_ERR_UNSUPPORTED, "objective kernel supports m <= 1024 (got %d)", a.m);
 }
 
 }  // namespace simt

@@ -1,0 +1,742 @@
+// Tensor-core layers for wide dictionaries (256 < m <= 1024), and for
+// batches of problems of any width: one launch per layer.
+//
+// For m > 256 neither B (m x m) nor the accumulator of a full sample row fits
+// on chip, so the state (z, g = c - B z) of layer t lives in HBM and a layer
+//   z' = ST(z + alpha_t g, alpha_t lam),   g' = g + (z - z') B     (Eq. pgd / Eq. steprec)
+// is one GEMM-shaped launch: CTA (row tile r, column block b) computes the
+// 128 x 256 block [r, b] of (z - z') B on the tensor cores and finishes its
+// block of g' and z' in the epilogue.  Per K-chunk of 64 codes:
+//   * all 16 warps build the A operand (z - z') of the chunk from z and g
+//     (FP32 soft-threshold, split into BF16 hi / lo) straight into shared
+//     memory in the K-major 128-byte-swizzled layout;
+//   * thread 0 streams the chunk's B tile (hi and lo, pre-split and
+//     pre-swizzled) from L2 with one bulk copy, and issues
+//       BF16X3: a_hi b_hi + a_lo b_hi + a_hi b_lo      BF16: a_hi b_hi
+//     as tcgen05.mma (A and B from shared memory, FP32 accumulator in tensor
+//     memory), two stages deep.
+// Every REFRESH layers (at the checkpoints when checkpoints are kept) the
+// A operand is -z' and the epilogue adds C instead of g, so g' = c - B z' is
+// rebuilt from scratch (the drift bound of the resident kernel).
+// The adjoint layer has the same shape: A = h = G * mask_t, and the epilogue
+// forms G' = h - alpha_t (B h) and the block's share of
+// dalpha_t = <h, g^(t) - lam sign z^(t+1)>.
+// Work items (problem, row tile, column block) come from a table in the
+// launch parameters, so a ragged batch of problems is one launch per layer.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace slista {
+namespace tcw {
+
+using namespace tc;
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int NT = 512;                          // 16 warps
+constexpr int TILE_A = BM * BK * 2;              // one BF16 A chunk (16 KB)
+constexpr int TILE_B = BN * BK * 2;              // one BF16 B tile (32 KB)
+constexpr int TILE_PAIR = 2 * TILE_B;            // hi then lo, as stored in the workspace
+constexpr int REFRESH = 8;
+constexpr uint32_t IDESC = idesc_bf16(BM, BN);
+
+enum Mode { FWD = 0, ADJ = 1 };
+
+template <bool SPLIT>
+struct WCfg {
+    static constexpr int OFF_B = SPLIT ? 2 * TILE_A : TILE_A;
+    static constexpr int STAGE = OFF_B + (SPLIT ? 2 * TILE_B : TILE_B);
+    static constexpr uint32_t BBYTES = SPLIT ? 2 * TILE_B : TILE_B;
+    static constexpr int SMEM = 2 * STAGE + 1024;
+};
+
+int read_and_clear_flag(cudaStream_t st)
+{
+    int h = 0;
+    SLISTA_CUDA_TRY(cudaMemcpyFromSymbolAsync(&h, tc_flag, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+    SLISTA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h != 0) {
+        const int zero = 0;
+        SLISTA_CUDA_TRY(cudaMemcpyToSymbolAsync(tc_flag, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+        SLISTA_CUDA_TRY(cudaStreamSynchronize(st));
+        return fail(SLISTA_ERR_TIMEOUT, "a wide-layer kernel's bounded wait expired (device flag %d)", h);
+    }
+    return SLISTA_OK;
+}
+
+// One layer of one problem.
+struct WLayer {
+    const uint8_t *Bt;        // split B tiles [column block][K chunk] (hi, lo)
+    const float *C;           // N x m
+    const float *Zin, *Gin;   // FWD: state at layer t (Zin == nullptr: z = 0, g = C); ADJ: Gin = G
+    float *Zout, *Gout;       // FWD: state at layer t+1 (either may be nullptr); ADJ: Gout = next G
+    const uint32_t *mask_in;  // ADJ: support of z^(t+1)
+    uint32_t *mask_out;       // FWD: support of z^(t+1) (nullable)
+    const float *Zq, *Gq;     // ADJ: z^(t+1) and g^(t) of the forward trajectory (Gq == nullptr: C)
+    float *partial;           // ADJ: per-item sums of dalpha_t (indexed by item within the problem)
+    const float *alpha;       // step sizes (nullptr: 1 / L)
+    const double *Lp;
+    int t, m, N, refresh, skip_mma;
+    float lam;
+};
+
+template <int NP>
+struct WBatch {
+    int nprob;
+    int base[NP + 1];  // first work item of each problem; base[nprob] = total
+    WLayer L[NP];
+};
+
+__host__ __device__ inline int n_colblocks(int m) { return (m + BN - 1) / BN; }
+__host__ __device__ inline int n_kchunks(int m) { return (m + BK - 1) / BK; }
+inline int n_items(int m, int N) { return ceil_div(N, BM) * n_colblocks(m); }
+
+// 16 consecutive entries (columns k0..k0+15) of row `row` of an N x m FP32
+// matrix, zero outside the matrix or when M is null.
+__device__ __forceinline__ void load16(const float *__restrict__ M, int row, bool ok, int m, int k0, float (&v)[16])
+{
+    if (M != nullptr && ok && (m & 3) == 0) {
+        const float4 *src = reinterpret_cast<const float4 *>(M + (size_t)row * m + k0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 x = k0 + 4 * q < m ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[4 * q + 0] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            v[j] = (M != nullptr && ok && k0 + j < m) ? __ldg(M + (size_t)row * m + k0 + j) : 0.0f;
+    }
+}
+
+// 16 bits of a support mask (columns k0..k0+15, k0 a multiple of 16), zero past m.
+__device__ __forceinline__ uint32_t mask16(const uint32_t *__restrict__ words, int row, bool ok, int m, int k0)
+{
+    if (!ok || k0 >= m) return 0u;
+    const int W = (m + 31) / 32;
+    uint32_t b = (__ldg(words + (size_t)row * W + (k0 >> 5)) >> (k0 & 31)) & 0xffffu;
+    if (k0 + 16 > m) b &= (1u << (m - k0)) - 1u;
+    return b;
+}
+
+// Row `row` (0..127), codes kl..kl+15 (kl a multiple of 16) of an A chunk in
+// the K-major 128-byte-swizzled layout: two 16-byte units per part.
+template <bool SPLIT>
+__device__ __forceinline__ void store_a16(uint8_t *stage, int row, int kl, const float (&v)[16])
+{
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        hi[j] = *reinterpret_cast<const uint32_t *>(&h2);
+        if (SPLIT) {
+            const float2 hf = __bfloat1622float2(h2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+            lo[j] = *reinterpret_cast<const uint32_t *>(&l2);
+        }
+    }
+    const int rbase = (row >> 3) * 1024 + (row & 7) * 128;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int unit = (kl >> 3) + u;
+        const int off = rbase + ((unit ^ (row & 7)) << 4);
+        *reinterpret_cast<uint4 *>(stage + off) = make_uint4(hi[4 * u], hi[4 * u + 1], hi[4 * u + 2], hi[4 * u + 3]);
+        if (SPLIT)
+            *reinterpret_cast<uint4 *>(stage + TILE_A + off) =
+                make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]);
+    }
+}
+
+__device__ __forceinline__ float st_f(float u, float thr) { return copysignf(fmaxf(fabsf(u) - thr, 0.0f), u); }
+
+// ---------------------------------------------------------------------------
+// Prep: B (m x m FP32) -> tiles [cb][kc] of BN x BK (B_hi, then B_lo), each
+// K-major with the 128-byte swizzle; zero past m.
+// ---------------------------------------------------------------------------
+__global__ void split_tiles_kernel(const float *__restrict__ B, int m, uint8_t *__restrict__ out)
+{
+    const int ncb = n_colblocks(m), nkc = n_kchunks(m);
+    const long long KP = (long long)nkc * BK;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)ncb * BN * KP) return;
+    const int n = (int)(idx / KP), k = (int)(idx % KP);
+    const int cb = n / BN, nl = n % BN, kc = k / BK, kl = k % BK;
+    const float v = (n < m && k < m) ? __ldg(B + (size_t)n * m + k) : 0.0f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const uint32_t off = (uint32_t)((nl >> 3) * 1024 + (nl & 7) * 128 + (((kl >> 3) ^ (nl & 7)) << 4) + (kl & 7) * 2);
+    uint8_t *tile = out + ((size_t)cb * nkc + kc) * TILE_PAIR;
+    *reinterpret_cast<__nv_bfloat16 *>(tile + off) = hi;
+    *reinterpret_cast<__nv_bfloat16 *>(tile + TILE_B + off) = lo;
+}
+
+// ---------------------------------------------------------------------------
+// The layer kernel.
+// ---------------------------------------------------------------------------
+template <bool SPLIT, int MODE, int NP>
+__global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant__ WBatch<NP> P)
+{
+    using CF = WCfg<SPLIT>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[4];  // full[2] (B tile landed), done[2] (MMAs of the stage retired)
+    __shared__ uint32_t tmem_slot;
+    __shared__ float red[NT / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    int p = 0;
+    while (p + 1 < P.nprob && (int)blockIdx.x >= P.base[p + 1]) ++p;
+    const WLayer &L = P.L[p];
+    const int m = L.m, N = L.N;
+    const int ncb = n_colblocks(m), nkc = n_kchunks(m);
+    const int local = (int)blockIdx.x - P.base[p];
+    const int row0 = (local / ncb) * BM, col0 = (local % ncb) * BN;
+    const bool do_mma = !L.skip_mma;
+
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]);
+    if (tid == 0) {
+        for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    const float a = L.alpha ? __ldg(L.alpha + L.t) : (float)(1.0 / __ldg(L.Lp));
+    const float thr = a * L.lam;
+    const uint8_t *Bcol = L.Bt + (size_t)(col0 / BN) * nkc * TILE_PAIR;
+    const float *Zs = L.Zin;
+    const float *Gs = (MODE == FWD && L.Zin == nullptr) ? L.C : L.Gin;
+
+    // producer state (thread 0): pending bulk copies and the phases of full[s]
+    uint32_t pend = 0u, fph = 0u;
+    bool bad = false;     // thread 0: a wait for a B tile expired (folded into `failed` at the next barrier)
+    bool failed = false;  // uniform over the CTA
+    auto issue_b = [&](int kc) {
+        const int s = kc & 1;
+        mbar_arrive_expect_tx(full0 + 8 * s, CF::BBYTES);
+        bulk_g2s(sbase + s * CF::STAGE + CF::OFF_B, Bcol + (size_t)kc * TILE_PAIR, CF::BBYTES, full0 + 8 * s);
+        pend |= 1u << s;
+    };
+    auto wait_b = [&](int s, int code) {
+        const bool ok = mbar_wait(full0 + 8 * s, (fph >> s) & 1u, code);
+        fph ^= 1u << s;
+        pend &= ~(1u << s);
+        return ok;
+    };
+
+    if (do_mma) {
+        if (tid == 0) {
+            issue_b(0);
+            if (nkc > 1) issue_b(1);
+        }
+        const int prow = tid >> 2, pk = (tid & 3) * 16;  // producer: one row, 16 codes of the chunk
+        const int grow = row0 + prow;
+        const bool rok = grow < N;
+#pragma unroll 1
+        for (int kc = 0; kc < nkc; ++kc) {
+            const int s = kc & 1;
+            uint8_t *stage = smem + s * CF::STAGE;
+            if (kc >= 2) {  // stage s is free once the MMAs of chunk kc - 2 have retired
+                const bool ok = mbar_wait(done0 + 8 * s, ((kc >> 1) - 1) & 1, 21);
+                failed = __syncthreads_or(!ok || bad) != 0;
+                if (failed) break;
+                tc_fence_after();
+                if (tid == 0) issue_b(kc);
+            }
+            // --- A operand of chunk kc: 16 codes of row prow
+            const int k0 = kc * BK + pk;
+            float v[16];
+            if (MODE == FWD) {
+                float z[16], g[16];
+                load16(Zs, grow, rok, m, k0, z);
+                load16(Gs, grow, rok, m, k0, g);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float zn = st_f(fmaf(a, g[j], z[j]), thr);
+                    v[j] = L.refresh ? -zn : z[j] - zn;
+                }
+            } else {
+                float G[16];
+                load16(L.Gin, grow, rok, m, k0, G);
+                const uint32_t bits = mask16(L.mask_in, grow, rok, m, k0);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = ((bits >> j) & 1u) ? G[j] : 0.0f;
+            }
+            store_a16<SPLIT>(stage, prow, pk, v);
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                bad |= !wait_b(s, 22);
+                tc_fence_after();
+                const uint32_t a_base = sbase + s * CF::STAGE, b_base = a_base + CF::OFF_B;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint64_t ad = sdesc_sw128(a_base + kk * 32);
+                    const uint64_t bd = sdesc_sw128(b_base + kk * 32);
+                    mma_ss(tmem, ad, bd, IDESC, (kc | kk) ? 1u : 0u);
+                    if (SPLIT) {
+                        mma_ss(tmem, sdesc_sw128(a_base + TILE_A + kk * 32), bd, IDESC, 1u);
+                        mma_ss(tmem, ad, sdesc_sw128(b_base + TILE_B + kk * 32), IDESC, 1u);
+                    }
+                }
+                mma_commit(done0 + 8 * s);
+            }
+        }
+        if (!failed) {  // the last commit fires once every MMA issued before it has retired
+            const int kl = nkc - 1;
+            const bool ok = mbar_wait(done0 + 8 * (kl & 1), (kl >> 1) & 1, 23);
+            failed = __syncthreads_or(!ok || bad) != 0;
+        }
+        tc_fence_after();
+    }
+
+    // --- epilogue: warp w reads TMEM lanes 32 (w % 4).. (tile rows) and
+    // columns 64 (w / 4).. of the block, 16 at a time
+    const int q = warp & 3, cg = warp >> 2;
+    const int erow = row0 + 32 * q + lane;
+    const bool eok = erow < N;
+    const int W = (m + 31) / 32;
+    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cg * 64);
+    float part = 0.0f;
+    uint32_t word = 0u;
+#pragma unroll 1
+    for (int pc = 0; pc < 4; ++pc) {
+        const int c = col0 + cg * 64 + pc * 16;
+        float acc[16];
+        if (do_mma && !failed) {
+            tmem_ld16(tl + pc * 16, acc);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
+        }
+        if (failed || !eok || c >= m) continue;
+        if (MODE == FWD) {
+            float z[16], g[16];
+            load16(Zs, erow, true, m, c, z);
+            load16(Gs, erow, true, m, c, g);
+            float cv[16];
+            if (L.refresh && L.Gout) load16(L.C, erow, true, m, c, cv);
+            uint32_t bits = 0u;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float zn = st_f(fmaf(a, g[j], z[j]), thr);
+                z[j] = zn;
+                g[j] = (L.refresh ? cv[j] : g[j]) + acc[j];
+                bits |= (uint32_t)(zn != 0.0f) << j;
+            }
+            if (c + 16 > m) bits &= (1u << (m - c)) - 1u;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (c + j < m) {
+                    if (L.Zout) L.Zout[(size_t)erow * m + c + j] = z[j];
+                    if (L.Gout) L.Gout[(size_t)erow * m + c + j] = g[j];
+                }
+            }
+            word |= bits << (16 * (pc & 1));
+            if (pc & 1) {
+                if (L.mask_out) L.mask_out[(size_t)erow * W + ((c - 16) >> 5)] = word;
+                word = 0u;
+            } else if (c + 16 >= m && L.mask_out) {  // last piece of the row, odd count of pieces
+                L.mask_out[(size_t)erow * W + (c >> 5)] = word;
+            }
+        } else {
+            float G[16], gq[16], zq[16];
+            load16(L.Gin, erow, true, m, c, G);
+            load16(L.Gq ? L.Gq : L.C, erow, true, m, c, gq);
+            load16(L.Zq, erow, true, m, c, zq);
+            const uint32_t bits = mask16(L.mask_in, erow, true, m, c);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float h = ((bits >> j) & 1u) ? G[j] : 0.0f;
+                const float qv = gq[j] - L.lam * (float)((zq[j] > 0.0f) - (zq[j] < 0.0f));
+                part = fmaf(h, qv, part);
+                G[j] = fmaf(-a, acc[j], h);
+            }
+            if (L.Gout)
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c + j < m) L.Gout[(size_t)erow * m + c + j] = G[j];
+        }
+    }
+    if (MODE == ADJ) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
+        if (tid == 0) {
+            float sum = 0.0f;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) sum += red[w];
+            L.partial[local] = sum;
+        }
+    }
+
+    // --- teardown: drain pending bulk copies, release tensor memory
+    if (tid == 0)
+        for (int s = 0; s < 2; ++s)
+            if ((pend >> s) & 1u) wait_b(s, 24);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+// G_T = gZ (if given) or dF/dz^(T) = B z - c + lam sign(z) = -g^(T) + lam sign(z^(T)).
+__global__ void adjoint_seed_kernel(const float *__restrict__ ZT, const float *__restrict__ GT,
+                                    const float *__restrict__ gZ, size_t n, float lam, float *__restrict__ G)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (gZ) {
+        G[i] = __ldg(gZ + i);
+    } else {
+        const float z = __ldg(ZT + i);
+        G[i] = -__ldg(GT + i) + lam * (float)((z > 0.0f) - (z < 0.0f));
+    }
+}
+
+// dalpha[t] = sum of partial[t][0..nitem), FP64, fixed order (one warp per layer).
+__global__ void reduce_items_kernel(const float *__restrict__ partial, int nitem, int T, float *__restrict__ dalpha)
+{
+    const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    if (t >= T) return;
+    double s = 0.0;
+    for (int b = lane; b < nitem; b += 32) s += (double)partial[(size_t)t * nitem + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) dalpha[t] = (float)s;
+}
+
+// ---------------------------------------------------------------------------
+// Host side: every entry point runs a batch of problems (one problem is a
+// batch of one); per layer, one launch covers the work items of up to MAXP
+// problems.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int MAXP = 64;
+
+size_t tiles_bytes(int m) { return (size_t)n_colblocks(m) * n_kchunks(m) * TILE_PAIR; }
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+size_t state_bytes(int m, int N) { return align256(sizeof(float) * (size_t)N * m); }
+
+int split_tiles(const float *B, int m, uint8_t *out, cudaStream_t st)
+{
+    const long long total = (long long)n_colblocks(m) * BN * n_kchunks(m) * BK;
+    split_tiles_kernel<<<(unsigned)ceil_div(total, 256), 256, 0, st>>>(B, m, out);
+    return check_launch("split_tiles_kernel");
+}
+
+template <bool SPLIT, int MODE, int NP>
+int launch_chunk(const WLayer *Ls, int count, cudaStream_t st)
+{
+    WBatch<NP> P{};
+    P.nprob = count;
+    P.base[0] = 0;
+    for (int i = 0; i < count; ++i) {
+        P.L[i] = Ls[i];
+        P.base[i + 1] = P.base[i] + n_items(Ls[i].m, Ls[i].N);
+    }
+    if (P.base[count] == 0) return SLISTA_OK;
+    auto k = tcw_layer_kernel<SPLIT, MODE, NP>;
+    SLISTA_CUDA_TRY(allow_smem(k, WCfg<SPLIT>::SMEM));
+    k<<<P.base[count], NT, WCfg<SPLIT>::SMEM, st>>>(P);
+    return check_launch(MODE == FWD ? "tcw_layer_kernel (forward)" : "tcw_layer_kernel (adjoint)");
+}
+
+// One layer for every problem of the batch: launches of at most MAXP problems.
+template <int MODE>
+int launch_layers(const std::vector<WLayer> &Ls, bool split, cudaStream_t st)
+{
+    for (size_t i = 0; i < Ls.size(); i += MAXP) {
+        const int c = (int)std::min(Ls.size() - i, (size_t)MAXP);
+        int rc;
+        if (c == 1)
+            rc = split ? launch_chunk<true, MODE, 1>(&Ls[i], 1, st) : launch_chunk<false, MODE, 1>(&Ls[i], 1, st);
+        else
+            rc = split ? launch_chunk<true, MODE, MAXP>(&Ls[i], c, st)
+                       : launch_chunk<false, MODE, MAXP>(&Ls[i], c, st);
+        if (rc) return rc;
+    }
+    return SLISTA_OK;
+}
+
+bool refresh_at(int t, int T, int K, bool ckpt)
+{
+    return (ckpt && K < T) ? ((t + 1) % K == 0) : ((t + 1) % REFRESH == 0);
+}
+
+size_t fwd_bytes_one(int m, int N) { return align256(tiles_bytes(m)) + 4 * state_bytes(m, N); }
+
+size_t bwd_bytes_one(int m, int N, int T, int K)
+{
+    return align256(tiles_bytes(m)) + (size_t)(2 * K + 4) * state_bytes(m, N) +
+           align256(sizeof(float) * (size_t)T * n_items(m, N));
+}
+
+}  // namespace
+
+bool supported(int m) { return m >= 1 && m <= 1024; }
+
+size_t forward_ws_bytes(int m, int N) { return fwd_bytes_one(m, N); }
+
+size_t backward_ws_bytes(int m, int N, int T, int K) { return bwd_bytes_one(m, N, T, K); }
+
+size_t forward_batch_ws_bytes(const Problem *P, int count)
+{
+    size_t b = 0;
+    for (int i = 0; i < count; ++i) b += fwd_bytes_one(P[i].m, P[i].N);
+    return b;
+}
+
+size_t backward_batch_ws_bytes(const Problem *P, int count, int T, int K)
+{
+    size_t b = 0;
+    for (int i = 0; i < count; ++i) b += bwd_bytes_one(P[i].m, P[i].N, T, K < T ? K : T);
+    return b;
+}
+
+int forward_batch(const Problem *P, int count, int T, int K, int prec, void *ws, cudaStream_t st)
+{
+    const bool split = prec == SLISTA_PREC_BF16X3;
+    struct Buf {
+        uint8_t *tiles;
+        float *buf[4];
+        const float *Zc, *Gc;
+        int pp;
+        bool ck;
+    };
+    std::vector<Buf> bb(count);
+    uint8_t *cur = reinterpret_cast<uint8_t *>(ws);
+    for (int i = 0; i < count; ++i) {
+        Buf &b = bb[i];
+        b.tiles = cur;
+        cur += align256(tiles_bytes(P[i].m));
+        for (int j = 0; j < 4; ++j) {
+            b.buf[j] = reinterpret_cast<float *>(cur);
+            cur += state_bytes(P[i].m, P[i].N);
+        }
+        b.Zc = b.Gc = nullptr;
+        b.pp = 0;
+        b.ck = P[i].ckpt != nullptr && K >= 1 && K < T;
+        int rc = split_tiles(P[i].B, P[i].m, b.tiles, st);
+        if (rc) return rc;
+        if (T == 0 && P[i].N > 0)
+            SLISTA_CUDA_TRY(cudaMemsetAsync(P[i].Z, 0, sizeof(float) * (size_t)P[i].N * P[i].m, st));
+    }
+    std::vector<WLayer> Ls;
+    for (int t = 0; t < T; ++t) {
+        Ls.clear();
+        for (int i = 0; i < count; ++i) {
+            const Problem &q = P[i];
+            if (q.N == 0) continue;
+            Buf &b = bb[i];
+            const int W = (q.m + 31) / 32;
+            WLayer L{};
+            L.Bt = b.tiles;
+            L.C = q.C;
+            L.Zin = b.Zc;
+            L.Gin = b.Gc;
+            L.alpha = q.alpha;
+            L.Lp = q.L;
+            L.t = t;
+            L.m = q.m;
+            L.N = q.N;
+            L.lam = q.lam;
+            L.refresh = refresh_at(t, T, K, b.ck);
+            L.mask_out = q.masks ? q.masks + (size_t)t * q.N * W : nullptr;
+            if (t == T - 1) {
+                L.Zout = q.Z;
+                L.Gout = nullptr;
+                L.skip_mma = 1;  // g^(T) is not needed
+            } else if (b.ck && (t + 1) % K == 0) {
+                float *slot = q.ckpt + (size_t)((t + 1) / K - 1) * 2 * q.N * q.m;
+                L.Zout = slot;
+                L.Gout = slot + (size_t)q.N * q.m;
+            } else {
+                L.Zout = b.buf[2 * b.pp];
+                L.Gout = b.buf[2 * b.pp + 1];
+                b.pp ^= 1;
+            }
+            b.Zc = L.Zout;
+            b.Gc = L.Gout;
+            Ls.push_back(L);
+        }
+        int rc = launch_layers<FWD>(Ls, split, st);
+        if (rc) return rc;
+    }
+    return SLISTA_OK;
+}
+
+int backward_batch(const Problem *P, int count, int T, int Kin, int prec, void *ws, cudaStream_t st)
+{
+    const bool split = prec == SLISTA_PREC_BF16X3;
+    const int K = Kin < T ? Kin : T;
+    const bool ck = K < T;
+    struct Buf {
+        uint8_t *tiles, *seg;
+        float *Gb[2];
+        float *partial;
+        size_t state;
+        int nitem, gcur;
+        float *segZ(int i) const { return reinterpret_cast<float *>(seg + (size_t)(2 * i) * state); }
+        float *segG(int i) const { return reinterpret_cast<float *>(seg + (size_t)(2 * i + 1) * state); }
+    };
+    std::vector<Buf> bb(count);
+    uint8_t *cur = reinterpret_cast<uint8_t *>(ws);
+    for (int i = 0; i < count; ++i) {
+        Buf &b = bb[i];
+        const Problem &q = P[i];
+        b.state = state_bytes(q.m, q.N);
+        b.tiles = cur;
+        cur += align256(tiles_bytes(q.m));
+        b.seg = cur;
+        cur += (size_t)(2 * K + 2) * b.state;
+        b.Gb[0] = reinterpret_cast<float *>(cur);
+        b.Gb[1] = reinterpret_cast<float *>(cur + b.state);
+        cur += 2 * b.state;
+        b.partial = reinterpret_cast<float *>(cur);
+        b.nitem = n_items(q.m, q.N);
+        cur += align256(sizeof(float) * (size_t)T * b.nitem);
+        b.gcur = 0;
+        int rc = split_tiles(q.B, q.m, b.tiles, st);
+        if (rc) return rc;
+        if (q.N == 0) SLISTA_CUDA_TRY(cudaMemsetAsync(q.dalpha, 0, sizeof(float) * T, st));
+    }
+    const int nseg = ceil_div(T, K);
+    std::vector<WLayer> Ls;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int t0 = sg * K, t1 = t0 + K < T ? t0 + K : T;
+        const bool lastseg = sg == nseg - 1;
+        auto Z0 = [&](int i) -> const float * {
+            return t0 > 0 ? P[i].ckpt + (size_t)(t0 / K - 1) * 2 * P[i].N * P[i].m : nullptr;
+        };
+        auto G0 = [&](int i) -> const float * {
+            return t0 > 0 ? P[i].ckpt + (size_t)(t0 / K - 1) * 2 * P[i].N * P[i].m + (size_t)P[i].N * P[i].m
+                          : nullptr;
+        };
+        // recompute layers t0 .. t1-1 with the forward's arithmetic
+        for (int t = t0; t < t1; ++t) {
+            const int j = t - t0;
+            Ls.clear();
+            for (int i = 0; i < count; ++i) {
+                const Problem &q = P[i];
+                if (q.N == 0) continue;
+                const Buf &b = bb[i];
+                WLayer L{};
+                L.Bt = b.tiles;
+                L.C = q.C;
+                L.Zin = j == 0 ? Z0(i) : b.segZ(j);
+                L.Gin = j == 0 ? G0(i) : b.segG(j);
+                L.Zout = b.segZ(j + 1);
+                const bool need_g = (t + 1 < t1) || (lastseg && t + 1 == T);
+                L.Gout = need_g ? b.segG(j + 1) : nullptr;
+                L.skip_mma = need_g ? 0 : 1;
+                L.alpha = q.alpha;
+                L.t = t;
+                L.m = q.m;
+                L.N = q.N;
+                L.lam = q.lam;
+                L.refresh = refresh_at(t, T, K, ck);
+                Ls.push_back(L);
+            }
+            int rc = launch_layers<FWD>(Ls, split, st);
+            if (rc) return rc;
+        }
+        if (lastseg) {
+            const int n = t1 - t0;
+            for (int i = 0; i < count; ++i) {
+                const Problem &q = P[i];
+                if (q.N == 0) continue;
+                Buf &b = bb[i];
+                const size_t nm = (size_t)q.N * q.m;
+                adjoint_seed_kernel<<<(unsigned)ceil_div((long long)nm, 256), 256, 0, st>>>(
+                    b.segZ(n), b.segG(n), q.gZ, nm, q.lam, b.Gb[b.gcur]);
+                int rc = check_launch("adjoint_seed_kernel");
+                if (rc) return rc;
+            }
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            const int j = t - t0;
+            Ls.clear();
+            for (int i = 0; i < count; ++i) {
+                const Problem &q = P[i];
+                if (q.N == 0) continue;
+                Buf &b = bb[i];
+                const int W = (q.m + 31) / 32;
+                WLayer L{};
+                L.Bt = b.tiles;
+                L.C = q.C;
+                L.Gin = b.Gb[b.gcur];
+                L.Gout = t > 0 ? b.Gb[b.gcur ^ 1] : nullptr;
+                L.skip_mma = t > 0 ? 0 : 1;
+                L.mask_in = q.masks + (size_t)t * q.N * W;
+                L.Zq = b.segZ(j + 1);
+                L.Gq = j == 0 ? G0(i) : b.segG(j);  // nullptr at t = 0: g^(0) = c
+                L.partial = b.partial + (size_t)t * b.nitem;
+                L.alpha = q.alpha;
+                L.t = t;
+                L.m = q.m;
+                L.N = q.N;
+                L.lam = q.lam;
+                Ls.push_back(L);
+                b.gcur ^= 1;
+            }
+            int rc = launch_layers<ADJ>(Ls, split, st);
+            if (rc) return rc;
+        }
+    }
+    for (int i = 0; i < count; ++i) {
+        if (P[i].N == 0) continue;
+        reduce_items_kernel<<<ceil_div(T, 8), 256, 0, st>>>(bb[i].partial, bb[i].nitem, T, P[i].dalpha);
+        int rc = check_launch("reduce_items_kernel");
+        if (rc) return rc;
+    }
+    return SLISTA_OK;
+}
+
+int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st)
+{
+    Problem q{};
+    q.B = a.B;
+    q.C = a.C;
+    q.m = a.m;
+    q.N = a.N;
+    q.lam = a.lam;
+    q.alpha = a.alpha;
+    q.L = a.L;
+    q.Z = a.Z;
+    q.masks = a.masks;
+    q.ckpt = a.ckpt;
+    return forward_batch(&q, 1, a.T, a.ckpt_every, prec, ws, st);
+}
+
+int launch_backward(const BwdArgs &a, int prec, void *ws, cudaStream_t st)
+{
+    Problem q{};
+    q.B = a.B;
+    q.C = a.C;
+    q.m = a.m;
+    q.N = a.N;
+    q.lam = a.lam;
+    q.alpha = a.alpha;
+    q.masks = const_cast<uint32_t *>(a.masks);
+    q.ckpt = const_cast<float *>(a.ckpt);
+    q.gZ = a.gZ;
+    q.dalpha = a.dalpha;
+    return backward_batch(&q, 1, a.T, a.ckpt_every, prec, ws, st);
+}
+
+}  // namespace tcw
+}  // namespace slista
