@@ -4,6 +4,9 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -37,6 +40,29 @@ int check_launch(const char *what)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(SLISTA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
     return SLISTA_OK;
+}
+
+namespace {
+std::mutex g_smem_mu;
+std::map<std::pair<const void *, int>, size_t> g_smem;  // (kernel, device) -> bytes opted in
+}  // namespace
+
+bool smem_known(const void *kernel, size_t bytes)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    const auto it = g_smem.find({kernel, dev});
+    return it != g_smem.end() && it->second >= bytes;
+}
+
+void smem_record(const void *kernel, size_t bytes)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    size_t &v = g_smem[{kernel, dev}];
+    if (bytes > v) v = bytes;
 }
 
 int num_sms()

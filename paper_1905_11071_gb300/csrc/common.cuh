@@ -31,11 +31,22 @@ inline int pad32(int m) { return ((m + 31) / 32) * 32; }
 // Number of streaming multiprocessors of the current device (cached).
 int num_sms();
 
-// Dynamic shared memory opt-in for a kernel (idempotent per kernel).
+// Whether `kernel` was already opted in to `bytes` of dynamic shared memory
+// on the current device (smem_known), and the record of an opt-in.
+bool smem_known(const void *kernel, size_t bytes);
+void smem_record(const void *kernel, size_t bytes);
+
+// Dynamic shared memory opt-in for a kernel.  Done once per kernel and
+// device, so that calls made later under stream capture issue no attribute
+// change.
 template <class K>
 inline cudaError_t allow_smem(K kernel, size_t bytes)
 {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const void *fn = reinterpret_cast<const void *>(kernel);
+    if (smem_known(fn, bytes)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) smem_record(fn, bytes);
+    return e;
 }
 
 }  // namespace slista
