@@ -37,7 +37,14 @@ namespace {
 
 constexpr int KMAX = 64;  // largest matrix a warp solves in its own buffer
 constexpr int JM = eig::LANCZOS_JMAX;
-constexpr int SOLVE_WARPS = 8;
+// The solve kernel's block: A_WARPS warps with a shared-memory buffer for
+// B_SS or D_S D_S^T (supports of more than SMALL_K indices first, then the
+// small ones), and S_WARPS warps that solve supports of at most SMALL_K
+// indices with the matrix in registers (one row per lane).
+constexpr int A_WARPS = 8;
+constexpr int S_WARPS = 8;
+constexpr int SMALL_K = 32;
+constexpr int NCLS = 3;  // list classes: |S| > KMAX, SMALL_K < |S| <= KMAX, |S| <= SMALL_K
 constexpr int STEP_NB = 32;
 
 constexpr int GCOLS = 8;  // D_S columns staged per round in gram_ds
@@ -57,9 +64,9 @@ struct OistaWs {
     uint32_t *Scur, *Sprev;   // N x W: supp(z^(t)), support of the cached L_S
     int *flag;                // N: 1 if condition (star) fails at the current layer
     int *valid;               // N: LSv holds L_{Sprev}
-    int *list;                // 2 x 2 x N: samples needing L_S, [layer parity][|S| > 64 ? 0 : 1]
-    int *counter;             // 2 x 2: list lengths, same indexing
-    int *qpos;                // T x 2: queue positions of the solve kernels
+    int *list;                // 2 x NCLS x N: samples needing L_S, [layer parity][class]
+    int *counter;             // 2 x NCLS: list lengths, same indexing
+    int *qpos;                // T x NCLS: queue positions of the solve kernels
     float *Dt;                // m x n: D transposed (columns of D contiguous), when D is given
     int N, W;
 
@@ -67,7 +74,8 @@ struct OistaWs {
     {
         const size_t W = (size_t)(m + 31) / 32;
         return sizeof(double) * (size_t)N + 2 * sizeof(float) * (size_t)N * m + 2 * sizeof(uint32_t) * N * W +
-               sizeof(int) * (6 * (size_t)N + 4 + 2 * (size_t)T) + sizeof(float) * (size_t)m * 256 + 16;
+               sizeof(int) * ((2 + 2 * NCLS) * (size_t)N + 2 * NCLS + NCLS * (size_t)T) +
+               sizeof(float) * (size_t)m * 256 + 16;
     }
     static OistaWs carve(void *ws, int m, int N, int T)
     {
@@ -89,11 +97,11 @@ struct OistaWs {
         o.valid = reinterpret_cast<int *>(p);
         p += sizeof(int) * (size_t)N;
         o.list = reinterpret_cast<int *>(p);
-        p += sizeof(int) * 4 * (size_t)N;
+        p += sizeof(int) * 2 * NCLS * (size_t)N;
         o.counter = reinterpret_cast<int *>(p);
-        p += sizeof(int) * 4;
+        p += sizeof(int) * 2 * NCLS;
         o.qpos = reinterpret_cast<int *>(p);
-        p += sizeof(int) * 2 * (size_t)T;
+        p += sizeof(int) * NCLS * (size_t)T;
         o.Dt = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
         o.N = N;
         o.W = (int)W;
@@ -146,47 +154,52 @@ __device__ bool gather_bss(const float *__restrict__ B, int m, const int *idx, i
 
 // G = D_S D_S^T (n x n, n <= KMAX) into A, accumulated over the k support
 // columns; Dt is D transposed, so column j of D is the contiguous row j of Dt.
+// Lane a owns rows a and a + 32; the 64 columns go in four passes of 16.
 __device__ void gram_ds(const float *__restrict__ Dt, int n, const int *idx, int k, float *A, int lda, float *col)
 {
     const int lane = threadIdx.x & 31;
-    float acc[KMAX / 32][KMAX];  // rows lane and lane + 32 of G
-#pragma unroll
-    for (int r = 0; r < KMAX / 32; ++r)
-#pragma unroll
-        for (int b = 0; b < KMAX; ++b) acc[r][b] = 0.0f;
+    constexpr int PC = 16;  // columns per pass
 #pragma unroll 1
-    for (int s0 = 0; s0 < k; s0 += GCOLS) {
-        float x[GCOLS][KMAX / 32];
+    for (int b0 = 0; b0 < n; b0 += PC) {
+        float acc[KMAX / 32][PC];
 #pragma unroll
-        for (int c = 0; c < GCOLS; ++c)
+        for (int r = 0; r < KMAX / 32; ++r)
 #pragma unroll
-            for (int r = 0; r < KMAX / 32; ++r) {
-                const int a = lane + 32 * r;
-                x[c][r] = (s0 + c < k && a < n) ? __ldg(Dt + (size_t)idx[s0 + c] * n + a) : 0.0f;
-            }
-        __syncwarp();
+            for (int b = 0; b < PC; ++b) acc[r][b] = 0.0f;
+#pragma unroll 1
+        for (int s0 = 0; s0 < k; s0 += GCOLS) {
+            float x[GCOLS][KMAX / 32];
 #pragma unroll
-        for (int c = 0; c < GCOLS; ++c)
+            for (int c = 0; c < GCOLS; ++c)
 #pragma unroll
-            for (int r = 0; r < KMAX / 32; ++r) col[c * KMAX + lane + 32 * r] = x[c][r];
-        __syncwarp();
+                for (int r = 0; r < KMAX / 32; ++r) {
+                    const int a = lane + 32 * r;
+                    x[c][r] = (s0 + c < k && a < n) ? __ldg(Dt + (size_t)idx[s0 + c] * n + a) : 0.0f;
+                }
+            __syncwarp();
 #pragma unroll
-        for (int c = 0; c < GCOLS; ++c) {
+            for (int c = 0; c < GCOLS; ++c)
 #pragma unroll
-            for (int r = 0; r < KMAX / 32; ++r) {
-                const float da = col[c * KMAX + lane + 32 * r];
+                for (int r = 0; r < KMAX / 32; ++r) col[c * KMAX + lane + 32 * r] = x[c][r];
+            __syncwarp();
 #pragma unroll
-                for (int b = 0; b < KMAX; ++b) acc[r][b] = fmaf(da, col[c * KMAX + b], acc[r][b]);
+            for (int c = 0; c < GCOLS; ++c) {
+#pragma unroll
+                for (int r = 0; r < KMAX / 32; ++r) {
+                    const float da = col[c * KMAX + lane + 32 * r];
+#pragma unroll
+                    for (int b = 0; b < PC; ++b) acc[r][b] = fmaf(da, col[c * KMAX + b0 + b], acc[r][b]);
+                }
             }
         }
-    }
 #pragma unroll
-    for (int r = 0; r < KMAX / 32; ++r) {
-        const int a = lane + 32 * r;
-        if (a < n)
+        for (int r = 0; r < KMAX / 32; ++r) {
+            const int a = lane + 32 * r;
+            if (a < n)
 #pragma unroll
-            for (int b = 0; b < KMAX; ++b)
-                if (b < n) A[a * lda + b] = acc[r][b];
+                for (int b = 0; b < PC; ++b)
+                    if (b0 + b < n) A[a * lda + b0 + b] = acc[r][b];
+        }
     }
     __syncwarp();
 }
@@ -280,28 +293,136 @@ __device__ inline float max_diag(const float *A, int lda, int k)
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident solver for 2 <= |S| <= SMALL_K: lane a holds row a of
+// B_SS (ar[]) and entry a of the Lanczos vectors; k steps of the three-term
+// recurrence give the tridiagonal T_k (similar to B_SS), whose largest
+// eigenvalue is bracketed by Sturm multisection (the method of
+// eig::lanczos_max_eig_warp for k <= 32).  A diagonal B_SS gives its largest
+// entry exactly.
+// ---------------------------------------------------------------------------
+struct WarpEigS {
+    float al[SMALL_K], be[SMALL_K], e2[SMALL_K];
+    int idx[SMALL_K];
+};
+
+__device__ double solve_small(const float *__restrict__ B, int m, const int *idx, int k, WarpEigS &ws)
+{
+    const int lane = threadIdx.x & 31;
+    const bool on = lane < k;
+    float ar[SMALL_K];
+    const float *brow = B + (size_t)idx[on ? lane : 0] * m;
+#pragma unroll
+    for (int b = 0; b < SMALL_K; ++b) ar[b] = (on && b < k) ? __ldg(brow + idx[b]) : 0.0f;
+    bool off = false;
+#pragma unroll
+    for (int b = 0; b < SMALL_K; ++b) off |= (b != lane) && (ar[b] != 0.0f);
+    if (!__any_sync(0xffffffffu, off)) {
+        float d = -INFINITY;
+#pragma unroll
+        for (int b = 0; b < SMALL_K; ++b)
+            if (b == lane && on) d = ar[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+        return (double)d;
+    }
+    float q = on ? eig::start_vector(lane) : 0.0f;
+    float nrm = q * q;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    q *= rsqrtf(nrm);
+    float qp = 0.0f, beta_prev = 0.0f;
+    int j = 0;
+#pragma unroll 1
+    for (; j < k; ++j) {
+        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+        for (int b = 0; b < SMALL_K; b += 4) {
+            s0 = fmaf(ar[b], __shfl_sync(0xffffffffu, q, b), s0);
+            s1 = fmaf(ar[b + 1], __shfl_sync(0xffffffffu, q, b + 1), s1);
+            s2 = fmaf(ar[b + 2], __shfl_sync(0xffffffffu, q, b + 2), s2);
+            s3 = fmaf(ar[b + 3], __shfl_sync(0xffffffffu, q, b + 3), s3);
+        }
+        const float sv = (s0 + s1) + (s2 + s3);
+        float alpha = sv * q;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+        const float w = on ? sv - alpha * q - beta_prev * qp : 0.0f;
+        float bb = w * w;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bb += __shfl_xor_sync(0xffffffffu, bb, o);
+        const float beta = sqrtf(bb);
+        if (lane == 0) {
+            ws.al[j] = alpha;
+            ws.be[j] = beta;
+        }
+        if (beta <= 1e-6f * fabsf(alpha) || j + 1 == k) {  // invariant subspace or full dimension
+            ++j;
+            break;
+        }
+        qp = q;
+        q = w * (1.0f / beta);
+        beta_prev = beta;
+    }
+    __syncwarp();
+    return (double)eig::tridiag_max_eig_warp(ws.al, ws.be, ws.e2, j);
+}
+
+// Takes the next sample of list class cls of layer t (one warp); -1 when empty.
+__device__ __forceinline__ int next_sample(const OistaWs &ws, int t, int cls)
+{
+    const int lane = threadIdx.x & 31;
+    const int par = t & 1;
+    int q = 0;
+    if (lane == 0) q = atomicAdd(ws.qpos + NCLS * t + cls, 1);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= ws.counter[NCLS * par + cls]) return -1;
+    return ws.list[(size_t)(NCLS * par + cls) * ws.N + q];
+}
+
+__device__ __forceinline__ void publish(const OistaWs &ws, int i, const uint32_t *words, double LS)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        ws.LSv[i] = LS;
+        ws.valid[i] = 1;
+    }
+    for (int w = lane; w < ws.W; w += 32) ws.Sprev[(size_t)i * ws.W + w] = words[w];
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
 // L_S for the samples listed for layer t.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SOLVE_WARPS * 32) oista_solve_kernel(
+__global__ void __launch_bounds__((A_WARPS + S_WARPS) * 32, 1) oista_solve_kernel(
     const float *__restrict__ B, bool have_D, int n, int m, const double *__restrict__ Lp, OistaWs ws, int t)
 {
     extern __shared__ float4 smem4[];
-    WarpEig &we = reinterpret_cast<WarpEig *>(smem4)[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const int par = t & 1;
-    if (blockIdx.x == 0 && threadIdx.x < 2) ws.counter[2 * (par ^ 1) + threadIdx.x] = 0;  // next layer's lists
+    if (blockIdx.x == 0 && threadIdx.x < NCLS) ws.counter[NCLS * (par ^ 1) + threadIdx.x] = 0;  // next layer's lists
     const double L = __ldg(Lp);
-#pragma unroll 1
-    for (int cls = 0; cls < 2; ++cls) {  // large supports first: they set the kernel's tail
-        const int count = ws.counter[2 * par + cls];
-        const int *list = ws.list + (size_t)(2 * par + cls) * ws.N;
+    if (warp >= A_WARPS) {
+        // small supports, matrix in registers
+        WarpEigS &we = reinterpret_cast<WarpEigS *>(reinterpret_cast<WarpEig *>(smem4) + A_WARPS)[warp - A_WARPS];
 #pragma unroll 1
         for (;;) {
-            int q = 0;
-            if (lane == 0) q = atomicAdd(ws.qpos + 2 * t + cls, 1);
-            q = __shfl_sync(0xffffffffu, q, 0);
-            if (q >= count) break;
-            const int i = list[q];
+            const int i = next_sample(ws, t, 2);
+            if (i < 0) break;
+            const uint32_t *words = ws.Scur + (size_t)i * ws.W;
+            const int k = support_indices(words, ws.W, we.idx);
+            const double LS = k == 0 ? L : k == 1 ? (double)__ldg(B + (size_t)we.idx[0] * m + we.idx[0])
+                                                  : solve_small(B, m, we.idx, k, we);
+            publish(ws, i, words, LS);
+        }
+        return;
+    }
+    WarpEig &we = reinterpret_cast<WarpEig *>(smem4)[warp];
+#pragma unroll 1
+    for (int cls = 0; cls < NCLS; ++cls) {  // large supports first: they set the kernel's tail
+#pragma unroll 1
+        for (;;) {
+            const int i = next_sample(ws, t, cls);
+            if (i < 0) break;
             const uint32_t *words = ws.Scur + (size_t)i * ws.W;
             const int k = support_indices(words, ws.W, we.idx);
             double LS;
@@ -323,12 +444,7 @@ __global__ void __launch_bounds__(SOLVE_WARPS * 32) oista_solve_kernel(
                 LS = lanczos_global(B, m, we.idx, k, we);
             }
             __syncwarp();
-            if (lane == 0) {
-                ws.LSv[i] = LS;
-                ws.valid[i] = 1;
-            }
-            for (int w = lane; w < ws.W; w += 32) ws.Sprev[(size_t)i * ws.W + w] = words[w];
-            __syncwarp();
+            publish(ws, i, words, LS);
         }
     }
 }
@@ -376,8 +492,8 @@ __device__ void prepare_next(const float (&z)[TL::RM][TL::RN], const float (&g)[
         if ((f == 0 || want_ls) && changed) {
             int k = 0;
             for (int w = 0; w < ws.W; ++w) k += __popc(Sw[r * ws.W + w]);
-            const int cls = (k > KMAX) ? 0 : 1;
-            const int li = 2 * (next & 1) + cls;
+            const int cls = (k > KMAX) ? 0 : (k > SMALL_K) ? 1 : 2;
+            const int li = NCLS * (next & 1) + cls;
             const int pos = atomicAdd(ws.counter + li, 1);
             ws.list[(size_t)li * ws.N + pos] = gr;
         }
@@ -485,7 +601,7 @@ int launch_oista_mp(const OistaArgs &a, void *wsp, cudaStream_t st)
         SLISTA_CUDA_TRY(cudaMemsetAsync(a.Z, 0, sizeof(float) * (size_t)a.N * a.m, st));
         return SLISTA_OK;
     }
-    SLISTA_CUDA_TRY(cudaMemsetAsync(ws.counter, 0, sizeof(int) * (4 + 2 * (size_t)a.T), st));  // counters, qpos
+    SLISTA_CUDA_TRY(cudaMemsetAsync(ws.counter, 0, sizeof(int) * (2 * NCLS + NCLS * (size_t)a.T), st));  // counters, qpos
     const bool have_D = a.D != nullptr && a.n >= 1 && a.n <= KMAX;
     if (have_D) {
         transpose_kernel<<<ceil_div((long long)a.n * a.m, 256), 256, 0, st>>>(a.D, a.n, a.m, ws.Dt);
@@ -493,7 +609,7 @@ int launch_oista_mp(const OistaArgs &a, void *wsp, cudaStream_t st)
         if (rc0) return rc0;
     }
     const size_t step_smem = StepSmem<MP>::bytes;
-    const size_t solve_smem = sizeof(WarpEig) * SOLVE_WARPS;
+    const size_t solve_smem = sizeof(WarpEig) * A_WARPS + sizeof(WarpEigS) * S_WARPS;
     auto kinit = oista_init_kernel<MP>;
     auto kstep = oista_step_kernel<MP>;
     SLISTA_CUDA_TRY(allow_smem(kinit, step_smem));
@@ -506,7 +622,8 @@ int launch_oista_mp(const OistaArgs &a, void *wsp, cudaStream_t st)
     if (rc) return rc;
     const int solve_grid = num_sms();
     for (int t = 0; t < a.T; ++t) {
-        oista_solve_kernel<<<solve_grid, SOLVE_WARPS * 32, solve_smem, st>>>(a.B, have_D, a.n, a.m, a.L, ws, t);
+        oista_solve_kernel<<<solve_grid, (A_WARPS + S_WARPS) * 32, solve_smem, st>>>(a.B, have_D, a.n, a.m, a.L, ws,
+                                                                                       t);
         rc = check_launch("oista_solve_kernel");
         if (rc) return rc;
         kstep<<<grid, NT, step_smem, st>>>(a.B, a.m, a.N, a.lam, a.L, ws, t, a.T, want_ls && t + 2 == a.T, a.Z,
