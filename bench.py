@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--N", type=int, default=10000)
     p.add_argument("--T", type=int, default=40)
     p.add_argument("--prec", default="bf16x3", help="layer precision: bf16x3 (tensor cores, default), bf16, fp32")
+    p.add_argument("--oista-prec", default="fp32", help="Oracle-ISTA layer precision: fp32 (CUDA cores), bf16x3 (tensor cores)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-samples", type=int, default=0, help="oracle sample size (0 = auto)")
@@ -172,7 +173,7 @@ def run_ours(args, rank, world, local_rank):
         "slista_fwd": 2 if tc else 1,                         # (B split) + layer kernel
         "objective": 1,
         "slista_bwd": (1 + 2 * nseg + 1) if tc else 2,        # (B split) + recompute/adjoint per segment + reduce
-        "oista_fwd": 1 + 1 + 2 * T,                           # transpose D, init, solve + step per layer
+        "oista_fwd": 1 + 1 + 2 * T + (1 if args.oista_prec != "fp32" else 0),  # transpose D, init, (B split), solve + step per layer
     }
 
     def step(evs=None):
@@ -190,7 +191,7 @@ def run_ours(args, rank, world, local_rank):
         da = api.slista_grad(g.B, g.C, lam, alpha, st, prec=args.prec)
         if evs is not None:
             evs[4].record(stream)
-        Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=D)
+        Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=D, prec=args.oista_prec)
         if evs is not None:
             evs[5].record(stream)
         return Z, F, gap, da, Zo
@@ -251,7 +252,7 @@ def run_ours(args, rank, world, local_rank):
             Z, st = api.slista(g.B, g.C, lam, ad, prec=args.prec, keep_for_backward=True, ckpt_every=K)
             F, gap = api.objective(g.B, g.C, g.xsq, Z, lam)
             da = api.slista_grad(g.B, g.C, lam, ad, st, prec=args.prec)
-            Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=Dd)
+            Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=Dd, prec=args.oista_prec)
             Zh.copy_(Z, non_blocking=True)
             Fh.copy_(F, non_blocking=True)
             Gh.copy_(gap, non_blocking=True)
@@ -325,7 +326,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec,
         "data": "synthetic (seeded; D 64x256 unit-norm Gaussian, x = D z0 + 0.01 noise)",
         "config": {"workload": "slista_64x256", "n": n, "m": m, "N_per_gpu": N, "T": T, "lam": lam,
-                   "ckpt_every": K, "prec": args.prec,
+                   "ckpt_every": K, "prec": args.prec, "oista_prec": args.oista_prec,
                    "step": "gram+L -> slista fwd(masks,ckpt) -> objective+gap -> slista bwd -> oista fwd",
                    "l2": "flushed between timed steps (write of 2x L2 size, untimed)",
                    "parallelism": "dp%d" % world if world > 1 else "single"},

@@ -166,16 +166,18 @@ def slista_grad_batched(probs, ckpt_every: int, prec="bf16x3", gZs=None, stream=
     return [q["dalpha"] for q in qs]
 
 
-def oista(B, C, lam, L, T, D=None, stream=None):
+def oista(B, C, lam, L, T, D=None, prec="fp32", stream=None):
     """Oracle-ISTA (Algorithm 1).  Returns (Z, LS, accepted).  D (optional)
-    lets supports larger than 64 be solved on the n x n matrix D_S D_S^T."""
+    lets supports larger than 64 be solved on the n x n matrix D_S D_S^T.
+    prec: "fp32" (CUDA-core layers) or "bf16x3" / "bf16" (tensor-core layers)."""
     N, m = C.shape
+    p = _prec(prec)
     dev = C.device
     Z = torch.empty((N, m), dtype=torch.float32, device=dev)
     LS = torch.empty((N,), dtype=torch.float64, device=dev)
     acc = torch.empty((max(T, 1),), dtype=torch.int32, device=dev)
-    ws = workspace(_lib.slista_workspace_bytes(_lib.FN_OISTA, m, N, T, 0), dev, "oista")
-    _lib.oista_forward(B, C, lam, L, T, _lib.PREC_FP32, Z, LS=LS, accepted=acc[:T] if T > 0 else None,
+    ws = workspace(_lib.slista_workspace_bytes(_lib.FN_OISTA, m, N, T, p), dev, "oista")
+    _lib.oista_forward(B, C, lam, L, T, p, Z, LS=LS, accepted=acc[:T] if T > 0 else None,
                        ws=ws, D=D, stream=stream)
     return Z, LS, acc[:T]
 

@@ -163,7 +163,7 @@ size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_ev
                                         : tcw::supported(m) ? tcw::backward_ws_bytes(m, N, T, K) : 0;
             }
             return simt::backward_ws_bytes(m, N, T, ckpt_every < T ? ckpt_every : T);
-        case SLISTA_FN_OISTA: return simt::padded_mp(m) ? simt::oista_ws_bytes(m, N, T) : 0;
+        case SLISTA_FN_OISTA: return simt::padded_mp(m) ? simt::oista_ws_bytes(m, N, T, prec) : 0;
         default: return 0;
     }
 }
@@ -278,17 +278,18 @@ int oista_forward(const float *B, const float *C, const float *D, int n, int m, 
 {
     clear_error();
     SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 0, SLISTA_ERR_ARG, "oista_forward: bad sizes m=%d N=%d T=%d", m, N, T);
-    SLISTA_REQUIRE(prec == SLISTA_PREC_FP32, SLISTA_ERR_UNSUPPORTED, "oista_forward: only SLISTA_PREC_FP32");
+    SLISTA_REQUIRE(valid_prec(prec), SLISTA_ERR_ARG, "oista_forward: unknown precision %d", prec);
+    SLISTA_REQUIRE(prec != SLISTA_PREC_TF32, SLISTA_ERR_UNSUPPORTED, "oista_forward: TF32 is not built");
     SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "oista_forward: m <= 256 supported");
     SLISTA_REQUIRE(B && L, SLISTA_ERR_ARG, "oista_forward: B and L must not be NULL");
     SLISTA_REQUIRE(!D || n >= 1, SLISTA_ERR_ARG, "oista_forward: n must be >= 1 when D is given");
     SLISTA_REQUIRE(N == 0 || (C && Z), SLISTA_ERR_ARG, "oista_forward: C and Z must not be NULL");
     int rc = check_lam(lam);
     if (rc) return rc;
-    const size_t need = simt::oista_ws_bytes(m, N, T);
+    const size_t need = simt::oista_ws_bytes(m, N, T, prec);
     SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
                    "oista_forward: workspace of %zu bytes needed, %zu given", need, ws_bytes);
-    OistaArgs a{B, C, D, D ? n : 0, m, N, lam, L, T, Z, LS, accepted};
+    OistaArgs a{B, C, D, D ? n : 0, m, N, lam, L, T, Z, LS, accepted, prec};
     return simt::launch_oista(a, ws, as_stream(stream));
 }
 

@@ -53,6 +53,7 @@ struct OistaArgs {
     float *Z;
     double *LS;          // nullable
     int *accepted;       // nullable
+    int prec;            // SLISTA_PREC_FP32 (SIMT layers) or BF16 / BF16X3 (tensor-core layers)
 };
 
 namespace simt {
@@ -62,7 +63,7 @@ int launch_backward(const BwdArgs &a, void *ws, cudaStream_t st);
 size_t backward_ws_bytes(int m, int N, int T, int K);
 int launch_objective(const ObjArgs &a, cudaStream_t st);
 int launch_oista(const OistaArgs &a, void *ws, cudaStream_t st);
-size_t oista_ws_bytes(int m, int N, int T);
+size_t oista_ws_bytes(int m, int N, int T, int prec);
 }  // namespace simt
 
 namespace gram {
@@ -109,6 +110,27 @@ int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st);
 size_t backward_ws_bytes(int m, int N, int T, int K);
 int launch_backward(const BwdArgs &a, int prec, void *ws, cudaStream_t st);
 int read_and_clear_flag(cudaStream_t st);
+
+// Oracle-ISTA layer on the tensor cores (m <= 256, state in place).
+struct OistaStep {
+    const uint8_t *tiles;      // split B (oista_split)
+    const float *C;
+    float *Zs, *Gs, *Zfinal;
+    const double *L, *LSv;
+    int *flag;
+    uint32_t *Scur;
+    const uint32_t *Sprev;
+    const int *valid;
+    int *list, *counter;       // next layer's lists (3 classes, stride listN) and lengths
+    int listN;
+    int *accepted;
+    double *LS_out;
+    int m, N, t, T, want_ls;
+    float lam;
+};
+size_t oista_tiles_bytes(int m);
+int oista_split(const float *B, int m, uint8_t *tiles, cudaStream_t st);
+int launch_oista_step(const OistaStep &o, int prec, cudaStream_t st);
 }  // namespace tcw
 
 // Device-side error flag (set by bounded waits that expire).

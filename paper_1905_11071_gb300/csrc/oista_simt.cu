@@ -45,6 +45,8 @@ constexpr int A_WARPS = 8;
 constexpr int S_WARPS = 8;
 constexpr int SMALL_K = 32;
 constexpr int NCLS = 3;  // list classes: |S| > KMAX, SMALL_K < |S| <= KMAX, |S| <= SMALL_K
+// (the tensor-core step kernel files samples into the same classes: 64 / 32)
+static_assert(KMAX == 64 && SMALL_K == 32 && NCLS == 3, "list classes of the tensor-core step");
 constexpr int STEP_NB = 32;
 
 constexpr int GCOLS = 8;  // D_S columns staged per round in gram_ds
@@ -68,6 +70,7 @@ struct OistaWs {
     int *counter;             // 2 x NCLS: list lengths, same indexing
     int *qpos;                // T x NCLS: queue positions of the solve kernels
     float *Dt;                // m x n: D transposed (columns of D contiguous), when D is given
+    uint8_t *tiles;           // split B for the tensor-core layers (after Dt)
     int N, W;
 
     static size_t bytes(int m, int N, int T)
@@ -103,6 +106,8 @@ struct OistaWs {
         o.qpos = reinterpret_cast<int *>(p);
         p += sizeof(int) * NCLS * (size_t)T;
         o.Dt = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
+        o.tiles = reinterpret_cast<uint8_t *>(
+            (reinterpret_cast<uintptr_t>(o.Dt + (size_t)m * 256) + 255) & ~(uintptr_t)255);
         o.N = N;
         o.W = (int)W;
         return o;
@@ -615,6 +620,11 @@ int launch_oista_mp(const OistaArgs &a, void *wsp, cudaStream_t st)
     SLISTA_CUDA_TRY(allow_smem(kinit, step_smem));
     SLISTA_CUDA_TRY(allow_smem(kstep, step_smem));
     SLISTA_CUDA_TRY(allow_smem(oista_solve_kernel, solve_smem));
+    const bool tc = a.prec == SLISTA_PREC_BF16 || a.prec == SLISTA_PREC_BF16X3;
+    if (tc) {
+        int rc1 = tcw::oista_split(a.B, a.m, ws.tiles, st);
+        if (rc1) return rc1;
+    }
     const int grid = ceil_div(a.N, STEP_NB);
     const bool want_ls = a.LS != nullptr;
     kinit<<<grid, NT, step_smem, st>>>(a.C, a.m, a.N, a.lam, a.L, ws, want_ls && a.T == 1);
@@ -626,9 +636,36 @@ int launch_oista_mp(const OistaArgs &a, void *wsp, cudaStream_t st)
                                                                                        t);
         rc = check_launch("oista_solve_kernel");
         if (rc) return rc;
-        kstep<<<grid, NT, step_smem, st>>>(a.B, a.m, a.N, a.lam, a.L, ws, t, a.T, want_ls && t + 2 == a.T, a.Z,
-                                           a.LS, a.accepted);
-        rc = check_launch("oista_step_kernel");
+        if (tc) {
+            tcw::OistaStep o{};
+            o.tiles = ws.tiles;
+            o.C = a.C;
+            o.Zs = ws.Zs;
+            o.Gs = ws.Gs;
+            o.Zfinal = a.Z;
+            o.L = a.L;
+            o.LSv = ws.LSv;
+            o.flag = ws.flag;
+            o.Scur = ws.Scur;
+            o.Sprev = ws.Sprev;
+            o.valid = ws.valid;
+            o.list = ws.list + (size_t)NCLS * ((t + 1) & 1) * a.N;
+            o.counter = ws.counter + NCLS * ((t + 1) & 1);
+            o.listN = a.N;
+            o.accepted = a.accepted ? a.accepted + t : nullptr;
+            o.LS_out = a.LS;
+            o.m = a.m;
+            o.N = a.N;
+            o.t = t;
+            o.T = a.T;
+            o.want_ls = want_ls && t + 2 == a.T;
+            o.lam = a.lam;
+            rc = tcw::launch_oista_step(o, a.prec, st);
+        } else {
+            kstep<<<grid, NT, step_smem, st>>>(a.B, a.m, a.N, a.lam, a.L, ws, t, a.T, want_ls && t + 2 == a.T, a.Z,
+                                               a.LS, a.accepted);
+            rc = check_launch("oista_step_kernel");
+        }
         if (rc) return rc;
     }
     return SLISTA_OK;
@@ -647,7 +684,11 @@ int launch_oista(const OistaArgs &a, void *ws, cudaStream_t st)
     return fail(SLISTA_ERR_UNSUPPORTED, "OISTA kernel supports m <= 256 (got %d)", a.m);
 }
 
-size_t oista_ws_bytes(int m, int N, int T) { return OistaWs::bytes(m, N, T) + 64; }
+size_t oista_ws_bytes(int m, int N, int T, int prec)
+{
+    const bool tc = prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3;
+    return OistaWs::bytes(m, N, T) + 64 + (tc ? tcw::oista_tiles_bytes(m) + 256 : 0);
+}
 
 }  // namespace simt
 }  // namespace slista

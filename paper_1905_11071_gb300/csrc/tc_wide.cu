@@ -43,7 +43,7 @@ constexpr int TILE_PAIR = 2 * TILE_B;            // hi then lo, as stored in the
 constexpr int REFRESH = 8;
 constexpr uint32_t IDESC = idesc_bf16(BM, BN);
 
-enum Mode { FWD = 0, ADJ = 1 };
+enum Mode { FWD = 0, ADJ = 1, OIS = 2 };
 
 template <bool SPLIT>
 struct WCfg {
@@ -81,6 +81,20 @@ struct WLayer {
     const double *Lp;
     int t, m, N, refresh, skip_mma;
     float lam;
+    // Oracle-ISTA step (MODE == OIS, m <= 256, state updated in place): the
+    // step of sample i is 1 / L_S (cached for its support) when condition
+    // (star) held for it at this layer (flag_i == 0), else 1 / L; the epilogue
+    // prepares the next layer: supports, condition (star), the list of samples
+    // that need a new L_S (Algorithm 1; see oista_simt.cu).
+    const double *LSv;        // N: cached L_S
+    int *flag;                // N: in: (star) failed at layer t; out: at layer t+1
+    uint32_t *Scur;           // N x W: out: supp(z^(t+1))
+    const uint32_t *Sprev;    // N x W: support of the cached L_S
+    const int *valid;         // N: the cached L_S is valid
+    int *list, *counter;      // next layer's lists: class c at list + c * listN, length counter[c]
+    int *accepted;            // accepted steps at this layer (nullable)
+    double *LS_out;           // last layer: L_S per sample (nullable)
+    int want_ls, listN, last;
 };
 
 template <int NP>
@@ -176,6 +190,15 @@ __global__ void split_tiles_kernel(const float *__restrict__ B, int m, uint8_t *
     *reinterpret_cast<__nv_bfloat16 *>(tile + TILE_B + off) = lo;
 }
 
+// Oracle-ISTA step of sample `row`: 1 / L_S when condition (star) held at
+// this layer (flag 0), else the ISTA step aL = 1 / L (same rounding as the
+// FP32 step kernel).
+__device__ __forceinline__ float oista_step(const WLayer &L, int row, bool ok, float aL)
+{
+    if (!ok) return aL;
+    return __ldg(L.flag + row) == 0 ? (float)(1.0 / __ldg(L.LSv + row)) : aL;
+}
+
 // ---------------------------------------------------------------------------
 // The layer kernel.
 // ---------------------------------------------------------------------------
@@ -212,7 +235,6 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
     const uint32_t tmem = tmem_slot;
 
     const float a = L.alpha ? __ldg(L.alpha + L.t) : (float)(1.0 / __ldg(L.Lp));
-    const float thr = a * L.lam;
     const uint8_t *Bcol = L.Bt + (size_t)(col0 / BN) * nkc * TILE_PAIR;
     const float *Zs = L.Zin;
     const float *Gs = (MODE == FWD && L.Zin == nullptr) ? L.C : L.Gin;
@@ -242,6 +264,8 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         const int prow = tid >> 2, pk = (tid & 3) * 16;  // producer: one row, 16 codes of the chunk
         const int grow = row0 + prow;
         const bool rok = grow < N;
+        const float pa = MODE == OIS ? oista_step(L, grow, rok, a) : a;
+        const float pthr = pa * L.lam;
 #pragma unroll 1
         for (int kc = 0; kc < nkc; ++kc) {
             const int s = kc & 1;
@@ -256,13 +280,13 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
             // --- A operand of chunk kc: 16 codes of row prow
             const int k0 = kc * BK + pk;
             float v[16];
-            if (MODE == FWD) {
+            if (MODE != ADJ) {
                 float z[16], g[16];
                 load16(Zs, grow, rok, m, k0, z);
                 load16(Gs, grow, rok, m, k0, g);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const float zn = st_f(fmaf(a, g[j], z[j]), thr);
+                    const float zn = st_f(fmaf(pa, g[j], z[j]), pthr);
                     v[j] = L.refresh ? -zn : z[j] - zn;
                 }
             } else {
@@ -307,8 +331,12 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
     const bool eok = erow < N;
     const int W = (m + 31) / 32;
     const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cg * 64);
+    const float ea = MODE == OIS ? oista_step(L, erow, eok, a) : a;
+    const float ethr = ea * L.lam;
     float part = 0.0f;
     uint32_t word = 0u;
+    bool obad = false, ochg = false;  // OIS: (star) fails for the next layer; support changed
+    int ok_cnt = 0;                   // OIS: support size
 #pragma unroll 1
     for (int pc = 0; pc < 4; ++pc) {
         const int c = col0 + cg * 64 + pc * 16;
@@ -320,7 +348,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
             for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
         }
         if (failed || !eok || c >= m) continue;
-        if (MODE == FWD) {
+        if (MODE != ADJ) {
             float z[16], g[16];
             load16(Zs, erow, true, m, c, z);
             load16(Gs, erow, true, m, c, g);
@@ -329,10 +357,11 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
             uint32_t bits = 0u;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const float zn = st_f(fmaf(a, g[j], z[j]), thr);
+                const float zn = st_f(fmaf(ea, g[j], z[j]), ethr);
                 z[j] = zn;
                 g[j] = (L.refresh ? cv[j] : g[j]) + acc[j];
                 bits |= (uint32_t)(zn != 0.0f) << j;
+                if (MODE == OIS) obad |= (c + j < m) && (zn == 0.0f) && (fabsf(g[j]) > L.lam);
             }
             if (c + 16 > m) bits &= (1u << (m - c)) - 1u;
 #pragma unroll
@@ -343,11 +372,16 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
                 }
             }
             word |= bits << (16 * (pc & 1));
-            if (pc & 1) {
-                if (L.mask_out) L.mask_out[(size_t)erow * W + ((c - 16) >> 5)] = word;
+            const bool word_done = (pc & 1) || c + 16 >= m;  // odd piece, or the row's last piece
+            if (word_done) {
+                const int wi = (c - 16 * (pc & 1)) >> 5;
+                if (L.mask_out) L.mask_out[(size_t)erow * W + wi] = word;
+                if (MODE == OIS && !L.last) {
+                    L.Scur[(size_t)erow * W + wi] = word;
+                    ochg |= word != __ldg(L.Sprev + (size_t)erow * W + wi);
+                    ok_cnt += __popc(word);
+                }
                 word = 0u;
-            } else if (c + 16 >= m && L.mask_out) {  // last piece of the row, odd count of pieces
-                L.mask_out[(size_t)erow * W + (c >> 5)] = word;
             }
         } else {
             float G[16], gq[16], zq[16];
@@ -367,6 +401,40 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
                 for (int j = 0; j < 16; ++j)
                     if (c + j < m) L.Gout[(size_t)erow * m + c + j] = G[j];
         }
+    }
+    if (MODE == OIS) {
+        // combine the four column groups of each row, then one thread per row
+        // prepares the next layer (condition (star), the L_S list)
+        __shared__ int rbad[BM], rchg[BM], rk[BM], nacc;
+        for (int r = tid; r < BM; r += NT) rbad[r] = rchg[r] = rk[r] = 0;
+        if (tid == 0) nacc = 0;
+        __syncthreads();
+        if (eok && !failed) {
+            if (obad) atomicOr(&rbad[32 * q + lane], 1);
+            if (ochg) atomicOr(&rchg[32 * q + lane], 1);
+            if (ok_cnt) atomicAdd(&rk[32 * q + lane], ok_cnt);
+        }
+        __syncthreads();
+        if (cg == 0 && eok && !failed) {
+            if (__ldg(L.flag + erow) == 0) atomicAdd(&nacc, 1);
+            if (L.last) {
+                if (L.LS_out) L.LS_out[erow] = __ldg(L.LSv + erow);
+            }
+        }
+        __syncthreads();  // every read of flag[] precedes its update
+        if (cg == 0 && eok && !failed && !L.last) {
+            const int r = 32 * q + lane;
+            const int f = rbad[r];
+            L.flag[erow] = f;
+            const bool changed = rchg[r] != 0 || __ldg(L.valid + erow) == 0;
+            if ((f == 0 || L.want_ls) && changed) {
+                const int k = rk[r];
+                const int cls = k > 64 ? 0 : k > 32 ? 1 : 2;
+                const int pos = atomicAdd(L.counter + cls, 1);
+                L.list[(size_t)cls * L.listN + pos] = erow;
+            }
+        }
+        if (tid == 0 && L.accepted && nacc) atomicAdd(L.accepted, nacc);
     }
     if (MODE == ADJ) {
 #pragma unroll
@@ -452,7 +520,9 @@ int launch_chunk(const WLayer *Ls, int count, cudaStream_t st)
     auto k = tcw_layer_kernel<SPLIT, MODE, NP>;
     SLISTA_CUDA_TRY(allow_smem(k, WCfg<SPLIT>::SMEM));
     k<<<P.base[count], NT, WCfg<SPLIT>::SMEM, st>>>(P);
-    return check_launch(MODE == FWD ? "tcw_layer_kernel (forward)" : "tcw_layer_kernel (adjoint)");
+    return check_launch(MODE == FWD   ? "tcw_layer_kernel (forward)"
+                        : MODE == ADJ ? "tcw_layer_kernel (adjoint)"
+                                      : "tcw_layer_kernel (Oracle-ISTA step)");
 }
 
 // One layer for every problem of the batch: launches of at most MAXP problems.
@@ -704,6 +774,44 @@ int backward_batch(const Problem *P, int count, int T, int Kin, int prec, void *
         if (rc) return rc;
     }
     return SLISTA_OK;
+}
+
+size_t oista_tiles_bytes(int m) { return align256(tiles_bytes(m)); }
+
+int oista_split(const float *B, int m, uint8_t *tiles, cudaStream_t st) { return split_tiles(B, m, tiles, st); }
+
+int launch_oista_step(const OistaStep &o, int prec, cudaStream_t st)
+{
+    WLayer L{};
+    L.Bt = o.tiles;
+    L.C = o.C;
+    L.Zin = o.Zs;
+    L.Gin = o.Gs;
+    const bool last = o.t == o.T - 1;
+    L.Zout = last ? o.Zfinal : o.Zs;
+    L.Gout = last ? nullptr : o.Gs;
+    L.skip_mma = last ? 1 : 0;
+    L.alpha = nullptr;
+    L.Lp = o.L;
+    L.t = o.t;
+    L.m = o.m;
+    L.N = o.N;
+    L.lam = o.lam;
+    L.refresh = refresh_at(o.t, o.T, 0, false);
+    L.LSv = o.LSv;
+    L.flag = o.flag;
+    L.Scur = o.Scur;
+    L.Sprev = o.Sprev;
+    L.valid = o.valid;
+    L.list = o.list;
+    L.counter = o.counter;
+    L.listN = o.listN;
+    L.accepted = o.accepted;
+    L.LS_out = o.LS_out;
+    L.want_ls = o.want_ls;
+    L.last = last ? 1 : 0;
+    const bool split = prec == SLISTA_PREC_BF16X3;
+    return split ? launch_chunk<true, OIS, 1>(&L, 1, st) : launch_chunk<false, OIS, 1>(&L, 1, st);
 }
 
 int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st)

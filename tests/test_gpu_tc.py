@@ -296,3 +296,71 @@ def test_tc_backward_full_size_split_batch():
     dg = host(A.slista_grad(g.B, C, w.lam, alpha, s3, prec="bf16x3")).astype(np.float64)
     do, _ = oracle.slista_grad(w.D, w.X[rows], w.lam, host(alpha).astype(np.float32))
     assert np.linalg.norm(dg - do) <= GRAD_TOL["bf16x3"] * np.linalg.norm(do)
+
+
+# --------------------------------------------------------------------------- Oracle-ISTA on the tensor cores
+
+# decisions of condition (star) and of the thresholds are compared where the
+# oracle's margin exceeds the split product's error scale (the mask rule)
+TC_OISTA_MARGIN = 1e-4
+
+
+@pytest.mark.parametrize("with_D", [True, False])
+def test_tc_oista_parity_64x256(with_D):
+    """Algorithm 1 with the layer products on the tensor cores (BF16X3)."""
+    w = synth.slista_64x256(N=300, T=40)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    Zg, LSg, accg = A.oista(g.B, g.C, w.lam, g.L, w.T, D=dev(w.D) if with_D else None, prec="bf16x3")
+    Lo = oracle.lipschitz(w.D)
+    Zo, LSo, acco, deco, marg = oracle.oista(w.D, w.X, w.lam, Lo, w.T, with_margin=True)
+    safe = marg > TC_OISTA_MARGIN
+    assert safe.sum() >= 30
+    Zg = host(Zg)
+    zt = TOL["bf16x3"]["Z"] * max(1.0, float(np.abs(Zo).max()))
+    assert np.abs(Zg[safe].astype(np.float64) - Zo[safe]).max() <= zt
+    np.testing.assert_allclose(host(LSg)[safe], LSo[safe], rtol=1e-5)
+    Fg = host(A.objective(g.B, g.C, g.xsq, dev(Zg), w.lam, with_gap=False))
+    Fo = oracle.objective(w.D, w.X, Zo, w.lam, with_gap=False)
+    assert (np.abs(Fg[safe] - Fo[safe]) / np.abs(Fo[safe])).max() <= TOL["bf16x3"]["F"]
+    assert np.abs(host(accg) - acco).max() <= (~safe).sum()
+
+
+def test_tc_oista_fig3_setup():
+    """The toy setup of Fig. 3 (D 10 x 50, lam = 0.5, x in B_inf), m padded inside the kernel."""
+    w = synth.paper_binf(10, 50, N=400, lam=0.5, T=100, seed=2)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    Zg, LSg, accg = A.oista(g.B, g.C, w.lam, g.L, w.T, prec="bf16x3")
+    Zo, LSo, acco, deco, marg = oracle.oista(w.D, w.X, w.lam, oracle.lipschitz(w.D), w.T, with_margin=True)
+    safe = marg > TC_OISTA_MARGIN
+    assert safe.mean() > 0.5
+    zt = TOL["bf16x3"]["Z"] * max(1.0, float(np.abs(Zo).max()))
+    assert np.abs(host(Zg)[safe].astype(np.float64) - Zo[safe]).max() <= zt
+    np.testing.assert_allclose(host(LSg)[safe], LSo[safe], rtol=1e-5)
+    assert np.abs(host(accg) - acco).max() <= (~safe).sum()
+
+
+def test_tc_oista_zero_above_lambda_max():
+    w = synth.slista_64x256(N=200, T=10)
+    lam = float(np.float32(np.abs(w.X.astype(np.float64) @ w.D.astype(np.float64)).max() * 1.001))
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    Z, LS, acc = A.oista(g.B, g.C, lam, g.L, 10, D=dev(w.D), prec="bf16x3")
+    assert not Z.any()
+
+
+def test_tc_oista_full_size_sampled_rows():
+    """The benchmark workload (N = 10000, T = 40) on the tensor cores; 48
+    sampled rows against the oracle (samples are independent)."""
+    w = synth.slista_64x256()
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    Zg, LSg, accg = A.oista(g.B, g.C, w.lam, g.L, w.T, D=dev(w.D), prec="bf16x3")
+    rows = np.random.default_rng(3).choice(w.N, size=48, replace=False)
+    Zo, LSo, acco, deco, marg = oracle.oista(w.D, w.X[rows], w.lam, oracle.lipschitz(w.D), w.T, with_margin=True)
+    safe = marg > TC_OISTA_MARGIN
+    assert safe.sum() >= 10
+    zt = TOL["bf16x3"]["Z"] * max(1.0, float(np.abs(Zo).max()))
+    assert np.abs(host(Zg)[rows][safe].astype(np.float64) - Zo[safe]).max() <= zt
+    np.testing.assert_allclose(host(LSg)[rows][safe], LSo[safe], rtol=1e-5)
