@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--N", type=int, default=10000)
     p.add_argument("--T", type=int, default=40)
     p.add_argument("--prec", default="bf16x3", help="layer precision: bf16x3 (tensor cores, default), bf16, fp32")
-    p.add_argument("--oista-prec", default="fp32", help="Oracle-ISTA layer precision: fp32 (CUDA cores), bf16x3 (tensor cores)")
+    p.add_argument("--oista-prec", default="bf16x3", help="Oracle-ISTA layer precision: bf16x3 (tensor cores), fp32 (CUDA cores)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-samples", type=int, default=0, help="oracle sample size (0 = auto)")

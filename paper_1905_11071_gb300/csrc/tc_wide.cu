@@ -42,6 +42,9 @@ constexpr int TILE_B = BN * BK * 2;              // one BF16 B tile (32 KB)
 constexpr int TILE_PAIR = 2 * TILE_B;            // hi then lo, as stored in the workspace
 constexpr int REFRESH = 8;
 constexpr uint32_t IDESC = idesc_bf16(BM, BN);
+constexpr int SW = 128;       // epilogue slice: columns staged through shared memory at a time
+constexpr int SLD = SW + 1;   // row stride of a staged slice (odd: conflict-free column access)
+constexpr int EPI_SMEM = 2 * BM * SLD * 4;
 
 enum Mode { FWD = 0, ADJ = 1, OIS = 2 };
 
@@ -50,7 +53,7 @@ struct WCfg {
     static constexpr int OFF_B = SPLIT ? 2 * TILE_A : TILE_A;
     static constexpr int STAGE = OFF_B + (SPLIT ? 2 * TILE_B : TILE_B);
     static constexpr uint32_t BBYTES = SPLIT ? 2 * TILE_B : TILE_B;
-    static constexpr int SMEM = 2 * STAGE + 1024;
+    static constexpr int SMEM = (2 * STAGE > EPI_SMEM ? 2 * STAGE : EPI_SMEM) + 1024;
 };
 
 int read_and_clear_flag(cudaStream_t st)
@@ -164,6 +167,31 @@ __device__ __forceinline__ void store_a16(uint8_t *stage, int row, int kl, const
         if (SPLIT)
             *reinterpret_cast<uint4 *>(stage + TILE_A + off) =
                 make_uint4(lo[4 * u], lo[4 * u + 1], lo[4 * u + 2], lo[4 * u + 3]);
+    }
+}
+
+// Rows [row0, row0 + BM) x columns [cs, cs + SW) of a row-major N x m matrix
+// into a staged slice (row stride SLD), zero outside the matrix or when M is
+// null; each warp moves 32 consecutive floats of a row.
+__device__ __forceinline__ void stage_in(float *t, const float *__restrict__ M, int row0, int cs, int m, int N,
+                                         int tid)
+{
+#pragma unroll 4
+    for (int e = tid; e < BM * SW; e += NT) {
+        const int r = e / SW, c = e % SW;
+        const int gr = row0 + r, gc = cs + c;
+        t[r * SLD + c] = (M != nullptr && gr < N && gc < m) ? __ldg(M + (size_t)gr * m + gc) : 0.0f;
+    }
+}
+
+__device__ __forceinline__ void stage_out(const float *t, float *__restrict__ M, int row0, int cs, int m, int N,
+                                          int tid)
+{
+#pragma unroll 4
+    for (int e = tid; e < BM * SW; e += NT) {
+        const int r = e / SW, c = e % SW;
+        const int gr = row0 + r, gc = cs + c;
+        if (gr < N && gc < m) M[(size_t)gr * m + gc] = t[r * SLD + c];
     }
 }
 
@@ -324,66 +352,96 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         tc_fence_after();
     }
 
-    // --- epilogue: warp w reads TMEM lanes 32 (w % 4).. (tile rows) and
-    // columns 64 (w / 4).. of the block, 16 at a time
+    // --- epilogue.  Warp w reads TMEM lanes 32 (w % 4).. (the tile rows).
     const int q = warp & 3, cg = warp >> 2;
     const int erow = row0 + 32 * q + lane;
     const bool eok = erow < N;
     const int W = (m + 31) / 32;
-    const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cg * 64);
+    const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
     const float ea = MODE == OIS ? oista_step(L, erow, eok, a) : a;
     const float ethr = ea * L.lam;
     float part = 0.0f;
-    uint32_t word = 0u;
     bool obad = false, ochg = false;  // OIS: (star) fails for the next layer; support changed
     int ok_cnt = 0;                   // OIS: support size
+    if (MODE != ADJ && !failed) {
+        // z, g of the block pass through shared memory in two slices of 128
+        // columns, so that every global load and store is a coalesced row
+        // segment; thread (q, cg) finishes columns [32 cg, 32 cg + 32) of
+        // the slice for its row.
+        float *zt = reinterpret_cast<float *>(smem);
+        float *gt = zt + BM * SLD;
 #pragma unroll 1
-    for (int pc = 0; pc < 4; ++pc) {
-        const int c = col0 + cg * 64 + pc * 16;
-        float acc[16];
-        if (do_mma && !failed) {
-            tmem_ld16(tl + pc * 16, acc);
-        } else {
+        for (int sl = 0; sl < BN / SW; ++sl) {
+            const int cs = col0 + sl * SW;
+            if (cs >= m) break;  // uniform
+            stage_in(zt, Zs, row0, cs, m, N, tid);
+            stage_in(gt, Gs, row0, cs, m, N, tid);
+            __syncthreads();
+            float acc[32];
+            if (do_mma) {
+                float h0[16], h1[16];
+                tmem_ld16(tq + sl * SW + cg * 32, h0);
+                tmem_ld16(tq + sl * SW + cg * 32 + 16, h1);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
-        }
-        if (failed || !eok || c >= m) continue;
-        if (MODE != ADJ) {
-            float z[16], g[16];
-            load16(Zs, erow, true, m, c, z);
-            load16(Gs, erow, true, m, c, g);
-            float cv[16];
-            if (L.refresh && L.Gout) load16(L.C, erow, true, m, c, cv);
-            uint32_t bits = 0u;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float zn = st_f(fmaf(ea, g[j], z[j]), ethr);
-                z[j] = zn;
-                g[j] = (L.refresh ? cv[j] : g[j]) + acc[j];
-                bits |= (uint32_t)(zn != 0.0f) << j;
-                if (MODE == OIS) obad |= (c + j < m) && (zn == 0.0f) && (fabsf(g[j]) > L.lam);
-            }
-            if (c + 16 > m) bits &= (1u << (m - c)) - 1u;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                if (c + j < m) {
-                    if (L.Zout) L.Zout[(size_t)erow * m + c + j] = z[j];
-                    if (L.Gout) L.Gout[(size_t)erow * m + c + j] = g[j];
+                for (int j = 0; j < 16; ++j) {
+                    acc[j] = h0[j];
+                    acc[16 + j] = h1[j];
                 }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[j] = 0.0f;
             }
-            word |= bits << (16 * (pc & 1));
-            const bool word_done = (pc & 1) || c + 16 >= m;  // odd piece, or the row's last piece
-            if (word_done) {
-                const int wi = (c - 16 * (pc & 1)) >> 5;
+            const int r = 32 * q + lane;
+            float *zr = zt + r * SLD + cg * 32, *gr = gt + r * SLD + cg * 32;
+            uint32_t word = 0u;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float zn = st_f(fmaf(ea, gr[j], zr[j]), ethr);
+                zr[j] = zn;
+                word |= (uint32_t)(zn != 0.0f) << j;
+            }
+            const int c0 = cs + cg * 32;  // first code of this thread's word
+            if (c0 + 32 > m) word &= c0 < m ? (1u << (m - c0)) - 1u : 0u;
+            if (L.refresh && L.Gout) {  // g' = c + (-z') B: the slice of C replaces g
+                __syncthreads();
+                stage_in(gt, L.C, row0, cs, m, N, tid);
+                __syncthreads();
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float gn = gr[j] + acc[j];
+                gr[j] = gn;
+                if (MODE == OIS) obad |= (c0 + j < m) && (zr[j] == 0.0f) && (fabsf(gn) > L.lam);
+            }
+            if (eok && c0 < m) {
+                const int wi = c0 >> 5;
                 if (L.mask_out) L.mask_out[(size_t)erow * W + wi] = word;
                 if (MODE == OIS && !L.last) {
                     L.Scur[(size_t)erow * W + wi] = word;
                     ochg |= word != __ldg(L.Sprev + (size_t)erow * W + wi);
                     ok_cnt += __popc(word);
                 }
-                word = 0u;
             }
-        } else {
+            __syncthreads();
+            if (L.Zout) stage_out(zt, L.Zout, row0, cs, m, N, tid);
+            if (L.Gout) stage_out(gt, L.Gout, row0, cs, m, N, tid);
+            __syncthreads();
+        }
+    }
+    if (MODE == ADJ) {
+        // columns 64 (w / 4).. of the block, 16 at a time
+        const uint32_t tl = tq + (uint32_t)(cg * 64);
+#pragma unroll 1
+        for (int pc = 0; pc < 4; ++pc) {
+            const int c = col0 + cg * 64 + pc * 16;
+            float acc[16];
+            if (do_mma && !failed) {
+                tmem_ld16(tl + pc * 16, acc);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] = 0.0f;
+            }
+            if (failed || !eok || c >= m) continue;
             float G[16], gq[16], zq[16];
             load16(L.Gin, erow, true, m, c, G);
             load16(L.Gq ? L.Gq : L.C, erow, true, m, c, gq);

@@ -1,0 +1,75 @@
+"""Two studies of the paper run on the GPU path and checked against the FP64
+oracle:
+
+* Oracle-ISTA's accept / fall-back pattern (Section 3, Appendix B): on the
+  paper's 100 x 200 setup (x in B_inf), per layer the number of samples whose
+  step 1/L_S is accepted by condition (star) is the oracle's, up to the
+  samples whose decision margin is below the FP32 rounding scale; and the
+  objective reached after T layers matches the oracle's.
+* Learned steps (Section 4, Appendix E): Step-LISTA trained on 10 x 20,
+  lam = 0.2, N = 1000 (T = 20) lowers the unsupervised loss monotonically and
+  learns steps larger than ISTA's 1/L in the later layers (the supports of
+  late layers are small, and 1/L_S > 1/L on them).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_11071_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1905_11071_gb300 import build, _lib
+    build.build()
+    _lib.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.mark.parametrize("lam", [0.2, 0.5])
+def test_oista_accept_pattern_100x200(lam):
+    from paper_1905_11071_gb300 import api as A
+    w = synth.paper_binf(100, 200, N=32, lam=lam, T=300, seed=4)
+    g = A.gram(dev(w.D), dev(w.X))
+    Zg, LSg, accg = A.oista(g.B, g.C, w.lam, g.L, w.T, D=dev(w.D))
+    Lo = oracle.lipschitz(w.D)
+    Zo, LSo, acco, deco, marg = oracle.oista(w.D, w.X, w.lam, Lo, w.T, with_margin=True)
+    unsafe = int((marg <= 5e-6).sum())
+    assert np.abs(host(accg) - acco).max() <= unsafe
+    # Oracle-ISTA accepts its step at most layers once supports settle
+    assert acco[-50:].mean() >= 0.5 * w.N
+    safe = marg > 5e-6
+    Fg = host(A.objective(g.B, g.C, g.xsq, Zg, w.lam, with_gap=False))
+    Fo = oracle.objective(w.D, w.X, Zo, w.lam, with_gap=False)
+    assert (np.abs(Fg[safe] - Fo[safe]) / np.abs(Fo[safe])).max() <= 1e-5
+
+
+def test_learned_steps_10x20():
+    from paper_1905_11071_gb300 import api as A
+    T = 20
+    w = synth.paper_binf(10, 20, N=1000, lam=0.2, T=T, seed=0)
+    g = A.gram(dev(w.D), dev(w.X))
+    L = float(host(g.L)[0])
+    alpha0 = torch.full((T,), 1.0 / L, dtype=torch.float32, device="cuda")
+    alpha, hist = A.train_step_sizes(alpha0, g, w.lam, steps=60)
+    hist = np.asarray(hist)
+    assert np.all(np.diff(hist) <= 1e-9 * np.abs(hist[:-1]))  # backtracking never increases the loss
+    assert hist[-1] < hist[0]
+    a = host(alpha).astype(np.float64)
+    assert a[T // 2:].mean() > 1.0 / L
+    # the starting point is ISTA itself: its loss (hist[0]) against the oracle
+    Zi = oracle.ista(w.D, w.X, w.lam, oracle.lipschitz(w.D), T)
+    F_ista = oracle.objective(w.D, w.X, Zi, w.lam, with_gap=False).sum()
+    assert abs(hist[0] - F_ista) <= 1e-5 * abs(F_ista)
