@@ -16,6 +16,7 @@ collective on the data path) and rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -124,6 +125,23 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- ours
+
+def recorded_traffic(part: str):
+    """DRAM bytes per call of a bench part from the committed ncu capture
+    (profiles/dram_traffic.json), or None when any source file of that part
+    changed since the counters were taken (sha256 recorded with them)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)["parts"][part]
+        for rel, digest in rec["sources"].items():
+            with open(os.path.join(ROOT, rel), "rb") as g:
+                if hashlib.sha256(g.read()).hexdigest() != digest:
+                    return None
+        return float(rec["bytes_per_call"])
+    except (OSError, KeyError, ValueError):
+        return None
+
 
 def max_over_ranks(x: float, world: int, device) -> float:
     """The slowest rank's time: every rank contributes x, all get the maximum
@@ -318,7 +336,9 @@ def run_ours(args, rank, world, local_rank):
     dom = max(parts, key=lambda p: per_part[p])
     r = rooflines[dom]
     roofline = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
-                "unit": r["unit"], "frac": r["frac"], "traffic": None, "peak_source": r["peak_source"]}
+                "unit": r["unit"], "frac": r["frac"], "traffic": recorded_traffic(dom),
+                "traffic_unit": "bytes per call (dram__bytes_read.sum + dram__bytes_write.sum, profiles/dram_traffic.json)",
+                "peak_source": r["peak_source"]}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

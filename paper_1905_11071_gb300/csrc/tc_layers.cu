@@ -330,6 +330,15 @@ __device__ __forceinline__ void row16_to_tmem(const TcEngine<MP, SPLIT> &E, cons
     tmem_st16(E.taddr(tcol), v);
 }
 
+// Index of (layer s, tile, lane quadrant, code col, lane) in the adjoint's
+// internal buffers: for one code the 32 rows of a warp are consecutive, so
+// the row-per-lane accesses of the layer kernels are coalesced.
+template <int MP>
+__device__ __forceinline__ size_t lane_index(int s, int ntiles, int tile, int quad, int col, int lane)
+{
+    return ((((size_t)s * ntiles + tile) * 4 + quad) * MP + col) * 32 + lane;
+}
+
 struct TcParams {
     const uint8_t *Bsplit;
     const float *C;
@@ -345,8 +354,9 @@ struct TcParams {
     int TR;               // rows per tile
     // recompute and adjoint
     int t0, t1;           // layer range [t0, t1)
-    float *qbuf;          // (t1 - t0) x N x m: g^(t) - lam sign(z^(t+1))
-    float *Gbuf;          // N x m: adjoint state G
+    float *qbuf;          // (t1 - t0) layers of g^(t) - lam sign(z^(t+1)), tile layout (lane_index)
+    float *Gbuf;          // adjoint state G, tile layout (lane_index)
+    int ntiles;           // tiles of the batch (the tile layout's extent)
     const float *gZ;      // nullable upstream gradient
     int want_gT;          // recompute: form G_T after the last layer
     float *partial;       // T x gridDim.x per-CTA sums of dalpha
@@ -444,7 +454,7 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
                     const float zn = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
                     if constexpr (RECOMP) {
                         if (row_ok && col0 + j < m)
-                            p.qbuf[((size_t)(t - tb) * N + row) * m + col0 + j] =
+                            p.qbuf[lane_index<MP>(t - tb, p.ntiles, tile, quad, col0 + j, lane)] =
                                 gv[j] - lam * (float)((zn > 0.0f) - (zn < 0.0f));
                     }
                     gv[j] = refresh ? -zn : zo - zn;  // the MMA's A operand
@@ -481,8 +491,8 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
                                 if (col0 + j < m) {
                                     const size_t o = (size_t)row * m + col0 + j;
                                     const float zj = z[16 * pc + j];
-                                    p.Gbuf[o] = p.gZ ? __ldg(p.gZ + o)
-                                                     : -gv[j] + lam * (float)((zj > 0.0f) - (zj < 0.0f));
+                                    p.Gbuf[lane_index<MP>(0, p.ntiles, tile, quad, col0 + j, lane)] =
+                                        p.gZ ? __ldg(p.gZ + o) : -gv[j] + lam * (float)((zj > 0.0f) - (zj < 0.0f));
                                 }
                     }
                 }
@@ -534,11 +544,12 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
         const bool row_ok = (quad * 32 + lane < TR) && row < N;
         float G[CF::CW];
 #pragma unroll
-        for (int j = 0; j < CF::CW; ++j) G[j] = (row_ok && cbase + j < m) ? Gbuf[(size_t)row * m + cbase + j] : 0.0f;
+        for (int j = 0; j < CF::CW; ++j)
+            G[j] = (row_ok && cbase + j < m) ? Gbuf[lane_index<MP>(0, p.ntiles, tile, quad, cbase + j, lane)] : 0.0f;
 #pragma unroll 1
         for (int t = p.t1 - 1; t >= p.t0; --t) {
             const float a = __ldg(alpha + t);
-            const float *qrow = qbuf + ((size_t)(t - p.t0) * N + row) * m;
+            const float *qt = qbuf + lane_index<MP>(t - p.t0, p.ntiles, tile, quad, 0, lane);  // + 32 per code
             float part = 0.0f;
 #pragma unroll
             for (int pc = 0; pc < CF::NPC; ++pc) {
@@ -550,25 +561,11 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
                         (row_ok && valid) ? __ldg(masks + ((size_t)t * N + row) * W + (col0 >> 5)) & valid : 0u;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) G[16 * pc + j] = ((word >> j) & 1u) ? G[16 * pc + j] : 0.0f;  // h
-                    if (row_ok) {
-                        // <h, q_t> over these 32 columns (h = 0 off the support and past m)
-                        if ((m & 3) == 0) {
-                            const float4 *q4 = reinterpret_cast<const float4 *>(qrow + col0);
+                    // <h, q_t> over these 32 columns (h = 0 off the support, past m and past N);
+                    // q_t of one code is 32 consecutive floats over the warp's rows
 #pragma unroll
-                            for (int v = 0; v < 8; ++v)
-                                if (col0 + 4 * v < m) {
-                                    const float4 q = __ldg(q4 + v);
-                                    part = fmaf(G[16 * pc + 4 * v + 0], q.x, part);
-                                    part = fmaf(G[16 * pc + 4 * v + 1], q.y, part);
-                                    part = fmaf(G[16 * pc + 4 * v + 2], q.z, part);
-                                    part = fmaf(G[16 * pc + 4 * v + 3], q.w, part);
-                                }
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if ((word >> j) & 1u) part = fmaf(G[16 * pc + j], __ldg(qrow + col0 + j), part);
-                        }
-                    }
+                    for (int j = 0; j < 32; ++j)
+                        if ((word >> j) & 1u) part = fmaf(G[16 * pc + j], __ldg(qt + (size_t)(col0 + j) * 32), part);
                 }
                 float hv[16];
 #pragma unroll
@@ -602,7 +599,7 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
         if (p.t0 > 0 && row_ok) {
 #pragma unroll
             for (int j = 0; j < CF::CW; ++j)
-                if (cbase + j < m) Gbuf[(size_t)row * m + cbase + j] = G[j];
+                if (cbase + j < m) Gbuf[lane_index<MP>(0, p.ntiles, tile, quad, cbase + j, lane)] = G[j];
         }
         E.tile_done();
     }
@@ -687,10 +684,11 @@ size_t backward_ws_mp(int MP, int m, int N, int T, int K)
 {
     int TR = 0, grid = 0;
     tiling(N, &TR, &grid);
-    (void)TR;
     const size_t bsplit = (size_t)MP * MP * 4;
-    const size_t q = sizeof(float) * (size_t)K * N * m;
-    const size_t G = sizeof(float) * (size_t)N * m;
+    const int ntiles = N > 0 ? ceil_div(N, TR) : 0;
+    const size_t tileset = (size_t)ntiles * 128 * MP;  // tile layout: 4 quadrants x MP codes x 32 lanes
+    const size_t q = sizeof(float) * (size_t)K * tileset;
+    const size_t G = sizeof(float) * tileset;
     const size_t part = sizeof(float) * (size_t)T * (grid > 0 ? grid : 1);
     return bsplit + q + G + part + 256;
 }
@@ -701,9 +699,13 @@ int launch_backward_mp(const BwdArgs &a, void *ws, cudaStream_t st)
     using CF = Cfg<MP, SPLIT>;
     uint8_t *base = reinterpret_cast<uint8_t *>(ws);
     uint8_t *bsplit = base;
+    int TRt = 0, gridt = 0;
+    tiling(a.N, &TRt, &gridt);
+    const int ntiles = a.N > 0 ? ceil_div(a.N, TRt) : 0;
+    const size_t tileset = (size_t)ntiles * 128 * MP;
     float *qbuf = reinterpret_cast<float *>(base + (size_t)MP * MP * 4);
-    float *Gbuf = qbuf + (size_t)a.ckpt_every * a.N * a.m;
-    float *partial = Gbuf + (size_t)a.N * a.m;
+    float *Gbuf = qbuf + (size_t)a.ckpt_every * tileset;
+    float *partial = Gbuf + tileset;
     int rc = split_b<MP, SPLIT>(a.B, a.m, bsplit, st);
     if (rc) return rc;
     if (a.N == 0) {
@@ -725,6 +727,7 @@ int launch_backward_mp(const BwdArgs &a, void *ws, cudaStream_t st)
     p.K = a.ckpt_every;
     p.qbuf = qbuf;
     p.Gbuf = Gbuf;
+    p.ntiles = ntiles;
     p.gZ = a.gZ;
     p.partial = partial;
     int grid = 0;
