@@ -187,15 +187,22 @@ __host__ __device__ inline float start_vector(int a)
 __device__ inline float tridiag_max_eig_warp(const float *d, const float *e, float *e2, int k)
 {
     const int lane = threadIdx.x & 31;
-    for (int i = lane; i + 1 < k; i += 32) e2[i] = e[i] * e[i];
-    __syncwarp();
+    // Gershgorin bracket of the spectrum, one row per lane, then max over the warp
     float lo = -INFINITY, hi = -INFINITY, scale = 0.0f;
-    for (int i = 0; i < k; ++i) {
+    for (int i = lane; i < k; i += 32) {
+        if (i + 1 < k) e2[i] = e[i] * e[i];
         const float r = (i > 0 ? fabsf(e[i - 1]) : 0.0f) + (i + 1 < k ? fabsf(e[i]) : 0.0f);
         lo = fmaxf(lo, d[i]);
         hi = fmaxf(hi, d[i] + r);
         scale = fmaxf(scale, fabsf(d[i]) + r);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmaxf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        scale = fmaxf(scale, __shfl_xor_sync(0xffffffffu, scale, o));
+    }
+    __syncwarp();
     const float pivmin = fmaxf(scale * 1e-30f, 1e-37f);
     hi = hi + 2e-7f * scale;
     for (int round = 0; round < 8 && hi - lo > 1.2e-7f * scale; ++round) {

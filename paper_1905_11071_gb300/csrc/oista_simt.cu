@@ -310,7 +310,8 @@ struct WarpEigS {
     int idx[SMALL_K];
 };
 
-__device__ double solve_small(const float *__restrict__ B, int m, const int *idx, int k, WarpEigS &ws)
+__device__ double solve_small(const float *__restrict__ B, int m, const int *idx, int k, float *al, float *be,
+                              float *e2)
 {
     const int lane = threadIdx.x & 31;
     const bool on = lane < k;
@@ -357,8 +358,8 @@ __device__ double solve_small(const float *__restrict__ B, int m, const int *idx
         for (int o = 16; o > 0; o >>= 1) bb += __shfl_xor_sync(0xffffffffu, bb, o);
         const float beta = sqrtf(bb);
         if (lane == 0) {
-            ws.al[j] = alpha;
-            ws.be[j] = beta;
+            al[j] = alpha;
+            be[j] = beta;
         }
         if (beta <= 1e-6f * fabsf(alpha) || j + 1 == k) {  // invariant subspace or full dimension
             ++j;
@@ -369,7 +370,7 @@ __device__ double solve_small(const float *__restrict__ B, int m, const int *idx
         beta_prev = beta;
     }
     __syncwarp();
-    return (double)eig::tridiag_max_eig_warp(ws.al, ws.be, ws.e2, j);
+    return (double)eig::tridiag_max_eig_warp(al, be, e2, j);
 }
 
 // Takes the next sample of list class cls of layer t (one warp); -1 when empty.
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__((A_WARPS + S_WARPS) * 32, 1) oista_solve_kerne
             const uint32_t *words = ws.Scur + (size_t)i * ws.W;
             const int k = support_indices(words, ws.W, we.idx);
             const double LS = k == 0 ? L : k == 1 ? (double)__ldg(B + (size_t)we.idx[0] * m + we.idx[0])
-                                                  : solve_small(B, m, we.idx, k, we);
+                                                  : solve_small(B, m, we.idx, k, we.al, we.be, we.e2);
             publish(ws, i, words, LS);
         }
         return;
@@ -435,6 +436,8 @@ __global__ void __launch_bounds__((A_WARPS + S_WARPS) * 32, 1) oista_solve_kerne
                 LS = L;
             } else if (k == 1) {
                 LS = (double)__ldg(B + (size_t)we.idx[0] * m + we.idx[0]);
+            } else if (k <= SMALL_K) {
+                LS = solve_small(B, m, we.idx, k, we.al, we.be, we.e2);
             } else if (k <= KMAX) {
                 const int lda = eig::odd_ld(k);
                 if (gather_bss(B, m, we.idx, k, we.A, lda))

@@ -83,6 +83,7 @@ struct WLayer {
     const float *alpha;       // step sizes (nullptr: 1 / L)
     const double *Lp;
     int t, m, N, refresh, skip_mma;
+    int TR;                   // rows per tile (<= 128; 0: 128): smaller tiles spread a short batch over every SM
     float lam;
     // Oracle-ISTA step (MODE == OIS, m <= 256, state updated in place): the
     // step of sample i is 1 / L_S (cached for its support) when condition
@@ -109,7 +110,7 @@ struct WBatch {
 
 __host__ __device__ inline int n_colblocks(int m) { return (m + BN - 1) / BN; }
 __host__ __device__ inline int n_kchunks(int m) { return (m + BK - 1) / BK; }
-inline int n_items(int m, int N) { return ceil_div(N, BM) * n_colblocks(m); }
+inline int n_items(int m, int N, int TR = 0) { return ceil_div(N, TR > 0 ? TR : BM) * n_colblocks(m); }
 
 // 16 consecutive entries (columns k0..k0+15) of row `row` of an N x m FP32
 // matrix, zero outside the matrix or when M is null.
@@ -174,24 +175,24 @@ __device__ __forceinline__ void store_a16(uint8_t *stage, int row, int kl, const
 // into a staged slice (row stride SLD), zero outside the matrix or when M is
 // null; each warp moves 32 consecutive floats of a row.
 __device__ __forceinline__ void stage_in(float *t, const float *__restrict__ M, int row0, int cs, int m, int N,
-                                         int tid)
+                                         int TR, int tid)
 {
 #pragma unroll 4
     for (int e = tid; e < BM * SW; e += NT) {
         const int r = e / SW, c = e % SW;
         const int gr = row0 + r, gc = cs + c;
-        t[r * SLD + c] = (M != nullptr && gr < N && gc < m) ? __ldg(M + (size_t)gr * m + gc) : 0.0f;
+        t[r * SLD + c] = (M != nullptr && r < TR && gr < N && gc < m) ? __ldg(M + (size_t)gr * m + gc) : 0.0f;
     }
 }
 
 __device__ __forceinline__ void stage_out(const float *t, float *__restrict__ M, int row0, int cs, int m, int N,
-                                          int tid)
+                                          int TR, int tid)
 {
 #pragma unroll 4
     for (int e = tid; e < BM * SW; e += NT) {
         const int r = e / SW, c = e % SW;
         const int gr = row0 + r, gc = cs + c;
-        if (gr < N && gc < m) M[(size_t)gr * m + gc] = t[r * SLD + c];
+        if (r < TR && gr < N && gc < m) M[(size_t)gr * m + gc] = t[r * SLD + c];
     }
 }
 
@@ -246,7 +247,8 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
     const int m = L.m, N = L.N;
     const int ncb = n_colblocks(m), nkc = n_kchunks(m);
     const int local = (int)blockIdx.x - P.base[p];
-    const int row0 = (local / ncb) * BM, col0 = (local % ncb) * BN;
+    const int TR = L.TR > 0 ? L.TR : BM;  // rows of this tile that are real (the MMA always spans 128)
+    const int row0 = (local / ncb) * TR, col0 = (local % ncb) * BN;
     const bool do_mma = !L.skip_mma;
 
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -291,9 +293,18 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         }
         const int prow = tid >> 2, pk = (tid & 3) * 16;  // producer: one row, 16 codes of the chunk
         const int grow = row0 + prow;
-        const bool rok = grow < N;
+        const bool rok = prow < TR && grow < N;
         const float pa = MODE == OIS ? oista_step(L, grow, rok, a) : a;
         const float pthr = pa * L.lam;
+        // the loads of chunk kc + 1 are issued before chunk kc's barrier and
+        // MMA issue, so their latency overlaps the tensor-core work
+        float nz[16], ng[16];
+        if (MODE != ADJ) {
+            load16(Zs, grow, rok, m, pk, nz);
+            load16(Gs, grow, rok, m, pk, ng);
+        } else {
+            load16(L.Gin, grow, rok, m, pk, ng);
+        }
 #pragma unroll 1
         for (int kc = 0; kc < nkc; ++kc) {
             const int s = kc & 1;
@@ -309,20 +320,23 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
             const int k0 = kc * BK + pk;
             float v[16];
             if (MODE != ADJ) {
-                float z[16], g[16];
-                load16(Zs, grow, rok, m, k0, z);
-                load16(Gs, grow, rok, m, k0, g);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const float zn = st_f(fmaf(pa, g[j], z[j]), pthr);
-                    v[j] = L.refresh ? -zn : z[j] - zn;
+                    const float zn = st_f(fmaf(pa, ng[j], nz[j]), pthr);
+                    v[j] = L.refresh ? -zn : nz[j] - zn;
                 }
             } else {
-                float G[16];
-                load16(L.Gin, grow, rok, m, k0, G);
                 const uint32_t bits = mask16(L.mask_in, grow, rok, m, k0);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = ((bits >> j) & 1u) ? G[j] : 0.0f;
+                for (int j = 0; j < 16; ++j) v[j] = ((bits >> j) & 1u) ? ng[j] : 0.0f;
+            }
+            if (kc + 1 < nkc) {
+                if (MODE != ADJ) {
+                    load16(Zs, grow, rok, m, k0 + BK, nz);
+                    load16(Gs, grow, rok, m, k0 + BK, ng);
+                } else {
+                    load16(L.Gin, grow, rok, m, k0 + BK, ng);
+                }
             }
             store_a16<SPLIT>(stage, prow, pk, v);
             fence_proxy_async_smem();
@@ -355,7 +369,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
     // --- epilogue.  Warp w reads TMEM lanes 32 (w % 4).. (the tile rows).
     const int q = warp & 3, cg = warp >> 2;
     const int erow = row0 + 32 * q + lane;
-    const bool eok = erow < N;
+    const bool eok = 32 * q + lane < TR && erow < N;
     const int W = (m + 31) / 32;
     const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
     const float ea = MODE == OIS ? oista_step(L, erow, eok, a) : a;
@@ -374,8 +388,8 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         for (int sl = 0; sl < BN / SW; ++sl) {
             const int cs = col0 + sl * SW;
             if (cs >= m) break;  // uniform
-            stage_in(zt, Zs, row0, cs, m, N, tid);
-            stage_in(gt, Gs, row0, cs, m, N, tid);
+            stage_in(zt, Zs, row0, cs, m, N, TR, tid);
+            stage_in(gt, Gs, row0, cs, m, N, TR, tid);
             __syncthreads();
             float acc[32];
             if (do_mma) {
@@ -404,7 +418,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
             if (c0 + 32 > m) word &= c0 < m ? (1u << (m - c0)) - 1u : 0u;
             if (L.refresh && L.Gout) {  // g' = c + (-z') B: the slice of C replaces g
                 __syncthreads();
-                stage_in(gt, L.C, row0, cs, m, N, tid);
+                stage_in(gt, L.C, row0, cs, m, N, TR, tid);
                 __syncthreads();
             }
 #pragma unroll
@@ -423,8 +437,8 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
                 }
             }
             __syncthreads();
-            if (L.Zout) stage_out(zt, L.Zout, row0, cs, m, N, tid);
-            if (L.Gout) stage_out(gt, L.Gout, row0, cs, m, N, tid);
+            if (L.Zout) stage_out(zt, L.Zout, row0, cs, m, N, TR, tid);
+            if (L.Gout) stage_out(gt, L.Gout, row0, cs, m, N, TR, tid);
             __syncthreads();
         }
     }
@@ -572,7 +586,7 @@ int launch_chunk(const WLayer *Ls, int count, cudaStream_t st)
     P.base[0] = 0;
     for (int i = 0; i < count; ++i) {
         P.L[i] = Ls[i];
-        P.base[i + 1] = P.base[i] + n_items(Ls[i].m, Ls[i].N);
+        P.base[i + 1] = P.base[i] + n_items(Ls[i].m, Ls[i].N, Ls[i].TR);
     }
     if (P.base[count] == 0) return SLISTA_OK;
     auto k = tcw_layer_kernel<SPLIT, MODE, NP>;
@@ -868,6 +882,10 @@ int launch_oista_step(const OistaStep &o, int prec, cudaStream_t st)
     L.LS_out = o.LS_out;
     L.want_ls = o.want_ls;
     L.last = last ? 1 : 0;
+    // one column block per row tile: spread the rows evenly over the SMs
+    const int sms = num_sms();
+    const int rounds = ceil_div(ceil_div(o.N, BM), sms);
+    L.TR = o.N > 0 ? ceil_div(o.N, (long long)rounds * sms) : BM;
     const bool split = prec == SLISTA_PREC_BF16X3;
     return split ? launch_chunk<true, OIS, 1>(&L, 1, st) : launch_chunk<false, OIS, 1>(&L, 1, st);
 }
