@@ -126,6 +126,17 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- ours
 
+def arm_config(w, args, world: int) -> dict:
+    """The workload description shared by both arms of the benchmark."""
+    import math as _m
+    return {"workload": "slista_64x256", "n": w.n, "m": w.m, "N_per_gpu": w.N, "T": w.T, "lam": w.lam,
+            "ckpt_every": max(1, int(_m.ceil(_m.sqrt(max(w.T, 1))))), "prec": args.prec,
+            "oista_prec": args.oista_prec,
+            "step": "gram+L -> slista fwd(masks,ckpt) -> objective+gap -> slista bwd -> oista fwd",
+            "l2": "flushed between timed steps (write of 2x L2 size, untimed)",
+            "parallelism": "dp%d" % world if world > 1 else "single"}
+
+
 def recorded_traffic(part: str):
     """DRAM bytes per call of a bench part from the committed ncu capture
     (profiles/dram_traffic.json), or None when any source file of that part
@@ -345,11 +356,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec,
         "data": "synthetic (seeded; D 64x256 unit-norm Gaussian, x = D z0 + 0.01 noise)",
-        "config": {"workload": "slista_64x256", "n": n, "m": m, "N_per_gpu": N, "T": T, "lam": lam,
-                   "ckpt_every": K, "prec": args.prec, "oista_prec": args.oista_prec,
-                   "step": "gram+L -> slista fwd(masks,ckpt) -> objective+gap -> slista bwd -> oista fwd",
-                   "l2": "flushed between timed steps (write of 2x L2 size, untimed)",
-                   "parallelism": "dp%d" % world if world > 1 else "single"},
+        "config": arm_config(w, args, world),
         "clocks": clocks, "e2e": e2e,
         "gpu_launches": int(sum(launches_per_step.values()) * args.steps),
         "roofline": roofline, "parts": rooflines,
@@ -419,7 +426,7 @@ def run_reference(args, rank, world):
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
-            "config": {"workload": "slista_64x256", "n": w.n, "m": w.m, "N_per_gpu": w.N, "T": w.T},
+            "config": arm_config(w, args, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d samples per step of the %d-sample workload; per-dictionary L "
                                        "charged pro rata" % (ns, w.N)},

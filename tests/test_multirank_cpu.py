@@ -32,8 +32,9 @@ def _worker(rank, world, port, out):
     got = bench.max_over_ranks(ms, world, "cpu")
     val = bench.job_throughput(10000, world, got)
     w = synth.slista_64x256(seed=rank, N=16, T=2)
-    ref = bench.run_reference(type("A", (), {"N": 16, "T": 2, "cpu_samples": 1, "warmup": 0, "steps": 1})(),
-                              rank, world)
+    args = type("A", (), {"N": 16, "T": 2, "cpu_samples": 1, "warmup": 0, "steps": 1, "prec": "bf16x3",
+                          "oista_prec": "bf16x3"})()
+    ref = bench.run_reference(args, rank, world)
     out[rank] = (got, val, float(w.X[0, 0]), ref is None)
     dist.barrier()
     dist.destroy_process_group()
