@@ -109,7 +109,9 @@ struct Cfg {
     static constexpr bool LO_RES = SPLIT && MP <= 128;
     static constexpr bool LO_STREAM = SPLIT && MP > 128;
     static constexpr int SMEM_OPER = OPER + (LO_RES ? OPER : 0) + (LO_STREAM ? 2 * CHUNK : 0);
-    static constexpr int SMEM = SMEM_OPER + 1024 /*align*/ + 64 /*barriers, tmem slot, B_lo address*/;
+    static constexpr int STAGE_OFF = SMEM_OPER + 64;  // after the barriers, tmem slot and B_lo address
+    static constexpr int SMEM = STAGE_OFF + 1024 /*align*/;
+    static constexpr int SMEM_STAGED = SMEM + 16 * 32 * 16 * 4;  // + per-warp staging (forward kernel)
     static constexpr int T_G = 0, T_AHI = MP, T_ALO = MP + MP / 2;
     static constexpr int COLS_USED = SPLIT ? 2 * MP : MP + MP / 2;
     static constexpr int TMEM_COLS = COLS_USED <= 32 ? 32 : COLS_USED <= 64 ? 64 : COLS_USED <= 128 ? 128
@@ -190,6 +192,13 @@ struct TcEngine {
     }
 
     __device__ __forceinline__ uint32_t taddr(int col) const { return tmem + lane_base + (uint32_t)col; }
+
+    // this warp's 32 x 16-float staging area in shared memory
+    __device__ __forceinline__ float *warp_stage() const
+    {
+        float *base = reinterpret_cast<float *>(__cvta_shared_to_generic((size_t)(sB_u + CF::STAGE_OFF)));
+        return base + (threadIdx.x >> 5) * 32 * 16;
+    }
 
     __device__ __forceinline__ void load_stage(int s, int chunk)
     {
@@ -333,6 +342,34 @@ __device__ __forceinline__ void row16_to_tmem(const TcEngine<MP, SPLIT> &E, cons
 // Index of (layer s, tile, lane quadrant, code col, lane) in the adjoint's
 // internal buffers: for one code the 32 rows of a warp are consecutive, so
 // the row-per-lane accesses of the layer kernels are coalesced.
+// Row-per-lane 16-code pieces made coalesced through a per-warp staging area
+// of 32 rows x 16 floats in shared memory (column c of row r at
+// r * 16 + (c ^ (r & 15))): a lane writes or reads its own row there, and the
+// global side moves two 64-byte row segments per warp instruction.  Used for
+// the checkpoint and Z stores of the forward, whose layout (sample-major rows)
+// is the ABI's.
+__device__ __forceinline__ void stage_put(float *buf, const float (&v)[16])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) buf[lane * 16 + (c ^ (lane & 15))] = v[c];
+    __syncwarp();
+}
+
+// rows rbase .. rbase+31 (the first nrow real) x codes c0 .. c0+15 of a row-major N x m matrix
+__device__ __noinline__ void stage_to_global(const float *buf, float *M, int rbase, int nrow, int m, int c0)
+{
+    const int lane = threadIdx.x & 31;
+    const int h = lane >> 4, c = lane & 15;
+    if (c0 + c < m)
+#pragma unroll 1
+        for (int i = 0; i < 16; ++i) {
+            const int r = 2 * i + h;
+            if (r < nrow) M[(size_t)(rbase + r) * m + c0 + c] = buf[r * 16 + (c ^ (r & 15))];
+        }
+    __syncwarp();
+}
+
 template <int MP>
 __device__ __forceinline__ size_t lane_index(int s, int ntiles, int tile, int quad, int col, int lane)
 {
@@ -421,18 +458,20 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
                 if (ckpt && t > 0 && t % p.K == 0) {
                     // checkpoint (z^(t), g^(t)) every K layers, layout of slista_forward
                     float *ck = ckpt + (size_t)(t / p.K - 1) * 2 * N * m;
+                    float *wbuf = E.warp_stage();
+                    const int rbase = tile * TR + quad * 32;
+                    const int nrow = max(0, min(min(32, TR - quad * 32), N - rbase));
 #pragma unroll
                     for (int pc = 0; pc < CF::NPC; ++pc) {
                         const int col0 = cbase + 16 * pc;
                         float gv[16];
                         tmem_ld16(E.taddr(CF::T_G + col0), gv);
-                        if (row_ok)
+                        stage_put(wbuf, gv);
+                        stage_to_global(wbuf, ck + (size_t)N * m, rbase, nrow, m, col0);
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                if (col0 + j < m) {
-                                    ck[(size_t)row * m + col0 + j] = z[16 * pc + j];
-                                    ck[(size_t)N * m + (size_t)row * m + col0 + j] = gv[j];
-                                }
+                        for (int j = 0; j < 16; ++j) gv[j] = z[16 * pc + j];
+                        stage_put(wbuf, gv);
+                        stage_to_global(wbuf, ck, rbase, nrow, m, col0);
                     }
                 }
             }
@@ -500,10 +539,17 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
         }
         if (E.failed) break;
         if constexpr (!RECOMP) {
-            if (row_ok)
+            float *wbuf = E.warp_stage();
+            const int rbase = tile * TR + quad * 32;
+            const int nrow = max(0, min(min(32, TR - quad * 32), N - rbase));
 #pragma unroll
-                for (int j = 0; j < CF::CW; ++j)
-                    if (cbase + j < m) p.Z[(size_t)row * m + cbase + j] = z[j];
+            for (int pc = 0; pc < CF::NPC; ++pc) {
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = z[16 * pc + j];
+                stage_put(wbuf, v);
+                stage_to_global(wbuf, p.Z, rbase, nrow, m, cbase + 16 * pc);
+            }
         }
         E.tile_done();
     }
@@ -675,8 +721,8 @@ int launch_mp(const PgdArgs &a, void *ws, cudaStream_t st)
     int grid = 0;
     tiling(a.N, &p.TR, &grid);
     auto k = tc_pgd_forward_kernel<MP, SPLIT, false>;
-    SLISTA_CUDA_TRY(allow_smem(k, CF::SMEM));
-    k<<<grid, CF::NT, CF::SMEM, st>>>(p);
+    SLISTA_CUDA_TRY(allow_smem(k, CF::SMEM_STAGED));
+    k<<<grid, CF::NT, CF::SMEM_STAGED, st>>>(p);
     return check_launch("tc_pgd_forward_kernel");
 }
 
