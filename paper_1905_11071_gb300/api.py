@@ -229,7 +229,7 @@ def train_step_sizes(alpha0: torch.Tensor, g: Gram, lam: float, steps: int = 50,
     a = alpha.clone().requires_grad_(True)
     loss = slista_loss(a, g, lam)
     loss.backward()
-    cur = float(loss)
+    cur = float(loss.detach())
     grad = a.grad.detach().clone()
     hist.append(cur)
     if lr0 is None:

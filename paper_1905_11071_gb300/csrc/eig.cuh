@@ -184,7 +184,16 @@ __host__ __device__ inline float start_vector(int a)
 // Upper end of a bracket of the largest eigenvalue of the symmetric
 // tridiagonal matrix (d[0..k-1], e[0..k-2]) by Sturm multisection over one
 // warp (33 trial points per round).  e2 receives e^2.
-__device__ inline float tridiag_max_eig_warp(const float *d, const float *e, float *e2, int k)
+// With a lower bound `ref` of that eigenvalue (e.g. the lower end of the
+// bracket for a leading principal submatrix, whose largest eigenvalue is never
+// above it: Cauchy interlacing) and a trial upper end `top`, the first round
+// tests the 32 points of (ref, top] instead: if no eigenvalue lies above
+// `top`, the bracket found there is final and *within = true (one round
+// instead of a full multisection).  *lo_out (if given) receives the lower end
+// of the final bracket.
+__device__ inline float tridiag_max_eig_warp(const float *d, const float *e, float *e2, int k,
+                                             float ref = -INFINITY, float top = -INFINITY, bool *within = nullptr,
+                                             float *lo_out = nullptr)
 {
     const int lane = threadIdx.x & 31;
     // Gershgorin bracket of the spectrum, one row per lane, then max over the warp
@@ -205,6 +214,22 @@ __device__ inline float tridiag_max_eig_warp(const float *d, const float *e, flo
     __syncwarp();
     const float pivmin = fmaxf(scale * 1e-30f, 1e-37f);
     hi = hi + 2e-7f * scale;
+    if (within) *within = false;
+    lo = fmaxf(lo, ref);
+    if (top > lo && top < hi) {
+        const float x = lo + (top - lo) * (float)(lane + 1) / 32.0f;
+        const bool above_all = sturm_count(d, e2, k, x, pivmin) == k;
+        const unsigned b = __ballot_sync(0xffffffffu, above_all);
+        if (b) {
+            const int f = __ffs(b) - 1;
+            hi = lo + (top - lo) * (float)(f + 1) / 32.0f;
+            lo = f > 0 ? lo + (top - lo) * (float)f / 32.0f : lo;
+            if (within) *within = true;
+            if (lo_out) *lo_out = lo;
+            return hi;
+        }
+        lo = top;  // an eigenvalue lies above the tested interval
+    }
     for (int round = 0; round < 8 && hi - lo > 1.2e-7f * scale; ++round) {
         const float x = lo + (hi - lo) * (float)(lane + 1) / 33.0f;
         const bool above_all = sturm_count(d, e2, k, x, pivmin) == k;
@@ -215,6 +240,7 @@ __device__ inline float tridiag_max_eig_warp(const float *d, const float *e, flo
         lo = nlo;
         hi = nhi;
     }
+    if (lo_out) *lo_out = lo;
     return hi;
 }
 
@@ -223,20 +249,26 @@ __device__ inline float tridiag_max_eig_warp(const float *d, const float *e, flo
 // builds the tridiagonal T_J whose largest eigenvalue (the top Ritz value)
 // converges to that of A from below; in finite precision the extreme Ritz
 // values stay accurate without reorthogonalisation (Paige).  J = k steps are
-// run when k <= 16 (T_k is then similar to A); otherwise the top Ritz value
-// is taken after 16 steps and then every 8 more, up to min(k, LANCZOS_JMAX),
-// until it moves by less than 2e-7 (relative) over the last 8 steps.  (On
-// the supports of the 64 x 256 workload - |S| = 33 .. 160, B_SS or D_S D_S^T -
-// the top Ritz value is within 2.2e-7 of lambda_max after 24 steps and the
-// rule stops at 24.2 steps on average without an error above 1e-6.)  A is in
-// shared memory with leading dimension lda.
+// run when k <= LANCZOS_J0 (T_k is then similar to A); otherwise the top
+// Ritz value is bracketed after LANCZOS_J0 steps and then every
+// LANCZOS_DJ more, up to min(k, LANCZOS_JMAX), until it has moved by less
+// than 2e-7 (relative) since the previous check: that test is one
+// multisection round over the interval just above the previous bracket,
+// and only when it fails is the new Ritz value bracketed in full.  (On the
+// supports of the 64 x 256 workload - |S| = 11 .. 160, B_SS or D_S D_S^T -
+// the top Ritz value is within 1e-8 of lambda_max (FP64 model) when the rule
+// stops, at 12 - 14 steps on average.)  A is in shared memory with leading
+// dimension lda.  j0 replaces LANCZOS_J0 (j0 >= k: the full dimension, at
+// most LANCZOS_JMAX steps).
 // q, qp: k floats; al, be, e2: LANCZOS_JMAX floats of warp scratch.
 // RPL = rows per lane (>= ceil(k / 32)).
+constexpr int LANCZOS_J0 = 10;
+constexpr int LANCZOS_DJ = 2;
 constexpr int LANCZOS_JMAX = 64;
 
 template <int RPL>
 __device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q, float *qp, float *al, float *be,
-                                       float *e2)
+                                       float *e2, int j0 = LANCZOS_J0)
 {
     constexpr int JMAX = LANCZOS_JMAX;
     const int lane = threadIdx.x & 31;
@@ -256,9 +288,9 @@ __device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q,
     }
     __syncwarp();
     float beta_prev = 0.0f;
-    float theta_prev = -INFINITY, theta = 0.0f;
+    float ref = -INFINITY, theta = -INFINITY;
     int j = 0;
-    int target = k <= 16 ? k : 16;
+    int target = min(min(k, j0), JMAX);
     bool done = false;
 #pragma unroll 1
     for (;;) {
@@ -323,12 +355,11 @@ __device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q,
             __syncwarp();
             beta_prev = beta;
         }
-        theta = tridiag_max_eig_warp(al, be, e2, j);
-        if (done) break;                                        // exhausted
-        if (theta - theta_prev <= 2e-7f * fabsf(theta)) break;  // converged
+        bool conv = false;
+        theta = tridiag_max_eig_warp(al, be, e2, j, ref, theta + 2e-7f * fabsf(theta), &conv, &ref);
+        if (done || conv) break;  // exhausted, or moved by less than 2e-7 since the last check
         if (j >= JMAX || j >= k) break;
-        theta_prev = theta;
-        target = min(min(j + 8, k), JMAX);
+        target = min(min(j + LANCZOS_DJ, k), JMAX);
     }
     return (double)theta;
 }

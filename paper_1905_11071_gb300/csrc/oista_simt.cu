@@ -299,11 +299,11 @@ __device__ inline float max_diag(const float *A, int lda, int k)
 
 // ---------------------------------------------------------------------------
 // Register-resident solver for 2 <= |S| <= SMALL_K: lane a holds row a of
-// B_SS (ar[]) and entry a of the Lanczos vectors; k steps of the three-term
-// recurrence give the tridiagonal T_k (similar to B_SS), whose largest
-// eigenvalue is bracketed by Sturm multisection (the method of
-// eig::lanczos_max_eig_warp for k <= 32).  A diagonal B_SS gives its largest
-// entry exactly.
+// B_SS (ar[]) and entry a of the Lanczos vectors; the three-term recurrence
+// and the stopping rule of eig::lanczos_max_eig_warp (all k steps, T_k
+// similar to B_SS, when k <= LANCZOS_J0), the largest eigenvalue of the
+// tridiagonal bracketed by Sturm multisection.  A diagonal B_SS gives its
+// largest entry exactly.
 // ---------------------------------------------------------------------------
 struct WarpEigS {
     float al[SMALL_K], be[SMALL_K], e2[SMALL_K];
@@ -337,40 +337,52 @@ __device__ double solve_small(const float *__restrict__ B, int m, const int *idx
     for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
     q *= rsqrtf(nrm);
     float qp = 0.0f, beta_prev = 0.0f;
+    float ref = -INFINITY, theta = -INFINITY;
     int j = 0;
+    int target = k <= eig::LANCZOS_J0 ? k : eig::LANCZOS_J0;
 #pragma unroll 1
-    for (; j < k; ++j) {
-        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    for (;;) {
+        bool done = false;
+#pragma unroll 1
+        for (; j < target; ++j) {
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
 #pragma unroll
-        for (int b = 0; b < SMALL_K; b += 4) {
-            s0 = fmaf(ar[b], __shfl_sync(0xffffffffu, q, b), s0);
-            s1 = fmaf(ar[b + 1], __shfl_sync(0xffffffffu, q, b + 1), s1);
-            s2 = fmaf(ar[b + 2], __shfl_sync(0xffffffffu, q, b + 2), s2);
-            s3 = fmaf(ar[b + 3], __shfl_sync(0xffffffffu, q, b + 3), s3);
-        }
-        const float sv = (s0 + s1) + (s2 + s3);
-        float alpha = sv * q;
+            for (int b = 0; b < SMALL_K; b += 4) {
+                s0 = fmaf(ar[b], __shfl_sync(0xffffffffu, q, b), s0);
+                s1 = fmaf(ar[b + 1], __shfl_sync(0xffffffffu, q, b + 1), s1);
+                s2 = fmaf(ar[b + 2], __shfl_sync(0xffffffffu, q, b + 2), s2);
+                s3 = fmaf(ar[b + 3], __shfl_sync(0xffffffffu, q, b + 3), s3);
+            }
+            const float sv = (s0 + s1) + (s2 + s3);
+            float alpha = sv * q;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
-        const float w = on ? sv - alpha * q - beta_prev * qp : 0.0f;
-        float bb = w * w;
+            for (int o = 16; o > 0; o >>= 1) alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+            const float w = on ? sv - alpha * q - beta_prev * qp : 0.0f;
+            float bb = w * w;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bb += __shfl_xor_sync(0xffffffffu, bb, o);
-        const float beta = sqrtf(bb);
-        if (lane == 0) {
-            al[j] = alpha;
-            be[j] = beta;
+            for (int o = 16; o > 0; o >>= 1) bb += __shfl_xor_sync(0xffffffffu, bb, o);
+            const float beta = sqrtf(bb);
+            if (lane == 0) {
+                al[j] = alpha;
+                be[j] = beta;
+            }
+            if (beta <= 1e-6f * fabsf(alpha) || j + 1 == k) {  // invariant subspace or full dimension
+                ++j;
+                done = true;
+                break;
+            }
+            qp = q;
+            q = w * (1.0f / beta);
+            beta_prev = beta;
         }
-        if (beta <= 1e-6f * fabsf(alpha) || j + 1 == k) {  // invariant subspace or full dimension
-            ++j;
-            break;
-        }
-        qp = q;
-        q = w * (1.0f / beta);
-        beta_prev = beta;
+        __syncwarp();
+        // the stopping rule of eig::lanczos_max_eig_warp
+        bool conv = false;
+        theta = eig::tridiag_max_eig_warp(al, be, e2, j, ref, theta + 2e-7f * fabsf(theta), &conv, &ref);
+        if (done || conv) break;
+        target = min(j + eig::LANCZOS_DJ, k);
     }
-    __syncwarp();
-    return (double)eig::tridiag_max_eig_warp(al, be, e2, j);
+    return (double)theta;
 }
 
 // Takes the next sample of list class cls of layer t (one warp); -1 when empty.
