@@ -29,7 +29,9 @@
  * Conventions for every entry point:
  *   - Every pointer is a DEVICE pointer owned by the caller unless stated
  *     otherwise; the library allocates no memory.  Scratch space is passed as
- *     (ws, ws_bytes); size it with slista_workspace_bytes().
+ *     (ws, ws_bytes); size it with slista_workspace_bytes().  ws must start on
+ *     a 256-byte boundary (cudaMalloc and PyTorch allocations do), else
+ *     SLISTA_ERR_WORKSPACE.
  *   - Calls are asynchronous on the CUDA stream passed as `stream`
  *     (a cudaStream_t cast to void*; NULL = legacy default stream).
  *   - Return value: SLISTA_OK (0) or a negative SLISTA_ERR_* code; the message
@@ -59,7 +61,7 @@ extern "C" {
 #define SLISTA_OK               0
 #define SLISTA_ERR_ARG         -1  /* null pointer, non-positive size, alpha <= 0, lam < 0 ... */
 #define SLISTA_ERR_UNSUPPORTED -2  /* shape or precision not built */
-#define SLISTA_ERR_WORKSPACE   -3  /* ws_bytes smaller than slista_workspace_bytes() */
+#define SLISTA_ERR_WORKSPACE   -3  /* ws_bytes smaller than slista_workspace_bytes(), or ws not 256-byte aligned */
 #define SLISTA_ERR_CUDA        -4  /* a CUDA runtime call failed */
 #define SLISTA_ERR_TIMEOUT     -5  /* a kernel's bounded wait expired (see slista_device_status) */
 

@@ -97,6 +97,10 @@ int check_lam(float lam)
     return SLISTA_OK;
 }
 
+// The kernels move the workspace's operand tiles with 16-byte vector loads
+// and bulk copies, which need aligned addresses.
+bool ws_aligned(const void *ws) { return (reinterpret_cast<uintptr_t>(ws) & 255) == 0; }
+
 int forward_common(const PgdArgs &a, int prec, void *ws, size_t ws_bytes, cudaStream_t st, const char *name)
 {
     SLISTA_REQUIRE(valid_prec(prec), SLISTA_ERR_ARG, "%s: unknown precision %d", name, prec);
@@ -109,13 +113,13 @@ int forward_common(const PgdArgs &a, int prec, void *ws, size_t ws_bytes, cudaSt
                    "%s: tensor-core path supports m <= 1024 (got %d)", name, a.m);
     if (!tc::supported(a.m)) {  // m > 256: one launch per layer
         const size_t need = tcw::forward_ws_bytes(a.m, a.N);
-        SLISTA_REQUIRE(ws_bytes >= need && ws != nullptr, SLISTA_ERR_WORKSPACE,
-                       "%s: workspace of %zu bytes needed, %zu given", name, need, ws_bytes);
+        SLISTA_REQUIRE(ws_bytes >= need && ws != nullptr && ws_aligned(ws), SLISTA_ERR_WORKSPACE,
+                       "%s: workspace of %zu bytes (256-byte aligned) needed, %zu given", name, need, ws_bytes);
         return tcw::launch_forward(a, prec, ws, st);
     }
     const size_t need = tc::forward_ws_bytes(a.m);
-    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws != nullptr), SLISTA_ERR_WORKSPACE,
-                   "%s: workspace of %zu bytes needed, %zu given", name, need, ws_bytes);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws != nullptr && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
+                   "%s: workspace of %zu bytes (256-byte aligned) needed, %zu given", name, need, ws_bytes);
     return tc::launch_forward(a, prec, ws, st);
 }
 
@@ -265,8 +269,8 @@ int slista_backward(const float *B, const float *C, int m, int N, float lam, con
     const size_t need = wide  ? tcw::backward_ws_bytes(m, N, T, K)
                         : tcp ? tc::backward_ws_bytes(m, N, T, K)
                               : simt::backward_ws_bytes(m, N, T, K);
-    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
-                   "slista_backward: workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
+                   "slista_backward: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
     BwdArgs a{B, C, m, N, lam, alpha, T, masks, ckpt, K, gZ, dalpha};
     if (wide) return tcw::launch_backward(a, prec, ws, as_stream(stream));
     if (tcp) return tc::launch_backward(a, prec, ws, as_stream(stream));
@@ -287,8 +291,8 @@ int oista_forward(const float *B, const float *C, const float *D, int n, int m, 
     int rc = check_lam(lam);
     if (rc) return rc;
     const size_t need = simt::oista_ws_bytes(m, N, T, prec);
-    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
-                   "oista_forward: workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
+                   "oista_forward: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
     OistaArgs a{B, C, D, D ? n : 0, m, N, lam, L, T, Z, LS, accepted, prec};
     return simt::launch_oista(a, ws, as_stream(stream));
 }
@@ -379,8 +383,8 @@ int slista_forward_batched(const slista_problem_t *problems, int count, int T, i
     int rc = batch_args(problems, count, T, prec, ckpt_every, false, v, "slista_forward_batched");
     if (rc) return rc;
     const size_t need = tcw::forward_batch_ws_bytes(v.data(), count);
-    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
-                   "slista_forward_batched: workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
+                   "slista_forward_batched: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
     return tcw::forward_batch(v.data(), count, T, ckpt_every, prec, ws, as_stream(stream));
 }
 
@@ -392,8 +396,8 @@ int slista_backward_batched(const slista_problem_t *problems, int count, int T, 
     int rc = batch_args(problems, count, T, prec, ckpt_every, true, v, "slista_backward_batched");
     if (rc) return rc;
     const size_t need = tcw::backward_batch_ws_bytes(v.data(), count, T, ckpt_every);
-    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || ws), SLISTA_ERR_WORKSPACE,
-                   "slista_backward_batched: workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
+                   "slista_backward_batched: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
     return tcw::backward_batch(v.data(), count, T, ckpt_every, prec, ws, as_stream(stream));
 }
 

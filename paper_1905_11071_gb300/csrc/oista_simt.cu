@@ -73,41 +73,40 @@ struct OistaWs {
     uint8_t *tiles;           // split B for the tensor-core layers (after Dt)
     int N, W;
 
+    // Every array starts on a 256-byte boundary (the layer kernels read rows
+    // of Zs, Gs and Dt with 16-byte vector loads).
+    static size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
     static size_t bytes(int m, int N, int T)
     {
         const size_t W = (size_t)(m + 31) / 32;
-        return sizeof(double) * (size_t)N + 2 * sizeof(float) * (size_t)N * m + 2 * sizeof(uint32_t) * N * W +
-               sizeof(int) * ((2 + 2 * NCLS) * (size_t)N + 2 * NCLS + NCLS * (size_t)T) +
-               sizeof(float) * (size_t)m * 256 + 16;
+        return a256(sizeof(double) * (size_t)N) + 2 * a256(sizeof(float) * (size_t)N * m) +
+               2 * a256(sizeof(uint32_t) * N * W) + 2 * a256(sizeof(int) * (size_t)N) +
+               a256(sizeof(int) * 2 * NCLS * (size_t)N) + a256(sizeof(int) * (2 * NCLS + NCLS * (size_t)T)) +
+               a256(sizeof(float) * (size_t)m * 256) + 256;
     }
     static OistaWs carve(void *ws, int m, int N, int T)
     {
         const size_t W = (size_t)(m + 31) / 32;
-        char *p = reinterpret_cast<char *>(ws);
+        char *p = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(ws) + 255) & ~(uintptr_t)255);
+        auto take = [&p](size_t b) {
+            char *q = p;
+            p += a256(b);
+            return q;
+        };
         OistaWs o;
-        o.LSv = reinterpret_cast<double *>(p);
-        p += sizeof(double) * (size_t)N;
-        o.Zs = reinterpret_cast<float *>(p);
-        p += sizeof(float) * (size_t)N * m;
-        o.Gs = reinterpret_cast<float *>(p);
-        p += sizeof(float) * (size_t)N * m;
-        o.Scur = reinterpret_cast<uint32_t *>(p);
-        p += sizeof(uint32_t) * (size_t)N * W;
-        o.Sprev = reinterpret_cast<uint32_t *>(p);
-        p += sizeof(uint32_t) * (size_t)N * W;
-        o.flag = reinterpret_cast<int *>(p);
-        p += sizeof(int) * (size_t)N;
-        o.valid = reinterpret_cast<int *>(p);
-        p += sizeof(int) * (size_t)N;
-        o.list = reinterpret_cast<int *>(p);
-        p += sizeof(int) * 2 * NCLS * (size_t)N;
-        o.counter = reinterpret_cast<int *>(p);
-        p += sizeof(int) * 2 * NCLS;
-        o.qpos = reinterpret_cast<int *>(p);
-        p += sizeof(int) * NCLS * (size_t)T;
-        o.Dt = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
-        o.tiles = reinterpret_cast<uint8_t *>(
-            (reinterpret_cast<uintptr_t>(o.Dt + (size_t)m * 256) + 255) & ~(uintptr_t)255);
+        o.LSv = reinterpret_cast<double *>(take(sizeof(double) * (size_t)N));
+        o.Zs = reinterpret_cast<float *>(take(sizeof(float) * (size_t)N * m));
+        o.Gs = reinterpret_cast<float *>(take(sizeof(float) * (size_t)N * m));
+        o.Scur = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)N * W));
+        o.Sprev = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (size_t)N * W));
+        o.flag = reinterpret_cast<int *>(take(sizeof(int) * (size_t)N));
+        o.valid = reinterpret_cast<int *>(take(sizeof(int) * (size_t)N));
+        o.list = reinterpret_cast<int *>(take(sizeof(int) * 2 * NCLS * (size_t)N));
+        // counter and qpos adjacent: one memset clears both at the start of a call
+        o.counter = reinterpret_cast<int *>(take(sizeof(int) * (2 * NCLS + NCLS * (size_t)T)));
+        o.qpos = o.counter + 2 * NCLS;
+        o.Dt = reinterpret_cast<float *>(take(sizeof(float) * (size_t)m * 256));
+        o.tiles = reinterpret_cast<uint8_t *>(p);
         o.N = N;
         o.W = (int)W;
         return o;

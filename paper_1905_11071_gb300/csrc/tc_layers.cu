@@ -62,7 +62,7 @@ constexpr int REFRESH = 8;
 __device__ __forceinline__ void load_c16(const float *__restrict__ C, int row, bool row_ok, int m, int col0,
                                          uint32_t (&v)[16])
 {
-    if (row_ok && (m & 3) == 0) {
+    if (row_ok && (m & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0) {
         const float4 *src = reinterpret_cast<const float4 *>(C + (size_t)row * m + col0);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {

@@ -43,8 +43,7 @@ constexpr int TILE_PAIR = 2 * TILE_B;            // hi then lo, as stored in the
 constexpr int REFRESH = 8;
 constexpr uint32_t IDESC = idesc_bf16(BM, BN);
 constexpr int SW = 128;       // epilogue slice: columns staged through shared memory at a time
-constexpr int SLD = SW + 1;   // row stride of a staged slice (odd: conflict-free column access)
-constexpr int EPI_SMEM = 2 * BM * SLD * 4;
+constexpr int EPI_SMEM = 2 * BM * SW * 4;  // the z and g slices
 
 enum Mode { FWD = 0, ADJ = 1, OIS = 2 };
 
@@ -116,7 +115,7 @@ inline int n_items(int m, int N, int TR = 0) { return ceil_div(N, TR > 0 ? TR : 
 // matrix, zero outside the matrix or when M is null.
 __device__ __forceinline__ void load16(const float *__restrict__ M, int row, bool ok, int m, int k0, float (&v)[16])
 {
-    if (M != nullptr && ok && (m & 3) == 0) {
+    if (M != nullptr && ok && (m & 3) == 0 && (reinterpret_cast<uintptr_t>(M) & 15) == 0) {
         const float4 *src = reinterpret_cast<const float4 *>(M + (size_t)row * m + k0);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -171,28 +170,76 @@ __device__ __forceinline__ void store_a16(uint8_t *stage, int row, int kl, const
     }
 }
 
-// Rows [row0, row0 + BM) x columns [cs, cs + SW) of a row-major N x m matrix
-// into a staged slice (row stride SLD), zero outside the matrix or when M is
-// null; each warp moves 32 consecutive floats of a row.
-__device__ __forceinline__ void stage_in(float *t, const float *__restrict__ M, int row0, int cs, int m, int N,
-                                         int TR, int tid)
+// A staged slice holds rows 0..BM-1 x columns 0..SW-1 of the block, row r
+// at r * SW, its 16-byte units (4 columns) permuted by XOR with r % 8: a
+// warp's 16-byte accesses to one row (global side) or to 8 consecutive rows
+// at one unit (epilogue side) are then free of bank conflicts.
+__device__ __forceinline__ int sidx(int r, int c) { return r * SW + ((((c >> 2) ^ (r & 7)) << 2) | (c & 3)); }
+
+// Rows [row0, row0 + TR) x columns [cs, cs + SW) of the row-major N x m
+// matrices M0 (and M1 when NM = 2) into the staged slices t0 (t1), zero
+// outside the matrix or when the matrix is null.  With 16-byte aligned rows
+// each warp moves one 512-byte row segment per instruction and a thread
+// issues all of its loads before its first shared-memory store.
+template <int NM>
+__device__ __forceinline__ void stage_in(float *t0, const float *__restrict__ M0, float *t1,
+                                         const float *__restrict__ M1, int row0, int cs, int m, int N, int TR, int tid)
 {
+    const bool vec = (m & 3) == 0 && (reinterpret_cast<uintptr_t>(M0) & 15) == 0 &&
+                     (NM == 1 || (reinterpret_cast<uintptr_t>(M1) & 15) == 0);
+    if (vec) {
+        constexpr int V = SW / 4;         // 16-byte units per slice row
+        constexpr int PER = BM * V / NT;  // units per thread and matrix
+        float4 x0[PER], x1[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT, r = e / V, c = (e % V) * 4;
+            const int gr = row0 + r, gc = cs + c;
+            const bool ok = r < TR && gr < N && gc < m;
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            x0[k] = (ok && M0 != nullptr) ? __ldg(reinterpret_cast<const float4 *>(M0 + (size_t)gr * m + gc)) : zero;
+            if (NM == 2)
+                x1[k] = (ok && M1 != nullptr) ? __ldg(reinterpret_cast<const float4 *>(M1 + (size_t)gr * m + gc))
+                                              : zero;
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * NT, r = e / V, c = (e % V) * 4;
+            *reinterpret_cast<float4 *>(t0 + sidx(r, c)) = x0[k];
+            if (NM == 2) *reinterpret_cast<float4 *>(t1 + sidx(r, c)) = x1[k];
+        }
+        return;
+    }
 #pragma unroll 4
     for (int e = tid; e < BM * SW; e += NT) {
         const int r = e / SW, c = e % SW;
         const int gr = row0 + r, gc = cs + c;
-        t[r * SLD + c] = (M != nullptr && r < TR && gr < N && gc < m) ? __ldg(M + (size_t)gr * m + gc) : 0.0f;
+        const bool ok = r < TR && gr < N && gc < m;
+        t0[sidx(r, c)] = (ok && M0 != nullptr) ? __ldg(M0 + (size_t)gr * m + gc) : 0.0f;
+        if (NM == 2) t1[sidx(r, c)] = (ok && M1 != nullptr) ? __ldg(M1 + (size_t)gr * m + gc) : 0.0f;
     }
 }
 
+// The reverse of stage_in for one matrix (rows r < TR inside N x m).
 __device__ __forceinline__ void stage_out(const float *t, float *__restrict__ M, int row0, int cs, int m, int N,
                                           int TR, int tid)
 {
+    if ((m & 3) == 0 && (reinterpret_cast<uintptr_t>(M) & 15) == 0) {
+        constexpr int V = SW / 4;
+#pragma unroll 4
+        for (int e = tid; e < BM * V; e += NT) {
+            const int r = e / V, c = (e % V) * 4;
+            const int gr = row0 + r, gc = cs + c;
+            if (r < TR && gr < N && gc < m)
+                *reinterpret_cast<float4 *>(M + (size_t)gr * m + gc) = *reinterpret_cast<const float4 *>(t + sidx(r, c));
+        }
+        return;
+    }
 #pragma unroll 4
     for (int e = tid; e < BM * SW; e += NT) {
         const int r = e / SW, c = e % SW;
         const int gr = row0 + r, gc = cs + c;
-        if (r < TR && gr < N && gc < m) M[(size_t)gr * m + gc] = t[r * SLD + c];
+        if (r < TR && gr < N && gc < m) M[(size_t)gr * m + gc] = t[sidx(r, c)];
     }
 }
 
@@ -383,13 +430,12 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         // segment; thread (q, cg) finishes columns [32 cg, 32 cg + 32) of
         // the slice for its row.
         float *zt = reinterpret_cast<float *>(smem);
-        float *gt = zt + BM * SLD;
+        float *gt = zt + BM * SW;
 #pragma unroll 1
         for (int sl = 0; sl < BN / SW; ++sl) {
             const int cs = col0 + sl * SW;
             if (cs >= m) break;  // uniform
-            stage_in(zt, Zs, row0, cs, m, N, TR, tid);
-            stage_in(gt, Gs, row0, cs, m, N, TR, tid);
+            stage_in<2>(zt, Zs, gt, Gs, row0, cs, m, N, TR, tid);
             __syncthreads();
             float acc[32];
             if (do_mma) {
@@ -406,26 +452,45 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
                 for (int j = 0; j < 32; ++j) acc[j] = 0.0f;
             }
             const int r = 32 * q + lane;
-            float *zr = zt + r * SLD + cg * 32, *gr = gt + r * SLD + cg * 32;
             uint32_t word = 0u;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float zn = st_f(fmaf(ea, gr[j], zr[j]), ethr);
-                zr[j] = zn;
-                word |= (uint32_t)(zn != 0.0f) << j;
+            for (int u = 0; u < 8; ++u) {
+                float4 *zp = reinterpret_cast<float4 *>(zt + sidx(r, cg * 32 + 4 * u));
+                const float4 g4 = *reinterpret_cast<const float4 *>(gt + sidx(r, cg * 32 + 4 * u));
+                float4 z4 = *zp;
+                z4.x = st_f(fmaf(ea, g4.x, z4.x), ethr);
+                z4.y = st_f(fmaf(ea, g4.y, z4.y), ethr);
+                z4.z = st_f(fmaf(ea, g4.z, z4.z), ethr);
+                z4.w = st_f(fmaf(ea, g4.w, z4.w), ethr);
+                *zp = z4;
+                word |= ((uint32_t)(z4.x != 0.0f) | (uint32_t)(z4.y != 0.0f) << 1 | (uint32_t)(z4.z != 0.0f) << 2 |
+                         (uint32_t)(z4.w != 0.0f) << 3)
+                        << (4 * u);
             }
             const int c0 = cs + cg * 32;  // first code of this thread's word
             if (c0 + 32 > m) word &= c0 < m ? (1u << (m - c0)) - 1u : 0u;
             if (L.refresh && L.Gout) {  // g' = c + (-z') B: the slice of C replaces g
                 __syncthreads();
-                stage_in(gt, L.C, row0, cs, m, N, TR, tid);
+                stage_in<1>(gt, L.C, nullptr, nullptr, row0, cs, m, N, TR, tid);
                 __syncthreads();
             }
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float gn = gr[j] + acc[j];
-                gr[j] = gn;
-                if (MODE == OIS) obad |= (c0 + j < m) && (zr[j] == 0.0f) && (fabsf(gn) > L.lam);
+            for (int u = 0; u < 8; ++u) {
+                float4 *gp = reinterpret_cast<float4 *>(gt + sidx(r, cg * 32 + 4 * u));
+                float4 g4 = *gp;
+                g4.x += acc[4 * u];
+                g4.y += acc[4 * u + 1];
+                g4.z += acc[4 * u + 2];
+                g4.w += acc[4 * u + 3];
+                *gp = g4;
+                if (MODE == OIS) {
+                    const float4 z4 = *reinterpret_cast<const float4 *>(zt + sidx(r, cg * 32 + 4 * u));
+                    const int c = c0 + 4 * u;
+                    obad |= (c < m) && (z4.x == 0.0f) && (fabsf(g4.x) > L.lam);
+                    obad |= (c + 1 < m) && (z4.y == 0.0f) && (fabsf(g4.y) > L.lam);
+                    obad |= (c + 2 < m) && (z4.z == 0.0f) && (fabsf(g4.z) > L.lam);
+                    obad |= (c + 3 < m) && (z4.w == 0.0f) && (fabsf(g4.w) > L.lam);
+                }
             }
             if (eok && c0 < m) {
                 const int wi = c0 >> 5;

@@ -91,6 +91,13 @@ def test_argument_validation_without_gpu(lib):
     assert need >= 64 * 64 * 4 + 4 * 3 * 4 * 8
     assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_BF16X3, vp, vp, 3, None, vp, vp, need - 1,
                                None) == _lib.SLISTA_ERR_WORKSPACE
+    # a workspace off a 256-byte boundary (large enough) is refused before any launch
+    odd = ctypes.c_void_p(0x1010)
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_BF16X3, vp, vp, 3, None, vp, odd, need,
+                               None) == _lib.SLISTA_ERR_WORKSPACE
+    assert "256-byte" in _err(lib)
+    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, None, None, 1, odd, 1 << 30,
+                              None) == _lib.SLISTA_ERR_WORKSPACE
     # OISTA and objective null pointers
     assert lib.oista_forward(vp, vp, None, 0, 8, 4, 0.1, None, 3, 0, vp, None, None, None, 0, None) == _lib.SLISTA_ERR_ARG
     assert lib.oista_forward(vp, vp, vp, 4, 8, 4, 0.1, vp, 3, 0, vp, None, None, None, 0,

@@ -364,3 +364,41 @@ def test_tc_oista_full_size_sampled_rows():
     zt = TOL["bf16x3"]["Z"] * max(1.0, float(np.abs(Zo).max()))
     assert np.abs(host(Zg)[rows][safe].astype(np.float64) - Zo[safe]).max() <= zt
     np.testing.assert_allclose(host(LSg)[rows][safe], LSo[safe], rtol=1e-5)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_oista_odd_batch(prec):
+    """An odd batch size (N = 301) against the oracle: the per-sample state
+    arrays of the workspace start on 256-byte boundaries whatever N is, as the
+    layer kernels' 16-byte row loads need."""
+    w = synth.slista_64x256(N=301, T=20)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    Zg, LSg, accg = A.oista(g.B, g.C, w.lam, g.L, w.T, D=dev(w.D), prec=prec)
+    Zo, LSo, acco, deco, marg = oracle.oista(w.D, w.X, w.lam, oracle.lipschitz(w.D), w.T, with_margin=True)
+    safe = marg > TC_OISTA_MARGIN
+    assert safe.sum() >= 30
+    zt = TOL["bf16x3"]["Z"] * max(1.0, float(np.abs(Zo).max()))
+    assert np.abs(host(Zg)[safe].astype(np.float64) - Zo[safe]).max() <= zt
+    np.testing.assert_allclose(host(LSg)[safe], LSo[safe], rtol=1e-5)
+    assert np.abs(host(accg) - acco).max() <= (~safe).sum()
+
+
+def test_tc_unaligned_c_matches_aligned():
+    """C passed at an address 4 bytes past a 16-byte boundary (a view into a
+    larger buffer): the layer kernels fall back to scalar loads and give the
+    same codes and gradient bit for bit."""
+    w = synth.slista_64x256(N=300, T=12)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    buf = torch.empty(g.C.numel() + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = g.C.reshape(-1)
+    Cu = buf[1:].view(g.C.shape)
+    assert Cu.data_ptr() % 16 != 0
+    alpha = dev(synth.step_sizes(w.T, 1.0 / oracle.lipschitz(w.D), 0.3, seed=2))
+    Z1, s1 = A.slista(g.B, g.C, w.lam, alpha, prec="bf16x3", keep_for_backward=True, ckpt_every=4)
+    Z2, s2 = A.slista(g.B, Cu, w.lam, alpha, prec="bf16x3", keep_for_backward=True, ckpt_every=4)
+    assert torch.equal(Z1, Z2)
+    d1 = A.slista_grad(g.B, g.C, w.lam, alpha, s1, prec="bf16x3")
+    d2 = A.slista_grad(g.B, Cu, w.lam, alpha, s2, prec="bf16x3")
+    assert torch.equal(d1, d2)

@@ -191,3 +191,16 @@ def test_large_256x1024_full_size_sampled_rows():
     Lo = lipschitz(w.D)
     Zo = oracle.ista(w.D, w.X[rows], w.lam, Lo, w.T)
     _check("bf16x3", host(Z)[rows], F[rows], Zo, oracle.objective(w.D, w.X[rows], Zo, w.lam, with_gap=False))
+
+
+def test_wide_unaligned_c_matches_aligned():
+    """m > 256 with C 4 bytes past a 16-byte boundary: scalar loads, same codes."""
+    D, X, lam = _case(64, 320, 200, 29)
+    A = api()
+    g = A.gram(dev(D), dev(X))
+    buf = torch.empty(g.C.numel() + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = g.C.reshape(-1)
+    Cu = buf[1:].view(g.C.shape)
+    assert Cu.data_ptr() % 16 != 0
+    alpha = dev(synth.step_sizes(10, 1.0 / lipschitz(D), 0.3, seed=4))
+    assert torch.equal(A.slista(g.B, g.C, lam, alpha, prec="bf16x3"), A.slista(g.B, Cu, lam, alpha, prec="bf16x3"))
