@@ -71,6 +71,11 @@ struct CtaGroup {
 // Odd leading dimension for a k x k matrix (conflict-free column walks).
 __host__ __device__ constexpr int odd_ld(int k) { return (k & 1) ? k : k + 1; }
 
+// Leading dimension >= k with lda % 8 == 4: rows start on 16-byte boundaries
+// and the 16-byte loads of 8 lanes at one offset of 8 consecutive rows fall
+// in distinct bank groups (row stride an odd number of 16-byte units).
+__host__ __device__ constexpr int vec_ld(int k) { return 4 * (((k + 3) >> 2) | 1); }
+
 // Number of eigenvalues of the symmetric tridiagonal (d, e) below x.
 __device__ inline int sturm_count(const float *d, const float *e2, int k, float x, float pivmin)
 {
@@ -258,9 +263,11 @@ __device__ inline float tridiag_max_eig_warp(const float *d, const float *e, flo
 // supports of the 64 x 256 workload - |S| = 11 .. 160, B_SS or D_S D_S^T -
 // the top Ritz value is within 1e-8 of lambda_max (FP64 model) when the rule
 // stops, at 12 - 14 steps on average.)  A is in shared memory with leading
-// dimension lda.  j0 replaces LANCZOS_J0 (j0 >= k: the full dimension, at
-// most LANCZOS_JMAX steps).
-// q, qp: k floats; al, be, e2: LANCZOS_JMAX floats of warp scratch.
+// dimension lda; with lda = vec_ld(k) and 16-byte aligned A and q the rows
+// are read as 16-byte vectors, and columns k .. 4 ceil(k/4) - 1 of A must then
+// hold finite values (zeros).  j0 replaces LANCZOS_J0 (j0 >= k: the full
+// dimension, at most LANCZOS_JMAX steps).
+// q, qp: 4 ceil(k/4) floats; al, be, e2: LANCZOS_JMAX floats of warp scratch.
 // RPL = rows per lane (>= ceil(k / 32)).
 constexpr int LANCZOS_J0 = 10;
 constexpr int LANCZOS_DJ = 2;
@@ -286,6 +293,13 @@ __device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q,
         q[a] = start_vector(a) * inv;
         qp[a] = 0.0f;
     }
+    // rows as 16-byte vectors when the layout allows (vec_ld); q is then
+    // zero-padded to a multiple of 4 entries, so the pad columns of A (which
+    // the caller zeroes) contribute nothing
+    const bool vec = (lda & 7) == 4 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(q) & 15) == 0;
+    const int ku = (k + 3) >> 2;
+    if (vec && lane < 4 * ku - k) q[k + lane] = 0.0f;
     __syncwarp();
     float beta_prev = 0.0f;
     float ref = -INFINITY, theta = -INFINITY;
@@ -305,14 +319,26 @@ __device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q,
                 if (a < k) {
                     const float *row = A + a * lda;
                     float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-                    int b = 0;
-                    for (; b + 3 < k; b += 4) {
-                        s0 = fmaf(row[b], q[b], s0);
-                        s1 = fmaf(row[b + 1], q[b + 1], s1);
-                        s2 = fmaf(row[b + 2], q[b + 2], s2);
-                        s3 = fmaf(row[b + 3], q[b + 3], s3);
+                    if (vec) {
+                        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+                        const float4 *q4 = reinterpret_cast<const float4 *>(q);
+                        for (int u = 0; u < ku; ++u) {
+                            const float4 x = r4[u], y = q4[u];
+                            s0 = fmaf(x.x, y.x, s0);
+                            s1 = fmaf(x.y, y.y, s1);
+                            s2 = fmaf(x.z, y.z, s2);
+                            s3 = fmaf(x.w, y.w, s3);
+                        }
+                    } else {
+                        int b = 0;
+                        for (; b + 3 < k; b += 4) {
+                            s0 = fmaf(row[b], q[b], s0);
+                            s1 = fmaf(row[b + 1], q[b + 1], s1);
+                            s2 = fmaf(row[b + 2], q[b + 2], s2);
+                            s3 = fmaf(row[b + 3], q[b + 3], s3);
+                        }
+                        for (; b < k; ++b) s0 = fmaf(row[b], q[b], s0);
                     }
-                    for (; b < k; ++b) s0 = fmaf(row[b], q[b], s0);
                     s = (s0 + s1) + (s2 + s3);
                     dot = fmaf(s, q[a], dot);
                 }

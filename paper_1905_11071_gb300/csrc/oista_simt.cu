@@ -51,8 +51,8 @@ constexpr int STEP_NB = 32;
 
 constexpr int GCOLS = 8;  // D_S columns staged per round in gram_ds
 
-struct WarpEig {
-    static constexpr int LDA = eig::odd_ld(KMAX);
+struct alignas(16) WarpEig {
+    static constexpr int LDA = eig::vec_ld(KMAX);
     float A[KMAX * LDA];
     float q[256], qp[256], al[JM], be[JM], e2[JM];
     float col[GCOLS * KMAX];
@@ -113,42 +113,51 @@ struct OistaWs {
     }
 };
 
-// Index list of a support given by its words (one warp); returns |S|.
+// Index list of a support given by its words (one warp); returns |S|.  The
+// W <= 32 words are loaded at once, one per lane.
 __device__ int support_indices(const uint32_t *words, int W, int *idx)
 {
     const int lane = threadIdx.x & 31;
+    const uint32_t mine = lane < W ? words[lane] : 0u;
     int k = 0;
     for (int w = 0; w < W; ++w) {
-        const uint32_t bits = words[w];
+        const uint32_t bits = __shfl_sync(0xffffffffu, mine, w);
         const bool has = (bits >> lane) & 1u;
-        const uint32_t bal = __ballot_sync(0xffffffffu, has);
-        if (has) idx[k + __popc(bal & ((1u << lane) - 1u))] = w * 32 + lane;
-        k += __popc(bal);
+        if (has) idx[k + __popc(bits & ((1u << lane) - 1u))] = w * 32 + lane;
+        k += __popc(bits);
     }
     __syncwarp();
     return k;
 }
 
-// B_SS into A (leading dimension lda); returns whether an off-diagonal entry is non-zero.
+// B_SS into A (leading dimension lda >= 4 ceil(k/4), k <= 64), columns
+// k .. 4 ceil(k/4) - 1 zeroed; returns whether an off-diagonal entry is
+// non-zero.  Lane l gathers columns l and l + 32 of 8 rows at a time (16
+// loads in flight).
 __device__ bool gather_bss(const float *__restrict__ B, int m, const int *idx, int k, float *A, int lda)
 {
     const int lane = threadIdx.x & 31;
-    const int kk = k * k;
+    const int kp = (k + 3) & ~3;
+    const int c0 = lane, c1 = lane + 32;
+    const int j0 = c0 < k ? idx[c0] : 0, j1 = c1 < k ? idx[c1] : 0;
     bool off = false;
-    for (int e0 = 0; e0 < kk; e0 += 32 * 8) {  // eight independent loads in flight per lane
-        float x[8];
+#pragma unroll 1
+    for (int a0 = 0; a0 < k; a0 += 8) {
+        float x0[8], x1[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * 32 + lane;
-            x[u] = e < kk ? __ldg(B + (size_t)idx[e / k] * m + idx[e % k]) : 0.0f;
+            const int a = a0 + u;
+            const float *row = B + (size_t)(a < k ? idx[a] : 0) * m;
+            x0[u] = (a < k && c0 < k) ? __ldg(row + j0) : 0.0f;
+            x1[u] = (a < k && c1 < k) ? __ldg(row + j1) : 0.0f;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int e = e0 + u * 32 + lane;
-            if (e < kk) {
-                const int a = e / k, b = e % k;
-                A[a * lda + b] = x[u];
-                off |= (a != b) && (x[u] != 0.0f);
+            const int a = a0 + u;
+            if (a < k) {
+                if (c0 < kp) A[a * lda + c0] = x0[u];
+                if (c1 < kp) A[a * lda + c1] = x1[u];
+                off |= (a != c0 && x0[u] != 0.0f) || (a != c1 && x1[u] != 0.0f);
             }
         }
     }
@@ -156,20 +165,22 @@ __device__ bool gather_bss(const float *__restrict__ B, int m, const int *idx, i
     return __any_sync(0xffffffffu, off);
 }
 
-// G = D_S D_S^T (n x n, n <= KMAX) into A, accumulated over the k support
-// columns; Dt is D transposed, so column j of D is the contiguous row j of Dt.
-// Lane a owns rows a and a + 32; the 64 columns go in four passes of 16.
+// G = D_S D_S^T (n x n, n <= KMAX) into A (leading dimension lda), columns
+// n .. 4 ceil(n/4) - 1 zeroed; Dt is D transposed, so column j of D is the
+// contiguous row j of Dt.  Lane a owns rows a and a + 32.  Two passes over
+// the support columns (staged GCOLS at a time in col): columns 0..31 for
+// rows < 32, then columns 32..63 for all rows; the block of rows >= 32 x
+// columns < 32 is the transpose of the one computed for rows < 32.
 __device__ void gram_ds(const float *__restrict__ Dt, int n, const int *idx, int k, float *A, int lda, float *col)
 {
     const int lane = threadIdx.x & 31;
-    constexpr int PC = 16;  // columns per pass
 #pragma unroll 1
-    for (int b0 = 0; b0 < n; b0 += PC) {
-        float acc[KMAX / 32][PC];
+    for (int h = 0; h < 2; ++h) {
+        const int b0 = 32 * h;
+        if (b0 >= n) break;
+        float acc0[32], acc1[32];
 #pragma unroll
-        for (int r = 0; r < KMAX / 32; ++r)
-#pragma unroll
-            for (int b = 0; b < PC; ++b) acc[r][b] = 0.0f;
+        for (int b = 0; b < 32; ++b) acc0[b] = acc1[b] = 0.0f;
 #pragma unroll 1
         for (int s0 = 0; s0 < k; s0 += GCOLS) {
             float x[GCOLS][KMAX / 32];
@@ -188,23 +199,40 @@ __device__ void gram_ds(const float *__restrict__ Dt, int n, const int *idx, int
             __syncwarp();
 #pragma unroll
             for (int c = 0; c < GCOLS; ++c) {
+                const float d0 = col[c * KMAX + lane], d1 = col[c * KMAX + lane + 32];
+                const float4 *cb = reinterpret_cast<const float4 *>(col + c * KMAX + b0);
 #pragma unroll
-                for (int r = 0; r < KMAX / 32; ++r) {
-                    const float da = col[c * KMAX + lane + 32 * r];
-#pragma unroll
-                    for (int b = 0; b < PC; ++b) acc[r][b] = fmaf(da, col[c * KMAX + b0 + b], acc[r][b]);
+                for (int u = 0; u < 8; ++u) {
+                    const float4 v = cb[u];
+                    acc0[4 * u] = fmaf(d0, v.x, acc0[4 * u]);
+                    acc0[4 * u + 1] = fmaf(d0, v.y, acc0[4 * u + 1]);
+                    acc0[4 * u + 2] = fmaf(d0, v.z, acc0[4 * u + 2]);
+                    acc0[4 * u + 3] = fmaf(d0, v.w, acc0[4 * u + 3]);
+                    if (h == 1) {
+                        acc1[4 * u] = fmaf(d1, v.x, acc1[4 * u]);
+                        acc1[4 * u + 1] = fmaf(d1, v.y, acc1[4 * u + 1]);
+                        acc1[4 * u + 2] = fmaf(d1, v.z, acc1[4 * u + 2]);
+                        acc1[4 * u + 3] = fmaf(d1, v.w, acc1[4 * u + 3]);
+                    }
                 }
             }
         }
+        if (lane < n)
 #pragma unroll
-        for (int r = 0; r < KMAX / 32; ++r) {
-            const int a = lane + 32 * r;
-            if (a < n)
+            for (int b = 0; b < 32; ++b)
+                if (b0 + b < n) A[lane * lda + b0 + b] = acc0[b];
+        if (h == 1 && lane + 32 < n)
 #pragma unroll
-                for (int b = 0; b < PC; ++b)
-                    if (b0 + b < n) A[a * lda + b0 + b] = acc[r][b];
-        }
+            for (int b = 0; b < 32; ++b)
+                if (b0 + b < n) A[(lane + 32) * lda + b0 + b] = acc1[b];
     }
+    __syncwarp();
+    // rows 32.. x columns 0..31 by symmetry; zero pad columns
+    for (int a = 32; a < n; ++a)
+        if (lane < n) A[a * lda + lane] = A[lane * lda + a];
+    const int np = (n + 3) & ~3;
+    for (int a = lane; a < n; a += 32)
+        for (int b = n; b < np; ++b) A[a * lda + b] = 0.0f;
     __syncwarp();
 }
 
@@ -450,13 +478,13 @@ __global__ void __launch_bounds__((A_WARPS + S_WARPS) * 32, 1) oista_solve_kerne
             } else if (k <= SMALL_K) {
                 LS = solve_small(B, m, we.idx, k, we.al, we.be, we.e2);
             } else if (k <= KMAX) {
-                const int lda = eig::odd_ld(k);
+                const int lda = eig::vec_ld(k);
                 if (gather_bss(B, m, we.idx, k, we.A, lda))
                     LS = eig::lanczos_max_eig_warp<KMAX / 32>(we.A, lda, k, we.q, we.qp, we.al, we.be, we.e2);
                 else
                     LS = (double)max_diag(we.A, lda, k);
             } else if (have_D && n <= KMAX) {
-                const int lda = eig::odd_ld(n);
+                const int lda = eig::vec_ld(n);
                 gram_ds(ws.Dt, n, we.idx, k, we.A, lda, we.col);
                 LS = eig::lanczos_max_eig_warp<KMAX / 32>(we.A, lda, n, we.q, we.qp, we.al, we.be, we.e2);
             } else {
