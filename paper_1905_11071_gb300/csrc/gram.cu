@@ -81,9 +81,8 @@ __global__ void dtd_kernel(const float *__restrict__ D, int n, int m, float *__r
 // ---------------------------------------------------------------------------
 // Largest eigenvalue of a k x k symmetric PSD matrix K.  For k <= KL_SMEM the
 // matrix is formed in shared memory (from a shared copy of D when it fits) and
-// solved by one warp with Lanczos run to the full dimension up to 64 steps
-// (T_k is then similar to K for k <= 64) and a Sturm multisection on the
-// tridiagonal (eig.cuh).  Larger matrices fall back to power iteration on K in
+// solved by one warp with Lanczos and Sturm multisection on the tridiagonal,
+// with the stopping rule of eig::lanczos_max_eig_warp (eig.cuh).  Larger matrices fall back to power iteration on K in
 // global memory (FP32 products, FP64 Rayleigh quotients), which keeps the
 // largest quotient seen and stops after 400 iterations without progress.
 // ---------------------------------------------------------------------------
@@ -141,7 +140,7 @@ __global__ void __launch_bounds__(PI_NT) lipschitz_kernel(const float *__restric
         if (threadIdx.x < 32) {
             const double v = eig::lanczos_max_eig_warp<(KL_SMEM + 31) / 32>(
                 Ks, lda, k, vec, vec + k, vec + 2 * k, vec + 2 * k + eig::LANCZOS_JMAX,
-                vec + 2 * k + 2 * eig::LANCZOS_JMAX, k);
+                vec + 2 * k + 2 * eig::LANCZOS_JMAX);
             if (threadIdx.x == 0) *L = v;
         }
         return;

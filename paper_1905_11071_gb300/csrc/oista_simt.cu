@@ -413,14 +413,22 @@ __device__ double solve_small(const float *__restrict__ B, int m, const int *idx
 }
 
 // Takes the next sample of list class cls of layer t (one warp); -1 when empty.
+// The queue position is read before it is incremented, so that the warps of
+// the grid stop taking atomics on the three queue counters once a list is
+// exhausted (a stale read only costs one atomic, whose result decides).
 __device__ __forceinline__ int next_sample(const OistaWs &ws, int t, int cls)
 {
     const int lane = threadIdx.x & 31;
     const int par = t & 1;
-    int q = 0;
-    if (lane == 0) q = atomicAdd(ws.qpos + NCLS * t + cls, 1);
+    int q = 0, n = 0;
+    if (lane == 0) {
+        n = ws.counter[NCLS * par + cls];
+        int *qp = ws.qpos + NCLS * t + cls;
+        q = *reinterpret_cast<volatile int *>(qp) >= n ? n : atomicAdd(qp, 1);
+    }
     q = __shfl_sync(0xffffffffu, q, 0);
-    if (q >= ws.counter[NCLS * par + cls]) return -1;
+    n = __shfl_sync(0xffffffffu, n, 0);
+    if (q >= n) return -1;
     return ws.list[(size_t)(NCLS * par + cls) * ws.N + q];
 }
 

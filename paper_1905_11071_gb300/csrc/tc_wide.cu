@@ -181,33 +181,55 @@ __device__ __forceinline__ int sidx(int r, int c) { return r * SW + ((((c >> 2) 
 // outside the matrix or when the matrix is null.  With 16-byte aligned rows
 // each warp moves one 512-byte row segment per instruction and a thread
 // issues all of its loads before its first shared-memory store.
+constexpr int SV = SW / 4;           // 16-byte units per slice row
+constexpr int SPER = BM * SV / NT;   // units per thread and matrix
+
+template <int NM>
+__device__ __forceinline__ bool stage_vec(const float *M0, const float *M1, int m)
+{
+    return (m & 3) == 0 && (reinterpret_cast<uintptr_t>(M0) & 15) == 0 &&
+           (NM == 1 || (reinterpret_cast<uintptr_t>(M1) & 15) == 0);
+}
+
+// The vector path of stage_in in two halves: the loads into registers, then
+// the shared stores.
+template <int NM>
+__device__ __forceinline__ void stage_load(float4 (&x0)[SPER], float4 (&x1)[SPER], const float *__restrict__ M0,
+                                           const float *__restrict__ M1, int row0, int cs, int m, int N, int TR,
+                                           int tid)
+{
+#pragma unroll
+    for (int k = 0; k < SPER; ++k) {
+        const int e = tid + k * NT, r = e / SV, c = (e % SV) * 4;
+        const int gr = row0 + r, gc = cs + c;
+        const bool ok = r < TR && gr < N && gc < m;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        x0[k] = (ok && M0 != nullptr) ? __ldg(reinterpret_cast<const float4 *>(M0 + (size_t)gr * m + gc)) : zero;
+        if (NM == 2)
+            x1[k] = (ok && M1 != nullptr) ? __ldg(reinterpret_cast<const float4 *>(M1 + (size_t)gr * m + gc)) : zero;
+    }
+}
+
+template <int NM>
+__device__ __forceinline__ void stage_store(const float4 (&x0)[SPER], const float4 (&x1)[SPER], float *t0, float *t1,
+                                            int tid)
+{
+#pragma unroll
+    for (int k = 0; k < SPER; ++k) {
+        const int e = tid + k * NT, r = e / SV, c = (e % SV) * 4;
+        *reinterpret_cast<float4 *>(t0 + sidx(r, c)) = x0[k];
+        if (NM == 2) *reinterpret_cast<float4 *>(t1 + sidx(r, c)) = x1[k];
+    }
+}
+
 template <int NM>
 __device__ __forceinline__ void stage_in(float *t0, const float *__restrict__ M0, float *t1,
                                          const float *__restrict__ M1, int row0, int cs, int m, int N, int TR, int tid)
 {
-    const bool vec = (m & 3) == 0 && (reinterpret_cast<uintptr_t>(M0) & 15) == 0 &&
-                     (NM == 1 || (reinterpret_cast<uintptr_t>(M1) & 15) == 0);
-    if (vec) {
-        constexpr int V = SW / 4;         // 16-byte units per slice row
-        constexpr int PER = BM * V / NT;  // units per thread and matrix
-        float4 x0[PER], x1[PER];
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = tid + k * NT, r = e / V, c = (e % V) * 4;
-            const int gr = row0 + r, gc = cs + c;
-            const bool ok = r < TR && gr < N && gc < m;
-            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-            x0[k] = (ok && M0 != nullptr) ? __ldg(reinterpret_cast<const float4 *>(M0 + (size_t)gr * m + gc)) : zero;
-            if (NM == 2)
-                x1[k] = (ok && M1 != nullptr) ? __ldg(reinterpret_cast<const float4 *>(M1 + (size_t)gr * m + gc))
-                                              : zero;
-        }
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = tid + k * NT, r = e / V, c = (e % V) * 4;
-            *reinterpret_cast<float4 *>(t0 + sidx(r, c)) = x0[k];
-            if (NM == 2) *reinterpret_cast<float4 *>(t1 + sidx(r, c)) = x1[k];
-        }
+    if (stage_vec<NM>(M0, M1, m)) {
+        float4 x0[SPER], x1[SPER];
+        stage_load<NM>(x0, x1, M0, M1, row0, cs, m, N, TR, tid);
+        stage_store<NM>(x0, x1, t0, t1, tid);
         return;
     }
 #pragma unroll 4
@@ -264,15 +286,6 @@ __global__ void split_tiles_kernel(const float *__restrict__ B, int m, uint8_t *
     uint8_t *tile = out + ((size_t)cb * nkc + kc) * TILE_PAIR;
     *reinterpret_cast<__nv_bfloat16 *>(tile + off) = hi;
     *reinterpret_cast<__nv_bfloat16 *>(tile + TILE_B + off) = lo;
-}
-
-// Oracle-ISTA step of sample `row`: 1 / L_S when condition (star) held at
-// this layer (flag 0), else the ISTA step aL = 1 / L (same rounding as the
-// FP32 step kernel).
-__device__ __forceinline__ float oista_step(const WLayer &L, int row, bool ok, float aL)
-{
-    if (!ok) return aL;
-    return __ldg(L.flag + row) == 0 ? (float)(1.0 / __ldg(L.LSv + row)) : aL;
 }
 
 // ---------------------------------------------------------------------------
@@ -333,25 +346,67 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         return ok;
     };
 
+    // epilogue rows: warp w reads TMEM lanes 32 (w % 4).. (the tile rows)
+    const int q = warp & 3, cg = warp >> 2;
+    const int erow = row0 + 32 * q + lane;
+    const bool eok = 32 * q + lane < TR && erow < N;
+    const int W = (m + 31) / 32;
+    // Oracle-ISTA: the rows' inputs from the previous kernels (condition
+    // (star) flag, cached L_S, its validity and support words), all loaded at
+    // once before the products and kept in shared memory: step s_ea (1 / L_S
+    // or 1 / L), s_flag, s_valid, and s_sp[slice][column group][row].
+    static_assert(BN / SW == 2, "two epilogue slices");
+    __shared__ float s_ea[BM];
+    __shared__ int s_flag[BM], s_valid[BM];
+    __shared__ uint32_t s_sp[BN / SW][NT / 128][BM];
+    int pf_flag = 1, pf_valid = 1;
+    double pf_ls = 1.0;
+    uint32_t pf_sp0 = 0u, pf_sp1 = 0u;
+    if (MODE == OIS && eok) {
+        if (cg == 0) {
+            pf_flag = __ldg(L.flag + erow);
+            pf_ls = __ldg(L.LSv + erow);
+            pf_valid = __ldg(L.valid + erow);
+        }
+        const int c0 = col0 + cg * 32;
+        if (!L.last && c0 < m) pf_sp0 = __ldg(L.Sprev + (size_t)erow * W + (c0 >> 5));
+        if (!L.last && c0 + SW < m) pf_sp1 = __ldg(L.Sprev + (size_t)erow * W + ((c0 + SW) >> 5));
+    }
+    auto publish_rows = [&]() {
+        const int r = 32 * q + lane;
+        if (cg == 0) {
+            s_ea[r] = (eok && pf_flag == 0) ? (float)(1.0 / pf_ls) : a;
+            s_flag[r] = pf_flag;
+            s_valid[r] = pf_valid;
+        }
+        s_sp[0][cg][r] = pf_sp0;
+        s_sp[1][cg][r] = pf_sp1;
+    };
+    const int prow = tid >> 2, pk = (tid & 3) * 16;  // producer: one row, 16 codes of the chunk
+    const int grow = row0 + prow;
+    const bool rok = prow < TR && grow < N;
+    // the loads of chunk kc + 1 are issued before chunk kc's barrier and
+    // MMA issue, so their latency overlaps the tensor-core work
+    float nz[16], ng[16];
     if (do_mma) {
         if (tid == 0) {
             issue_b(0);
             if (nkc > 1) issue_b(1);
         }
-        const int prow = tid >> 2, pk = (tid & 3) * 16;  // producer: one row, 16 codes of the chunk
-        const int grow = row0 + prow;
-        const bool rok = prow < TR && grow < N;
-        const float pa = MODE == OIS ? oista_step(L, grow, rok, a) : a;
-        const float pthr = pa * L.lam;
-        // the loads of chunk kc + 1 are issued before chunk kc's barrier and
-        // MMA issue, so their latency overlaps the tensor-core work
-        float nz[16], ng[16];
         if (MODE != ADJ) {
             load16(Zs, grow, rok, m, pk, nz);
             load16(Gs, grow, rok, m, pk, ng);
         } else {
             load16(L.Gin, grow, rok, m, pk, ng);
         }
+    }
+    if (MODE == OIS) {  // (waits for the row inputs while chunk 0 loads)
+        publish_rows();
+        __syncthreads();
+    }
+    if (do_mma) {
+        const float pa = (MODE == OIS && rok) ? s_ea[prow] : a;
+        const float pthr = pa * L.lam;
 #pragma unroll 1
         for (int kc = 0; kc < nkc; ++kc) {
             const int s = kc & 1;
@@ -413,13 +468,9 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         tc_fence_after();
     }
 
-    // --- epilogue.  Warp w reads TMEM lanes 32 (w % 4).. (the tile rows).
-    const int q = warp & 3, cg = warp >> 2;
-    const int erow = row0 + 32 * q + lane;
-    const bool eok = 32 * q + lane < TR && erow < N;
-    const int W = (m + 31) / 32;
+    // --- epilogue
     const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
-    const float ea = MODE == OIS ? oista_step(L, erow, eok, a) : a;
+    const float ea = MODE == OIS ? s_ea[32 * q + lane] : a;
     const float ethr = ea * L.lam;
     float part = 0.0f;
     bool obad = false, ochg = false;  // OIS: (star) fails for the next layer; support changed
@@ -497,7 +548,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
                 if (L.mask_out) L.mask_out[(size_t)erow * W + wi] = word;
                 if (MODE == OIS && !L.last) {
                     L.Scur[(size_t)erow * W + wi] = word;
-                    ochg |= word != __ldg(L.Sprev + (size_t)erow * W + wi);
+                    ochg |= word != s_sp[sl][cg][32 * q + lane];
                     ok_cnt += __popc(word);
                 }
             }
@@ -553,7 +604,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         }
         __syncthreads();
         if (cg == 0 && eok && !failed) {
-            if (__ldg(L.flag + erow) == 0) atomicAdd(&nacc, 1);
+            if (s_flag[32 * q + lane] == 0) atomicAdd(&nacc, 1);
             if (L.last) {
                 if (L.LS_out) L.LS_out[erow] = __ldg(L.LSv + erow);
             }
@@ -563,7 +614,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
             const int r = 32 * q + lane;
             const int f = rbad[r];
             L.flag[erow] = f;
-            const bool changed = rchg[r] != 0 || __ldg(L.valid + erow) == 0;
+            const bool changed = rchg[r] != 0 || s_valid[r] == 0;
             if ((f == 0 || L.want_ls) && changed) {
                 const int k = rk[r];
                 const int cls = k > 64 ? 0 : k > 32 ? 1 : 2;
