@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--T", type=int, default=40)
     p.add_argument("--prec", default="bf16x3", help="layer precision: bf16x3 (tensor cores, default), bf16, fp32")
     p.add_argument("--oista-prec", default="bf16x3", help="Oracle-ISTA layer precision: bf16x3 (tensor cores), fp32 (CUDA cores)")
+    p.add_argument("--backward", default="traj", choices=["traj", "ckpt"],
+                   help="SLISTA backward: traj (the forward keeps the adjoint's inputs, one reverse sweep; "
+                        "tensor cores, m, T <= 256) or ckpt (checkpoints every ~sqrt(T) layers, recompute)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-samples", type=int, default=0, help="oracle sample size (0 = auto)")
@@ -126,13 +129,22 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- ours
 
+def backward_mode(w, args) -> str:
+    """The one-pass (trajectory) backward where its path exists, else checkpoints."""
+    tc = args.prec in ("bf16", "bf16x3")
+    return "traj" if (args.backward == "traj" and tc and w.m <= 256 and 1 <= w.T <= 256) else "ckpt"
+
+
 def arm_config(w, args, world: int) -> dict:
     """The workload description shared by both arms of the benchmark."""
     import math as _m
     return {"workload": "slista_64x256", "n": w.n, "m": w.m, "N_per_gpu": w.N, "T": w.T, "lam": w.lam,
-            "ckpt_every": max(1, int(_m.ceil(_m.sqrt(max(w.T, 1))))), "prec": args.prec,
-            "oista_prec": args.oista_prec,
-            "step": "gram+L -> slista fwd(masks,ckpt) -> objective+gap -> slista bwd -> oista fwd",
+            "backward": backward_mode(w, args),
+            "ckpt_every": (max(1, int(_m.ceil(_m.sqrt(max(w.T, 1))))) if backward_mode(w, args) == "ckpt"
+                           else None),
+            "prec": args.prec, "oista_prec": args.oista_prec,
+            "step": ("gram+L -> slista fwd(masks,%s) -> objective+gap -> slista bwd -> oista fwd" %
+                     ("trajectory" if backward_mode(w, args) == "traj" else "ckpt")),
             "l2": "flushed between timed steps (write of 2x L2 size, untimed)",
             "parallelism": "dp%d" % world if world > 1 else "single"}
 
@@ -196,12 +208,14 @@ def run_ours(args, rank, world, local_rank):
 
     parts = ["gram", "slista_fwd", "objective", "slista_bwd", "oista_fwd"]
     tc = args.prec in ("bf16", "bf16x3")
+    traj = backward_mode(w, args) == "traj"
     nseg = -(-T // K)
     launches_per_step = {
         "gram": 3,                                            # D^T D, X D (+ ||x||^2), L
         "slista_fwd": 2 if tc else 1,                         # (B split) + layer kernel
         "objective": 1,
-        "slista_bwd": (1 + 2 * nseg + 1) if tc else 2,        # (B split) + recompute/adjoint per segment + reduce
+        # (B split) + one reverse sweep + reduce, or + recompute/adjoint per segment + reduce
+        "slista_bwd": 3 if traj else ((1 + 2 * nseg + 1) if tc else 2),
         "oista_fwd": 1 + 1 + 2 * T + (1 if args.oista_prec != "fp32" else 0),  # transpose D, init, (B split), solve + step per layer
     }
 
@@ -211,7 +225,8 @@ def run_ours(args, rank, world, local_rank):
         g = api.gram(D, X)
         if evs is not None:
             evs[1].record(stream)
-        Z, st = api.slista(g.B, g.C, lam, alpha, prec=args.prec, keep_for_backward=True, ckpt_every=K)
+        Z, st = api.slista(g.B, g.C, lam, alpha, prec=args.prec, keep_for_backward=True, ckpt_every=K,
+                           trajectory=traj)
         if evs is not None:
             evs[2].record(stream)
         F, gap = api.objective(g.B, g.C, g.xsq, Z, lam)
@@ -278,7 +293,8 @@ def run_ours(args, rank, world, local_rank):
             Xd = Xh.to(dev, non_blocking=True)
             ad = Ah.to(dev, non_blocking=True)
             g = api.gram(Dd, Xd)
-            Z, st = api.slista(g.B, g.C, lam, ad, prec=args.prec, keep_for_backward=True, ckpt_every=K)
+            Z, st = api.slista(g.B, g.C, lam, ad, prec=args.prec, keep_for_backward=True, ckpt_every=K,
+                               trajectory=traj)
             F, gap = api.objective(g.B, g.C, g.xsq, Z, lam)
             da = api.slista_grad(g.B, g.C, lam, ad, st, prec=args.prec)
             Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=Dd, prec=args.oista_prec)
@@ -323,11 +339,13 @@ def run_ours(args, rank, world, local_rank):
         layer_peak = fp32_peak
         layer_bound, layer_src = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
     algo = {
-        # useful B z products: 2 m^2 per sample per layer (T - 1 contractions)
-        "slista_fwd": (layer_bound, 2 * mm * mm * (T - 1) * N / 1e12, "TFLOP/s", layer_peak, layer_src),
-        # adjoint: recompute (K - 1 contractions per segment, + 1 for g^(T)) and B h (T - 1)
-        "slista_bwd": (layer_bound, 2 * mm * mm * (2 * T - nseg) * N / 1e12, "TFLOP/s", layer_peak,
+        # useful B z products: 2 m^2 per sample per layer (T - 1 contractions; T with the
+        # trajectory, whose forward also forms g^(T))
+        "slista_fwd": (layer_bound, 2 * mm * mm * (T if traj else T - 1) * N / 1e12, "TFLOP/s", layer_peak,
                        layer_src),
+        # adjoint: B h (T - 1), plus the recompute (K - 1 contractions per segment, + 1 for g^(T))
+        "slista_bwd": (layer_bound, 2 * mm * mm * ((T - 1) if traj else (2 * T - nseg)) * N / 1e12, "TFLOP/s",
+                       layer_peak, layer_src),
         # Oracle-ISTA: the layer products only (eigen-solves not counted), FP32 CUDA cores
         "oista_fwd": ("alu", 2 * mm * mm * (T - 1) * N / 1e12, "TFLOP/s", fp32_peak,
                       "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"),

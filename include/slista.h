@@ -78,6 +78,7 @@ extern "C" {
 #define SLISTA_FN_SLISTA_BWD 3
 #define SLISTA_FN_OISTA      4
 #define SLISTA_FN_OBJECTIVE  5
+#define SLISTA_FN_SLISTA_BWD_TRAJ 6
 
 /* Message describing the last failed call on this host thread ("" if none). */
 SLISTA_API const char *slista_last_error(void);
@@ -185,6 +186,36 @@ SLISTA_API int slista_backward(const float *B, const float *C, int m, int N, flo
                     const uint32_t *masks, const float *ckpt, int ckpt_every,
                     const float *gZ, float *dalpha,
                     void *ws, size_t ws_bytes, void *stream);
+
+/* ---- one-pass backward (tensor cores, m <= 256, 1 <= T <= 256) -----------
+ *
+ * The same sub-gradient as slista_backward without the recompute: the
+ * forward also writes the adjoint's inputs, the trajectory
+ *     q_t = g^(t) - lam sign(z^(t+1))  for t = 0 .. T-1,   dF/dz^(T)
+ * (Eq. steprec and the adjoint of slista_backward), and the backward is a
+ * single reverse sweep over them.  Memory for speed: the trajectory holds
+ * (T + 1) x N x m floats (plus tile padding) against the checkpoints'
+ * ceil(T/K) - 1 pairs of N x m.
+ *
+ * slista_traj_floats: length of the trajectory buffer (float32) for the
+ * current device (its layout follows the tiling of the batch over the
+ * device's SMs and is internal: only slista_forward_traj writes it and only
+ * slista_backward_traj on the same device reads it); 0 if (m, T) is outside
+ * the path's range.
+ * slista_forward_traj: slista_forward at SLISTA_PREC_BF16 / BF16X3 writing
+ * Z, masks (required: the backward reads them) and traj; ws as for
+ * slista_forward (SLISTA_FN_SLISTA_FWD).
+ * slista_backward_traj: dalpha (T) from masks and traj of a
+ * slista_forward_traj call with the same B, lam, alpha, T, prec and N; gZ
+ * (nullable, N x m) replaces dF/dz^(T) as in slista_backward.  ws:
+ * slista_workspace_bytes(SLISTA_FN_SLISTA_BWD_TRAJ, m, N, T, prec, 1). */
+SLISTA_API size_t slista_traj_floats(int m, int N, int T);
+SLISTA_API int slista_forward_traj(const float *B, const float *C, int m, int N, float lam,
+                                   const float *alpha, int T, int prec, float *Z, uint32_t *masks,
+                                   float *traj, void *ws, size_t ws_bytes, void *stream);
+SLISTA_API int slista_backward_traj(const float *B, int m, int N, float lam, const float *alpha, int T,
+                                    int prec, const uint32_t *masks, const float *traj, const float *gZ,
+                                    float *dalpha, void *ws, size_t ws_bytes, void *stream);
 
 /* ---- ragged batches (many independent problems in one launch per layer) ----
  *

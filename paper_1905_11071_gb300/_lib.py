@@ -33,12 +33,14 @@ FN_SLISTA_FWD = 2
 FN_SLISTA_BWD = 3
 FN_OISTA = 4
 FN_OBJECTIVE = 5
+FN_SLISTA_BWD_TRAJ = 6
 
 EXPORTS = [
     "slista_last_error", "slista_device_status", "slista_workspace_bytes", "slista_ckpt_floats",
     "slista_mask_words", "lasso_gram", "lasso_lipschitz", "ista_forward", "slista_forward",
     "slista_backward", "oista_forward", "lasso_objective", "slista_forward_noalloc",
     "slista_batched_workspace_bytes", "slista_forward_batched", "slista_backward_batched",
+    "slista_traj_floats", "slista_forward_traj", "slista_backward_traj",
 ]
 
 
@@ -89,6 +91,10 @@ def load(path: str = LIB_PATH):
         lib.slista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp, i, vp, sz, vp]
         lib.slista_backward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, i, vp, vp, vp, sz, vp]
         lib.slista_forward_noalloc.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp]
+        lib.slista_traj_floats.argtypes = [i, i, i]
+        lib.slista_traj_floats.restype = sz
+        lib.slista_forward_traj.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
+        lib.slista_backward_traj.argtypes = [vp, i, i, f, vp, i, i, vp, vp, vp, vp, vp, sz, vp]
         lib.oista_forward.argtypes = [vp, vp, vp, i, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
         lib.lasso_objective.argtypes = [vp, vp, vp, vp, i, i, f, vp, vp, vp]
         pp = ctypes.POINTER(Problem)
@@ -252,6 +258,49 @@ def slista_backward(B, C, lam, alpha, prec, masks, ckpt, ckpt_every, dalpha, gZ=
     _check(load().slista_backward(_ptr(B), _ptr(C), m, N, float(lam), _ptr(alpha), T, int(prec), _ptr(masks),
                                   _ptr(ckpt), int(ckpt_every), _ptr(gZ), _ptr(dalpha), _ptr(ws), wsb,
                                   _stream(stream)), "slista_backward")
+
+
+def slista_traj_floats(m: int, N: int, T: int) -> int:
+    return int(load().slista_traj_floats(int(m), int(N), int(T)))
+
+
+def slista_forward_traj(B, C, lam, alpha, prec, Z, masks, traj, ws=None, stream=None) -> None:
+    """Tensor-core forward that also writes the one-pass backward's trajectory."""
+    import torch
+    m = B.shape[0]
+    N = C.shape[0]
+    T = alpha.shape[0]
+    _need(B, torch.float32, (m, m), "B")
+    _need(C, torch.float32, (N, m), "C")
+    _need(alpha, torch.float32, (T,), "alpha")
+    _need(Z, torch.float32, (N, m), "Z")
+    _need(masks, torch.int32, None, "masks")
+    _need(traj, torch.float32, None, "traj")
+    if masks.numel() < slista_mask_words(m, N, T):
+        raise ValueError("masks too small")
+    if traj.numel() < slista_traj_floats(m, N, T):
+        raise ValueError("traj too small")
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().slista_forward_traj(_ptr(B), _ptr(C), m, N, float(lam), _ptr(alpha), T, int(prec), _ptr(Z),
+                                      _ptr(masks), _ptr(traj), _ptr(ws), wsb, _stream(stream)),
+           "slista_forward_traj")
+
+
+def slista_backward_traj(B, N, lam, alpha, prec, masks, traj, dalpha, gZ=None, ws=None, stream=None) -> None:
+    """One reverse sweep over the trajectory of slista_forward_traj."""
+    import torch
+    m = B.shape[0]
+    T = alpha.shape[0]
+    _need(B, torch.float32, (m, m), "B")
+    _need(alpha, torch.float32, (T,), "alpha")
+    _need(masks, torch.int32, None, "masks")
+    _need(traj, torch.float32, None, "traj")
+    _opt(gZ, torch.float32, (N, m), "gZ")
+    _need(dalpha, torch.float32, (T,), "dalpha")
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().slista_backward_traj(_ptr(B), m, int(N), float(lam), _ptr(alpha), T, int(prec), _ptr(masks),
+                                       _ptr(traj), _ptr(gZ), _ptr(dalpha), _ptr(ws), wsb, _stream(stream)),
+           "slista_backward_traj")
 
 
 def oista_forward(B, C, lam, L, T, prec, Z, LS=None, accepted=None, ws=None, D=None, stream=None) -> None:

@@ -77,15 +77,20 @@ def ista(B, C, lam, L, T, prec="fp32", stream=None) -> torch.Tensor:
 
 @dataclass
 class ForwardState:
-    """What slista_backward needs from a forward call."""
+    """What slista_backward needs from a forward call: masks and checkpoints,
+    or (trajectory forward) masks and the trajectory."""
     masks: torch.Tensor
     ckpt: Optional[torch.Tensor]
     ckpt_every: int
+    traj: Optional[torch.Tensor] = None
 
 
 def slista(B, C, lam, alpha, prec="fp32", keep_for_backward: bool = False,
-           ckpt_every: Optional[int] = None, stream=None):
-    """Step-LISTA forward (Eq. steprec).  Returns Z, or (Z, ForwardState)."""
+           ckpt_every: Optional[int] = None, trajectory: bool = False, stream=None):
+    """Step-LISTA forward (Eq. steprec).  Returns Z, or (Z, ForwardState).
+    trajectory=True (tensor-core precisions, m <= 256, T <= 256) keeps the
+    adjoint's inputs instead of checkpoints: more memory, no recompute in
+    slista_grad."""
     N, m = C.shape
     T = alpha.shape[0]
     p = _prec(prec)
@@ -95,6 +100,14 @@ def slista(B, C, lam, alpha, prec="fp32", keep_for_backward: bool = False,
     if not keep_for_backward:
         _lib.slista_forward(B, C, lam, alpha, p, Z, ws=ws, stream=stream)
         return Z
+    if trajectory:
+        masks = torch.empty((max(1, _lib.slista_mask_words(m, N, T)),), dtype=torch.int32, device=dev)
+        nt = _lib.slista_traj_floats(m, N, T)
+        if nt == 0:
+            raise ValueError("trajectory forward: m <= 256 and 1 <= T <= 256 on the tensor cores")
+        traj = torch.empty((nt,), dtype=torch.float32, device=dev)
+        _lib.slista_forward_traj(B, C, lam, alpha, p, Z, masks, traj, ws=ws, stream=stream)
+        return Z, ForwardState(masks, None, T, traj)
     K = ckpt_every or default_ckpt_every(T)
     masks = torch.empty((max(1, _lib.slista_mask_words(m, N, T)),), dtype=torch.int32, device=dev)
     nck = _lib.slista_ckpt_floats(m, N, T, K)
@@ -109,6 +122,11 @@ def slista_grad(B, C, lam, alpha, state: ForwardState, gZ=None, prec="fp32", str
     T = alpha.shape[0]
     p = _prec(prec)
     dalpha = torch.empty((T,), dtype=torch.float32, device=C.device)
+    if state.traj is not None:
+        ws = workspace(_lib.slista_workspace_bytes(_lib.FN_SLISTA_BWD_TRAJ, m, N, T, p, 1), C.device, "bwd")
+        _lib.slista_backward_traj(B, N, lam, alpha, p, state.masks, state.traj, dalpha, gZ=gZ, ws=ws,
+                                  stream=stream)
+        return dalpha
     ws = workspace(_lib.slista_workspace_bytes(_lib.FN_SLISTA_BWD, m, N, T, p, state.ckpt_every), C.device,
                    "bwd")
     _lib.slista_backward(B, C, lam, alpha, p, state.masks, state.ckpt, state.ckpt_every, dalpha, gZ=gZ,

@@ -168,6 +168,10 @@ size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_ev
             }
             return simt::backward_ws_bytes(m, N, T, ckpt_every < T ? ckpt_every : T);
         case SLISTA_FN_OISTA: return simt::padded_mp(m) ? simt::oista_ws_bytes(m, N, T, prec) : 0;
+        case SLISTA_FN_SLISTA_BWD_TRAJ:
+            if ((prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3) && tc::supported(m) && T >= 1)
+                return tc::backward_traj_ws_bytes(m, N, T);
+            return 0;
         default: return 0;
     }
 }
@@ -275,6 +279,59 @@ int slista_backward(const float *B, const float *C, int m, int N, float lam, con
     if (wide) return tcw::launch_backward(a, prec, ws, as_stream(stream));
     if (tcp) return tc::launch_backward(a, prec, ws, as_stream(stream));
     return simt::launch_backward(a, ws, as_stream(stream));
+}
+
+size_t slista_traj_floats(int m, int N, int T)
+{
+    if (m <= 0 || N < 0 || T < 1) return 0;
+    return tc::traj_floats(m, N, T);
+}
+
+int slista_forward_traj(const float *B, const float *C, int m, int N, float lam, const float *alpha, int T, int prec,
+                        float *Z, uint32_t *masks, float *traj, void *ws, size_t ws_bytes, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 1, SLISTA_ERR_ARG, "slista_forward_traj: bad sizes m=%d N=%d T=%d", m, N,
+                   T);
+    SLISTA_REQUIRE(prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3,
+                   valid_prec(prec) ? SLISTA_ERR_UNSUPPORTED : SLISTA_ERR_ARG,
+                   "slista_forward_traj: precision %d not supported (BF16 or BF16X3)", prec);
+    SLISTA_REQUIRE(tc::supported(m) && T <= 256, SLISTA_ERR_UNSUPPORTED,
+                   "slista_forward_traj: m <= 256 and T <= 256 supported (got m=%d, T=%d)", m, T);
+    SLISTA_REQUIRE(B && alpha, SLISTA_ERR_ARG, "slista_forward_traj: B and alpha must not be NULL");
+    SLISTA_REQUIRE(N == 0 || (C && Z && masks && traj), SLISTA_ERR_ARG,
+                   "slista_forward_traj: C, Z, masks and traj must not be NULL");
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    const size_t need = tc::forward_ws_bytes(m);
+    SLISTA_REQUIRE(ws_bytes >= need && ws != nullptr && ws_aligned(ws), SLISTA_ERR_WORKSPACE,
+                   "slista_forward_traj: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
+    PgdArgs a{B, C, m, N, lam, alpha, nullptr, T, Z, masks, nullptr, T};
+    return tc::launch_forward_traj(a, prec, traj, ws, as_stream(stream));
+}
+
+int slista_backward_traj(const float *B, int m, int N, float lam, const float *alpha, int T, int prec,
+                         const uint32_t *masks, const float *traj, const float *gZ, float *dalpha, void *ws,
+                         size_t ws_bytes, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 1, SLISTA_ERR_ARG, "slista_backward_traj: bad sizes m=%d N=%d T=%d", m,
+                   N, T);
+    SLISTA_REQUIRE(prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3,
+                   valid_prec(prec) ? SLISTA_ERR_UNSUPPORTED : SLISTA_ERR_ARG,
+                   "slista_backward_traj: precision %d not supported (BF16 or BF16X3)", prec);
+    SLISTA_REQUIRE(tc::supported(m) && T <= 256, SLISTA_ERR_UNSUPPORTED,
+                   "slista_backward_traj: m <= 256 and T <= 256 supported (got m=%d, T=%d)", m, T);
+    SLISTA_REQUIRE(B && alpha && dalpha, SLISTA_ERR_ARG, "slista_backward_traj: B, alpha, dalpha must not be NULL");
+    SLISTA_REQUIRE(N == 0 || (masks && traj), SLISTA_ERR_ARG, "slista_backward_traj: masks and traj must not be NULL");
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    const size_t need = tc::backward_traj_ws_bytes(m, N, T);
+    SLISTA_REQUIRE(ws_bytes >= need && ws != nullptr && ws_aligned(ws), SLISTA_ERR_WORKSPACE,
+                   "slista_backward_traj: workspace of %zu bytes (256-byte aligned) needed, %zu given", need,
+                   ws_bytes);
+    BwdArgs a{B, nullptr, m, N, lam, alpha, T, masks, nullptr, T, gZ, dalpha};
+    return tc::launch_backward_traj(a, prec, traj, ws, as_stream(stream));
 }
 
 int oista_forward(const float *B, const float *C, const float *D, int n, int m, int N, float lam, const double *L,

@@ -83,6 +83,13 @@ size_t backward_ws_bytes(int m, int N, int T, int K);
 int launch_backward(const BwdArgs &a, int prec, void *ws, cudaStream_t st);
 int launch_forward_noalloc(const PgdArgs &a, int prec, cudaStream_t st);
 int noalloc_max_m();
+// One-pass backward: the forward writes the adjoint's inputs (the
+// trajectory, traj_floats() floats; 1 <= T <= 256), the backward is one
+// reverse sweep (gZ, if given, replaces dF/dz^(T)).
+size_t traj_floats(int m, int N, int T);
+size_t backward_traj_ws_bytes(int m, int N, int T);
+int launch_forward_traj(const PgdArgs &a, int prec, float *traj, void *ws, cudaStream_t st);
+int launch_backward_traj(const BwdArgs &a, int prec, const float *traj, void *ws, cudaStream_t st);
 }  // namespace tc
 
 namespace tcw {

@@ -397,19 +397,29 @@ struct TcParams {
     const float *gZ;      // nullable upstream gradient
     int want_gT;          // recompute: form G_T after the last layer
     float *partial;       // T x gridDim.x per-CTA sums of dalpha
+    const float *Ginit;   // adjoint: initial G row-major (N x m) instead of Gbuf (nullable)
 };
 
 // ---------------------------------------------------------------------------
-// Forward (RECOMP = false): T layers from z = 0, g = c, writing Z, masks and
-// checkpoints.  Recompute (RECOMP = true): layers [t0, t1) from the
+// Kernel modes (KM):
+// Forward (KM_FWD): T layers from z = 0, g = c, writing Z, masks and
+// checkpoints.  Forward with trajectory (KM_TRAJ): the same, without
+// checkpoints, also writing q_t of every layer into slot t of qbuf and, after
+// one more contraction, dF/dz^(T) = -g^(T) + lam sign(z^(T)) into slot T (the
+// inputs of the adjoint, which then needs no recompute).
+// Recompute (KM_RECOMP): layers [t0, t1) from the
 // checkpoint at t0 with the forward's arithmetic, writing q_t per layer and,
 // for the last segment, G_T = gZ or dF/dz^(T) = -g^(T) + lam sign(z^(T)).
 // Thread (warp w, lane l): tile row 32*(w%4) + l, code columns
 // [CW*(w/4), CW*(w/4) + CW), z of those columns in registers.
 // ---------------------------------------------------------------------------
-template <int MP, bool SPLIT, bool RECOMP>
+enum { KM_FWD = 0, KM_RECOMP = 1, KM_TRAJ = 2 };
+
+template <int MP, bool SPLIT, int KM>
 __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(const TcParams p)
 {
+    constexpr bool RECOMP = KM == KM_RECOMP;
+    constexpr bool WRITE_Q = KM != KM_FWD;
     using CF = Cfg<MP, SPLIT>;
     extern __shared__ uint8_t smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -476,7 +486,7 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
                 }
             }
             const bool last = (t == te - 1);
-            const bool contract_after = !last || (RECOMP && p.want_gT);
+            const bool contract_after = !last || KM == KM_TRAJ || (RECOMP && p.want_gT);
             // --- epilogue: z update and the split step a = z - z' into tensor memory
             // (a = -z' on refresh layers, whose accumulator is reloaded with c)
             const bool refresh = ckpt ? ((t + 1) % p.K == 0) : ((t + 1) % REFRESH == 0);
@@ -491,11 +501,6 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
                     const float zo = z[16 * pc + j];
                     const float u = fmaf(a, gv[j], zo);
                     const float zn = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
-                    if constexpr (RECOMP) {
-                        if (row_ok && col0 + j < m)
-                            p.qbuf[lane_index<MP>(t - tb, p.ntiles, tile, quad, col0 + j, lane)] =
-                                gv[j] - lam * (float)((zn > 0.0f) - (zn < 0.0f));
-                    }
                     gv[j] = refresh ? -zn : zo - zn;  // the MMA's A operand
                     z[16 * pc + j] = zn;
                     word |= (uint32_t)(zn != 0.0f) << (16 * (pc & 1) + j);
@@ -507,6 +512,25 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
                 }
                 if (pc & 1) word = 0u;
             }
+            if constexpr (WRITE_Q) {
+                // q_t = g^(t) - lam sign(z^(t+1)) in a second pass over the
+                // accumulator (still g^(t)), off the first pass's register
+                // budget; every lane takes part in the (warp-wide) loads
+                float *qt = p.qbuf + lane_index<MP>(t - tb, p.ntiles, tile, quad, 0, lane);
+#pragma unroll
+                for (int pc = 0; pc < CF::NPC; ++pc) {
+                    const int col0 = cbase + 16 * pc;
+                    float gv[16];
+                    tmem_ld16(E.taddr(CF::T_G + col0), gv);
+                    if (row_ok)
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float zn = z[16 * pc + j];
+                            if (col0 + j < m)
+                                qt[(size_t)(col0 + j) * 32] = gv[j] - lam * (float)((zn > 0.0f) - (zn < 0.0f));
+                        }
+                }
+            }
             if (refresh && contract_after) {
 #pragma unroll 1
                 for (int pc = 0; pc < CF::NPC; ++pc)
@@ -516,9 +540,13 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
             if (!contract_after) break;
             // --- contraction g += a B on the tensor cores
             if (!E.contract(false)) break;
-            if constexpr (RECOMP) {
+            if constexpr (WRITE_Q) {
                 if (last) {
-                    // G_T = gZ, or dF/dz^(T) = B z - c + lam sign(z) = -g + lam sign(z)
+                    // G_T = gZ, or dF/dz^(T) = B z - c + lam sign(z) = -g + lam sign(z); the
+                    // trajectory keeps the latter in slot T of qbuf
+                    float *gt = RECOMP ? p.Gbuf + lane_index<MP>(0, p.ntiles, tile, quad, 0, lane)
+                                       : p.qbuf + lane_index<MP>(te - tb, p.ntiles, tile, quad, 0, lane);
+                    const float *gz = RECOMP ? p.gZ : nullptr;
 #pragma unroll
                     for (int pc = 0; pc < CF::NPC; ++pc) {
                         const int col0 = cbase + 16 * pc;
@@ -530,8 +558,8 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
                                 if (col0 + j < m) {
                                     const size_t o = (size_t)row * m + col0 + j;
                                     const float zj = z[16 * pc + j];
-                                    p.Gbuf[lane_index<MP>(0, p.ntiles, tile, quad, col0 + j, lane)] =
-                                        p.gZ ? __ldg(p.gZ + o) : -gv[j] + lam * (float)((zj > 0.0f) - (zj < 0.0f));
+                                    gt[(size_t)(col0 + j) * 32] =
+                                        gz ? __ldg(gz + o) : -gv[j] + lam * (float)((zj > 0.0f) - (zj < 0.0f));
                                 }
                     }
                 }
@@ -589,9 +617,20 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
         const int row = tile * TR + quad * 32 + lane;
         const bool row_ok = (quad * 32 + lane < TR) && row < N;
         float G[CF::CW];
+        if (p.Ginit) {
 #pragma unroll
-        for (int j = 0; j < CF::CW; ++j)
-            G[j] = (row_ok && cbase + j < m) ? Gbuf[lane_index<MP>(0, p.ntiles, tile, quad, cbase + j, lane)] : 0.0f;
+            for (int pc = 0; pc < CF::NPC; ++pc) {
+                uint32_t v[16];
+                load_c16(p.Ginit, row, row_ok, m, cbase + 16 * pc, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) G[16 * pc + j] = __uint_as_float(v[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < CF::CW; ++j)
+                G[j] = (row_ok && cbase + j < m) ? Gbuf[lane_index<MP>(0, p.ntiles, tile, quad, cbase + j, lane)]
+                                                 : 0.0f;
+        }
 #pragma unroll 1
         for (int t = p.t1 - 1; t >= p.t0; --t) {
             const float a = __ldg(alpha + t);
@@ -720,7 +759,7 @@ int launch_mp(const PgdArgs &a, void *ws, cudaStream_t st)
     p.K = a.ckpt_every;
     int grid = 0;
     tiling(a.N, &p.TR, &grid);
-    auto k = tc_pgd_forward_kernel<MP, SPLIT, false>;
+    auto k = tc_pgd_forward_kernel<MP, SPLIT, KM_FWD>;
     SLISTA_CUDA_TRY(allow_smem(k, CF::SMEM_STAGED));
     k<<<grid, CF::NT, CF::SMEM_STAGED, st>>>(p);
     return check_launch("tc_pgd_forward_kernel");
@@ -778,7 +817,7 @@ int launch_backward_mp(const BwdArgs &a, void *ws, cudaStream_t st)
     p.partial = partial;
     int grid = 0;
     tiling(a.N, &p.TR, &grid);
-    auto kr = tc_pgd_forward_kernel<MP, SPLIT, true>;
+    auto kr = tc_pgd_forward_kernel<MP, SPLIT, KM_RECOMP>;
     auto ka = tc_adjoint_kernel<MP, SPLIT>;
     SLISTA_CUDA_TRY(allow_smem(kr, CF::SMEM));
     SLISTA_CUDA_TRY(allow_smem(ka, CF::SMEM));
@@ -795,6 +834,93 @@ int launch_backward_mp(const BwdArgs &a, void *ws, cudaStream_t st)
         rc = check_launch("tc_adjoint_kernel");
         if (rc) return rc;
     }
+    tc_reduce_partials_kernel<<<ceil_div(a.T, 8), 256, 0, st>>>(partial, grid, a.T, a.dalpha);
+    return check_launch("tc_reduce_partials_kernel");
+}
+
+// Trajectory of the one-pass backward: (T + 1) slots of the tile layout
+// (lane_index): q_t for t < T, dF/dz^(T) in slot T.
+size_t traj_floats_mp(int MP, int N, int T)
+{
+    int TR = 0, grid = 0;
+    tiling(N, &TR, &grid);
+    const size_t ntiles = N > 0 ? (size_t)ceil_div(N, TR) : 0;
+    return (size_t)(T + 1) * ntiles * 128 * MP;
+}
+
+template <int MP, bool SPLIT>
+int launch_traj_mp(const PgdArgs &a, float *traj, void *ws, cudaStream_t st)
+{
+    using CF = Cfg<MP, SPLIT>;
+    uint8_t *bsplit = reinterpret_cast<uint8_t *>(ws);
+    int rc = split_b<MP, SPLIT>(a.B, a.m, bsplit, st);
+    if (rc) return rc;
+    if (a.N == 0) return SLISTA_OK;
+    TcParams p{};
+    p.Bsplit = bsplit;
+    p.C = a.C;
+    p.m = a.m;
+    p.N = a.N;
+    p.lam = a.lam;
+    p.alpha = a.alpha;
+    p.Lp = a.L;
+    p.T = a.T;
+    p.Z = a.Z;
+    p.masks = a.masks;
+    p.ckpt = nullptr;
+    p.K = a.T;
+    p.qbuf = traj;
+    int grid = 0;
+    tiling(a.N, &p.TR, &grid);
+    p.ntiles = ceil_div(a.N, p.TR);
+    auto k = tc_pgd_forward_kernel<MP, SPLIT, KM_TRAJ>;
+    SLISTA_CUDA_TRY(allow_smem(k, CF::SMEM_STAGED));
+    k<<<grid, CF::NT, CF::SMEM_STAGED, st>>>(p);
+    return check_launch("tc_pgd_forward_kernel (trajectory)");
+}
+
+size_t backward_traj_ws_mp(int MP, int N, int T)
+{
+    int TR = 0, grid = 0;
+    tiling(N, &TR, &grid);
+    return (size_t)MP * MP * 4 + sizeof(float) * (size_t)T * (grid > 0 ? grid : 1) + 256;
+}
+
+template <int MP, bool SPLIT>
+int launch_backward_traj_mp(const BwdArgs &a, const float *traj, void *ws, cudaStream_t st)
+{
+    using CF = Cfg<MP, SPLIT>;
+    uint8_t *bsplit = reinterpret_cast<uint8_t *>(ws);
+    float *partial = reinterpret_cast<float *>(bsplit + (size_t)MP * MP * 4);
+    int rc = split_b<MP, SPLIT>(a.B, a.m, bsplit, st);
+    if (rc) return rc;
+    if (a.N == 0) {
+        SLISTA_CUDA_TRY(cudaMemsetAsync(a.dalpha, 0, sizeof(float) * a.T, st));
+        return SLISTA_OK;
+    }
+    TcParams p{};
+    p.Bsplit = bsplit;
+    p.m = a.m;
+    p.N = a.N;
+    p.lam = a.lam;
+    p.alpha = a.alpha;
+    p.T = a.T;
+    p.masks = const_cast<uint32_t *>(a.masks);
+    int grid = 0;
+    tiling(a.N, &p.TR, &grid);
+    p.ntiles = ceil_div(a.N, p.TR);
+    const size_t tileset = (size_t)p.ntiles * 128 * MP;
+    p.qbuf = const_cast<float *>(traj);
+    p.Gbuf = const_cast<float *>(traj) + (size_t)a.T * tileset;  // read only: one segment
+    p.Ginit = a.gZ;
+    p.partial = partial;
+    p.t0 = 0;
+    p.t1 = a.T;
+    auto ka = tc_adjoint_kernel<MP, SPLIT>;
+    SLISTA_CUDA_TRY(allow_smem(ka, CF::SMEM));
+    ka<<<grid, CF::NT, CF::SMEM, st>>>(p);
+    rc = check_launch("tc_adjoint_kernel (trajectory)");
+    if (rc) return rc;
     tc_reduce_partials_kernel<<<ceil_div(a.T, 8), 256, 0, st>>>(partial, grid, a.T, a.dalpha);
     return check_launch("tc_reduce_partials_kernel");
 }
@@ -838,6 +964,50 @@ int launch_backward(const BwdArgs &a, int prec, void *ws, cudaStream_t st)
         case 256: return split ? launch_backward_mp<256, true>(a, ws, st) : launch_backward_mp<256, false>(a, ws, st);
     }
     return fail(SLISTA_ERR_UNSUPPORTED, "tensor-core path supports m <= 256 (got %d)", a.m);
+}
+
+size_t traj_floats(int m, int N, int T)
+{
+    const int MP = mp_for(m);
+    if (MP == 0 || T < 1 || T > ADJ_KMAX || N < 0) return 0;
+    return traj_floats_mp(MP, N, T);
+}
+
+size_t backward_traj_ws_bytes(int m, int N, int T)
+{
+    const int MP = mp_for(m);
+    if (MP == 0) return 0;
+    return backward_traj_ws_mp(MP, N, T);
+}
+
+int launch_forward_traj(const PgdArgs &a, int prec, float *traj, void *ws, cudaStream_t st)
+{
+    const bool split = prec == SLISTA_PREC_BF16X3;
+    switch (mp_for(a.m)) {
+        case 64: return split ? launch_traj_mp<64, true>(a, traj, ws, st) : launch_traj_mp<64, false>(a, traj, ws, st);
+        case 128:
+            return split ? launch_traj_mp<128, true>(a, traj, ws, st) : launch_traj_mp<128, false>(a, traj, ws, st);
+        case 256:
+            return split ? launch_traj_mp<256, true>(a, traj, ws, st) : launch_traj_mp<256, false>(a, traj, ws, st);
+    }
+    return fail(SLISTA_ERR_UNSUPPORTED, "trajectory forward supports m <= 256 (got %d)", a.m);
+}
+
+int launch_backward_traj(const BwdArgs &a, int prec, const float *traj, void *ws, cudaStream_t st)
+{
+    const bool split = prec == SLISTA_PREC_BF16X3;
+    switch (mp_for(a.m)) {
+        case 64:
+            return split ? launch_backward_traj_mp<64, true>(a, traj, ws, st)
+                         : launch_backward_traj_mp<64, false>(a, traj, ws, st);
+        case 128:
+            return split ? launch_backward_traj_mp<128, true>(a, traj, ws, st)
+                         : launch_backward_traj_mp<128, false>(a, traj, ws, st);
+        case 256:
+            return split ? launch_backward_traj_mp<256, true>(a, traj, ws, st)
+                         : launch_backward_traj_mp<256, false>(a, traj, ws, st);
+    }
+    return fail(SLISTA_ERR_UNSUPPORTED, "trajectory backward supports m <= 256 (got %d)", a.m);
 }
 
 // ---------------------------------------------------------------------------

@@ -98,6 +98,20 @@ def test_argument_validation_without_gpu(lib):
     assert "256-byte" in _err(lib)
     assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, None, None, 1, odd, 1 << 30,
                               None) == _lib.SLISTA_ERR_WORKSPACE
+    # one-pass backward: precision, width and depth limits, workspace
+    assert lib.slista_forward_traj(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_FP32, vp, vp, vp, odd, 1 << 30,
+                                   None) == _lib.SLISTA_ERR_UNSUPPORTED
+    assert lib.slista_forward_traj(vp, vp, 300, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, vp, vp, odd, 1 << 30,
+                                   None) == _lib.SLISTA_ERR_UNSUPPORTED
+    assert lib.slista_backward_traj(vp, 8, 4, 0.1, vp, 300, _lib.PREC_BF16X3, vp, vp, None, vp, odd, 1 << 30,
+                                    None) == _lib.SLISTA_ERR_UNSUPPORTED
+    assert lib.slista_forward_traj(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, None, vp, odd, 1 << 30,
+                                   None) == _lib.SLISTA_ERR_ARG
+    assert lib.slista_forward_traj(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, vp, vp, odd, 1 << 30,
+                                   None) == _lib.SLISTA_ERR_WORKSPACE
+    assert lib.slista_backward_traj(vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, vp, None, vp, odd, 1 << 30,
+                                    None) == _lib.SLISTA_ERR_WORKSPACE
+    assert _lib.slista_traj_floats(300, 4, 3) == 0 and _lib.slista_traj_floats(8, 4, 300) == 0
     # OISTA and objective null pointers
     assert lib.oista_forward(vp, vp, None, 0, 8, 4, 0.1, None, 3, 0, vp, None, None, None, 0, None) == _lib.SLISTA_ERR_ARG
     assert lib.oista_forward(vp, vp, vp, 4, 8, 4, 0.1, vp, 3, 0, vp, None, None, None, 0,

@@ -402,3 +402,68 @@ def test_tc_unaligned_c_matches_aligned():
     d1 = A.slista_grad(g.B, g.C, w.lam, alpha, s1, prec="bf16x3")
     d2 = A.slista_grad(g.B, Cu, w.lam, alpha, s2, prec="bf16x3")
     assert torch.equal(d1, d2)
+
+
+# --------------------------------------------------------------------------- one-pass backward (trajectory)
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("N,T", [(300, 40), (129, 7), (1, 3)])
+def test_tc_traj_backward_matches_oracle_gradient(prec, N, T):
+    """The forward that keeps q_t and dF/dz^(T), then one reverse sweep: the
+    sub-gradient against the FP64 oracle; codes and masks are those of the
+    plain forward (same refresh schedule) bit for bit."""
+    w, alpha = _grad_case(N=N, T=T, seed=17)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    Z, st = A.slista(g.B, g.C, w.lam, dev(alpha), prec=prec, keep_for_backward=True, trajectory=True)
+    assert st.traj is not None and st.ckpt is None
+    assert torch.equal(Z, A.slista(g.B, g.C, w.lam, dev(alpha), prec=prec))
+    dg = host(A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, prec=prec)).astype(np.float64)
+    do, _ = oracle.slista_grad(w.D, w.X, w.lam, alpha)
+    rel = np.linalg.norm(dg - do) / max(np.linalg.norm(do), 1e-12)
+    assert rel <= GRAD_TOL[prec], (prec, N, T, rel)
+
+
+def test_tc_traj_backward_upstream_gradient_and_determinism():
+    w, alpha = _grad_case(N=256, T=12, seed=11)
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    Z, st = A.slista(g.B, g.C, w.lam, dev(alpha), prec="bf16x3", keep_for_backward=True, trajectory=True)
+    d_default = A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, prec="bf16x3")
+    assert torch.equal(d_default, A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, prec="bf16x3"))
+    Bo, Co, _ = oracle.gram(w.D, w.X)
+    Zh = host(Z).astype(np.float64)
+    GT = Zh @ Bo - Co + w.lam * np.sign(Zh)
+    d_gz = host(A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, gZ=dev(GT.astype(np.float32)),
+                              prec="bf16x3")).astype(np.float64)
+    dd = host(d_default).astype(np.float64)
+    assert np.linalg.norm(d_gz - dd) <= 1e-4 * np.linalg.norm(dd)
+    assert not A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, gZ=torch.zeros_like(Z), prec="bf16x3").any()
+    G1 = dev(np.random.default_rng(5).standard_normal(Z.shape).astype(np.float32))
+    d1 = A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, gZ=G1, prec="bf16x3")
+    d2 = A.slista_grad(g.B, g.C, w.lam, dev(alpha), st, gZ=2 * G1, prec="bf16x3")
+    torch.testing.assert_close(d2, 2 * d1, rtol=1e-5, atol=1e-5 * float(d1.abs().max()))
+    # the checkpointed backward with the same upstream gradient
+    _, sc = A.slista(g.B, g.C, w.lam, dev(alpha), prec="bf16x3", keep_for_backward=True, ckpt_every=4)
+    dc = host(A.slista_grad(g.B, g.C, w.lam, dev(alpha), sc, gZ=G1, prec="bf16x3")).astype(np.float64)
+    assert np.linalg.norm(host(d1).astype(np.float64) - dc) <= 1e-4 * np.linalg.norm(dc)
+
+
+def test_tc_traj_full_size_matches_checkpointed():
+    """The benchmark workload (N = 10000, T = 40): the one-pass sub-gradient
+    against the checkpointed one and, on 256 sampled rows, the oracle."""
+    w = synth.slista_64x256()
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    alpha = (1.0 / g.L.double()).float().expand(w.T).contiguous()
+    _, st = A.slista(g.B, g.C, w.lam, alpha, prec="bf16x3", keep_for_backward=True, trajectory=True)
+    dt = A.slista_grad(g.B, g.C, w.lam, alpha, st, prec="bf16x3").double()
+    _, sc = A.slista(g.B, g.C, w.lam, alpha, prec="bf16x3", keep_for_backward=True)
+    dc = A.slista_grad(g.B, g.C, w.lam, alpha, sc, prec="bf16x3").double()
+    torch.testing.assert_close(dt, dc, rtol=1e-4, atol=1e-4 * float(dc.abs().max()))
+    rows = np.random.default_rng(8).choice(w.N, size=256, replace=False)
+    C = g.C[torch.from_numpy(rows).cuda()].contiguous()
+    _, s3 = A.slista(g.B, C, w.lam, alpha, prec="bf16x3", keep_for_backward=True, trajectory=True)
+    dg = host(A.slista_grad(g.B, C, w.lam, alpha, s3, prec="bf16x3")).astype(np.float64)
+    do, _ = oracle.slista_grad(w.D, w.X[rows], w.lam, host(alpha).astype(np.float32))
+    assert np.linalg.norm(dg - do) <= GRAD_TOL["bf16x3"] * np.linalg.norm(do)
