@@ -400,8 +400,13 @@ def oracle_step(w, rows, alpha64, L_fixed_s=None):
     return time.perf_counter() - t0
 
 
+CPU_TARGET_S = 12.0  # CPU work of the default baseline sample
+
+
 def cpu_baseline(w, n_samples: int):
-    """Times the oracle on a bounded sample of the workload (single thread)."""
+    """Times the oracle on a bounded sample of the workload (single thread).
+    n_samples = 0: a 24-sample probe sizes the sample to about CPU_TARGET_S
+    seconds of oracle work (at most the whole batch)."""
     import oracle
     oracle.build()
     D = w.D.astype(np.float64)
@@ -409,6 +414,10 @@ def cpu_baseline(w, n_samples: int):
     L = oracle.lipschitz(D)  # per-dictionary work, charged pro rata below
     fixed = time.perf_counter() - t0
     alpha64 = np.full(w.T, 1.0 / L)
+    if n_samples <= 0:
+        probe = min(24, w.N)
+        tp = oracle_step(w, np.arange(probe), alpha64)
+        n_samples = int(min(w.N, max(probe, round(probe * CPU_TARGET_S / max(tp, 1e-6)))))
     rows = np.arange(n_samples)
     per = oracle_step(w, rows, alpha64)
     per_sample = per / n_samples
@@ -469,8 +478,7 @@ def main():
     out, w = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            ns = args.cpu_samples or 24
-            out["cpu_baseline"] = cpu_baseline(w, ns)
+            out["cpu_baseline"] = cpu_baseline(w, args.cpu_samples)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

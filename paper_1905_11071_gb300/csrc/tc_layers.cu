@@ -670,6 +670,14 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
                 part_s[t - p.t0] += sum;
             }
             if (t == 0) break;  // G^(0) is not needed
+            if (t - 1 >= p.t0) {
+                // q_{t-1} of this warp's codes into L2 while the products run
+                // (one 128-byte line per code: the warp's 32 rows)
+                const float *qn = qbuf + lane_index<MP>(t - 1 - p.t0, p.ntiles, tile, quad, 0, 0);
+#pragma unroll
+                for (int c = lane; c < CF::CW; c += 32) prefetch_l2(qn + (size_t)(cbase + c) * 32);
+                if (row_ok) prefetch_l2(masks + ((size_t)(t - 1) * N + row) * W + (cbase >> 5));
+            }
             // --- B h on the tensor cores, then G = h - alpha_t B h
             if (!E.contract(true)) break;
 #pragma unroll
