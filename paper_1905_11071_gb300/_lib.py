@@ -44,6 +44,11 @@ EXPORTS = [
 ]
 
 
+# entry points that return a size (size_t): every other one returns an int status
+SIZE_RETURNING = ("slista_workspace_bytes", "slista_ckpt_floats", "slista_mask_words",
+                  "slista_batched_workspace_bytes", "slista_traj_floats")
+
+
 class Problem(ctypes.Structure):
     """slista_problem_t: one problem of a ragged batch (device pointers)."""
     _fields_ = [("B", ctypes.c_void_p), ("C", ctypes.c_void_p), ("m", ctypes.c_int), ("N", ctypes.c_int),
@@ -103,8 +108,7 @@ def load(path: str = LIB_PATH):
         lib.slista_forward_batched.argtypes = [pp, i, i, i, i, vp, sz, vp]
         lib.slista_backward_batched.argtypes = [pp, i, i, i, i, vp, sz, vp]
         for name in EXPORTS:
-            if name not in ("slista_last_error", "slista_workspace_bytes", "slista_ckpt_floats",
-                            "slista_mask_words", "slista_batched_workspace_bytes"):
+            if name not in SIZE_RETURNING + ("slista_last_error",):
                 getattr(lib, name).restype = i
         _lib = lib
         return lib

@@ -35,6 +35,20 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(_lib.EXPORTS) <= set(names)
 
 
+def test_size_returning_entry_points_keep_size_t(lib):
+    """The binding types every size_t result as such (a 32-bit int would
+    truncate, e.g., a 10^10-float trajectory and under-allocate it)."""
+    import ctypes
+    for name in _lib.SIZE_RETURNING:
+        assert getattr(lib, name).restype is ctypes.c_size_t, name
+    for name in _lib.EXPORTS:
+        if name not in _lib.SIZE_RETURNING + ("slista_last_error",):
+            assert getattr(lib, name).restype is ctypes.c_int, name
+    assert _lib.slista_mask_words(256, 10 ** 6, 10 ** 4) == 256 // 32 * 10 ** 10  # > 2^32
+    # trajectory sizes of large batches exceed 2^32 floats (device-dependent tiling: >= the plain size)
+    assert _lib.slista_traj_floats(256, 10 ** 6, 40) >= 41 * 10 ** 6 * 256
+
+
 def test_sizes(lib):
     assert _lib.slista_mask_words(256, 10000, 40) == 40 * 10000 * 8
     assert _lib.slista_mask_words(20, 7, 3) == 3 * 7 * 1
