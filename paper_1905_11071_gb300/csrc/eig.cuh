@@ -312,24 +312,42 @@ __device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q,
         for (; j < target; ++j) {
             float w[RPL];
             float dot = 0.0f;
+            if (vec) {
+                // the rows of this lane side by side (one pass over the
+                // Lanczos vector, independent FMA chains per row)
+                const float4 *q4 = reinterpret_cast<const float4 *>(q);
+                float acc[RPL][4];
 #pragma unroll
-            for (int rr = 0; rr < RPL; ++rr) {
-                const int a = lane + 32 * rr;
-                float s = 0.0f;
-                if (a < k) {
-                    const float *row = A + a * lda;
-                    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-                    if (vec) {
-                        const float4 *r4 = reinterpret_cast<const float4 *>(row);
-                        const float4 *q4 = reinterpret_cast<const float4 *>(q);
-                        for (int u = 0; u < ku; ++u) {
-                            const float4 x = r4[u], y = q4[u];
-                            s0 = fmaf(x.x, y.x, s0);
-                            s1 = fmaf(x.y, y.y, s1);
-                            s2 = fmaf(x.z, y.z, s2);
-                            s3 = fmaf(x.w, y.w, s3);
+                for (int rr = 0; rr < RPL; ++rr) acc[rr][0] = acc[rr][1] = acc[rr][2] = acc[rr][3] = 0.0f;
+                for (int u = 0; u < ku; ++u) {
+                    const float4 y = q4[u];
+#pragma unroll
+                    for (int rr = 0; rr < RPL; ++rr) {
+                        const int a = lane + 32 * rr;
+                        if (a < k) {
+                            const float4 x = reinterpret_cast<const float4 *>(A + a * lda)[u];
+                            acc[rr][0] = fmaf(x.x, y.x, acc[rr][0]);
+                            acc[rr][1] = fmaf(x.y, y.y, acc[rr][1]);
+                            acc[rr][2] = fmaf(x.z, y.z, acc[rr][2]);
+                            acc[rr][3] = fmaf(x.w, y.w, acc[rr][3]);
                         }
-                    } else {
+                    }
+                }
+#pragma unroll
+                for (int rr = 0; rr < RPL; ++rr) {
+                    const int a = lane + 32 * rr;
+                    const float sv = (acc[rr][0] + acc[rr][1]) + (acc[rr][2] + acc[rr][3]);
+                    w[rr] = a < k ? sv : 0.0f;
+                    if (a < k) dot = fmaf(sv, q[a], dot);
+                }
+            } else {
+#pragma unroll
+                for (int rr = 0; rr < RPL; ++rr) {
+                    const int a = lane + 32 * rr;
+                    float sv = 0.0f;
+                    if (a < k) {
+                        const float *row = A + a * lda;
+                        float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
                         int b = 0;
                         for (; b + 3 < k; b += 4) {
                             s0 = fmaf(row[b], q[b], s0);
@@ -338,11 +356,11 @@ __device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q,
                             s3 = fmaf(row[b + 3], q[b + 3], s3);
                         }
                         for (; b < k; ++b) s0 = fmaf(row[b], q[b], s0);
+                        sv = (s0 + s1) + (s2 + s3);
+                        dot = fmaf(sv, q[a], dot);
                     }
-                    s = (s0 + s1) + (s2 + s3);
-                    dot = fmaf(s, q[a], dot);
+                    w[rr] = sv;
                 }
-                w[rr] = s;
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
