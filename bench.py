@@ -338,6 +338,13 @@ def run_ours(args, rank, world, local_rank):
     else:
         layer_peak = fp32_peak
         layer_bound, layer_src = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+    oista_work = 2 * mm * mm * (T - 1) * N / 1e12
+    if args.oista_prec in ("bf16", "bf16x3"):
+        onprod = 3 if args.oista_prec == "bf16x3" else 1
+        oista_algo = ("tensor", oista_work, "TFLOP/s", pk["bf16_tflops"] / onprod,
+                      "%s bf16_tflops (burst) / %d products" % (pk_kind, onprod))
+    else:
+        oista_algo = ("alu", oista_work, "TFLOP/s", fp32_peak, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz")
     algo = {
         # useful B z products: 2 m^2 per sample per layer (T - 1 contractions; T with the
         # trajectory, whose forward also forms g^(T))
@@ -346,9 +353,9 @@ def run_ours(args, rank, world, local_rank):
         # adjoint: B h (T - 1), plus the recompute (K - 1 contractions per segment, + 1 for g^(T))
         "slista_bwd": (layer_bound, 2 * mm * mm * ((T - 1) if traj else (2 * T - nseg)) * N / 1e12, "TFLOP/s",
                        layer_peak, layer_src),
-        # Oracle-ISTA: the layer products only (eigen-solves not counted), FP32 CUDA cores
-        "oista_fwd": ("alu", 2 * mm * mm * (T - 1) * N / 1e12, "TFLOP/s", fp32_peak,
-                      "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"),
+        # Oracle-ISTA: the layer products only (the eigen-solves, which take most of its
+        # time on the CUDA cores, are not counted), on the tensor cores or the CUDA cores
+        "oista_fwd": oista_algo,
         # Gram: read D, X, write B, C, xsq
         "gram": ("hbm", (4.0 * (n * m + N * n + N * m + m * m) + 8.0 * N) / 1e9, "GB/s", pk["hbm_gbs"], pk_kind),
         # objective: read Z, C, xsq, B, write F, gap
