@@ -10,8 +10,9 @@ Tolerances (FP32 path; see the design doc for the derivation):
   * step-size sub-gradient: ||d_gpu - d_oracle||_2 <= 1e-4 ||d_oracle||_2;
   * Oracle-ISTA: the same bounds on samples whose decision margin along the
     oracle trajectory exceeds 5e-6 (smaller margins can flip on rounding);
-  * L and L_S: relative error <= 1e-5 (FP32 Householder reduction, backward
-    error about 4 k 2^-24 for k <= 64).
+  * L and L_S: relative error <= 1e-5 (FP32 Lanczos and Sturm multisection:
+    rounding of the products and of the pivots, about k 2^-24 for k <= 64,
+    plus the stopping rule's 2e-7).
 """
 import numpy as np
 import pytest
