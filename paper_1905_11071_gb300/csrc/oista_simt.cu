@@ -452,6 +452,10 @@ __global__ void __launch_bounds__((A_WARPS + S_WARPS) * 32, 1) oista_solve_kerne
     extern __shared__ float4 smem4[];
     const int warp = threadIdx.x >> 5;
     const int par = t & 1;
+    // launched as a programmatic dependent of the previous layer's kernel:
+    // nothing of it is read or written before this
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (blockIdx.x == 0 && threadIdx.x < NCLS) ws.counter[NCLS * (par ^ 1) + threadIdx.x] = 0;  // next layer's lists
     const double L = __ldg(Lp);
     if (warp >= A_WARPS) {
@@ -682,8 +686,22 @@ int launch_oista_mp(const OistaArgs &a, void *wsp, cudaStream_t st)
     if (rc) return rc;
     const int solve_grid = num_sms();
     for (int t = 0; t < a.T; ++t) {
-        oista_solve_kernel<<<solve_grid, (A_WARPS + S_WARPS) * 32, solve_smem, st>>>(a.B, have_D, a.n, a.m, a.L, ws,
-                                                                                       t);
+        if (tc) {  // may start while the previous layer's kernel finishes (griddepcontrol.wait inside)
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3(solve_grid);
+            cfg.blockDim = dim3((A_WARPS + S_WARPS) * 32);
+            cfg.dynamicSmemBytes = solve_smem;
+            cfg.stream = st;
+            cudaLaunchAttribute attr{};
+            attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr.val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = &attr;
+            cfg.numAttrs = 1;
+            SLISTA_CUDA_TRY(cudaLaunchKernelEx(&cfg, oista_solve_kernel, a.B, have_D, a.n, a.m, a.L, ws, t));
+        } else {
+            oista_solve_kernel<<<solve_grid, (A_WARPS + S_WARPS) * 32, solve_smem, st>>>(a.B, have_D, a.n, a.m, a.L,
+                                                                                           ws, t);
+        }
         rc = check_launch("oista_solve_kernel");
         if (rc) return rc;
         if (tc) {

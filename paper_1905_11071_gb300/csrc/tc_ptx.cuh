@@ -65,6 +65,14 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  : "memory");
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while its predecessor in the
+// stream finishes; it must wait here before touching anything the
+// predecessor writes or reads (a no-op for an ordinary launch).  The
+// trigger lets the next such kernel start as this one's CTAs leave the SMs.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Brings the 128-byte line at a global address into L2 (no register result).
 __device__ __forceinline__ void prefetch_l2(const void *p)
 {

@@ -323,6 +323,10 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    // (Oracle-ISTA layers are launched as programmatic dependents of the
+    // solve kernel: nothing of the previous kernels is read before this)
+    grid_dependency_wait();
+    grid_dependents_launch();
 
     const float a = L.alpha ? __ldg(L.alpha + L.t) : (float)(1.0 / __ldg(L.Lp));
     const uint8_t *Bcol = L.Bt + (size_t)(col0 / BN) * nkc * TILE_PAIR;
@@ -695,7 +699,7 @@ int split_tiles(const float *B, int m, uint8_t *out, cudaStream_t st)
 }
 
 template <bool SPLIT, int MODE, int NP>
-int launch_chunk(const WLayer *Ls, int count, cudaStream_t st)
+int launch_chunk(const WLayer *Ls, int count, cudaStream_t st, bool dependent = false)
 {
     WBatch<NP> P{};
     P.nprob = count;
@@ -707,7 +711,21 @@ int launch_chunk(const WLayer *Ls, int count, cudaStream_t st)
     if (P.base[count] == 0) return SLISTA_OK;
     auto k = tcw_layer_kernel<SPLIT, MODE, NP>;
     SLISTA_CUDA_TRY(allow_smem(k, WCfg<SPLIT>::SMEM));
-    k<<<P.base[count], NT, WCfg<SPLIT>::SMEM, st>>>(P);
+    if (dependent) {  // may start while the previous kernel in the stream finishes (see grid_dependency_wait)
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(P.base[count]);
+        cfg.blockDim = dim3(NT);
+        cfg.dynamicSmemBytes = WCfg<SPLIT>::SMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute attr{};
+        attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr.val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        SLISTA_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, P));
+    } else {
+        k<<<P.base[count], NT, WCfg<SPLIT>::SMEM, st>>>(P);
+    }
     return check_launch(MODE == FWD   ? "tcw_layer_kernel (forward)"
                         : MODE == ADJ ? "tcw_layer_kernel (adjoint)"
                                       : "tcw_layer_kernel (Oracle-ISTA step)");
@@ -1003,7 +1021,7 @@ int launch_oista_step(const OistaStep &o, int prec, cudaStream_t st)
     const int rounds = ceil_div(ceil_div(o.N, BM), sms);
     L.TR = o.N > 0 ? ceil_div(o.N, (long long)rounds * sms) : BM;
     const bool split = prec == SLISTA_PREC_BF16X3;
-    return split ? launch_chunk<true, OIS, 1>(&L, 1, st) : launch_chunk<false, OIS, 1>(&L, 1, st);
+    return split ? launch_chunk<true, OIS, 1>(&L, 1, st, true) : launch_chunk<false, OIS, 1>(&L, 1, st, true);
 }
 
 int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st)
