@@ -323,12 +323,6 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    // (Oracle-ISTA layers are launched as programmatic dependents of the
-    // solve kernel: nothing of the previous kernels is read before this)
-    grid_dependency_wait();
-    grid_dependents_launch();
-
-    const float a = L.alpha ? __ldg(L.alpha + L.t) : (float)(1.0 / __ldg(L.Lp));
     const uint8_t *Bcol = L.Bt + (size_t)(col0 / BN) * nkc * TILE_PAIR;
     const float *Zs = L.Zin;
     const float *Gs = (MODE == FWD && L.Zin == nullptr) ? L.C : L.Gin;
@@ -349,6 +343,17 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         pend &= ~(1u << s);
         return ok;
     };
+    // The first two B tiles are in flight before the wait below: the tiles
+    // are written once, before the layers.  Oracle-ISTA layers are launched
+    // as programmatic dependents of the solve kernel: nothing else of the
+    // previous kernels is read or written before the wait.
+    if (do_mma && tid == 0) {
+        issue_b(0);
+        if (nkc > 1) issue_b(1);
+    }
+    grid_dependency_wait();
+    grid_dependents_launch();
+    const float a = L.alpha ? __ldg(L.alpha + L.t) : (float)(1.0 / __ldg(L.Lp));
 
     // epilogue rows: warp w reads TMEM lanes 32 (w % 4).. (the tile rows)
     const int q = warp & 3, cg = warp >> 2;
@@ -393,10 +398,6 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
     // MMA issue, so their latency overlaps the tensor-core work
     float nz[16], ng[16];
     if (do_mma) {
-        if (tid == 0) {
-            issue_b(0);
-            if (nkc > 1) issue_b(1);
-        }
         if (MODE != ADJ) {
             load16(Zs, grow, rok, m, pk, nz);
             load16(Gs, grow, rok, m, pk, ng);
