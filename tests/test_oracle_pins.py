@@ -298,6 +298,91 @@ def test_oista_monotone_and_safe_regime():
         assert abs(LS[i] - oracle.support_lipschitz(D, mask, L)) < 1e-12
 
 
+def _support_identification(Zall, zstar_support):
+    """T* of Prop. 3.1: the first iteration from which every iterate has the
+    support of z*."""
+    same = np.array([np.array_equal(z != 0, zstar_support) for z in Zall])
+    off = np.where(~same)[0]
+    assert len(off) and not same[0] and same[-1]
+    return int(off.max()) + 1
+
+
+def test_oista_rates_after_support_identification():
+    """Prop. 3.2: for t > T*, F(z^t) - F* <= L_S* ||z* - z^T*||^2 / (2(t - T*))
+    and, with mu* = min eig D_S*^T D_S* > 0, F(z^t) - F* <=
+    (1 - mu*/L_S*)^(t - T*) (F(z^T*) - F*).  The linear bound has teeth:
+    ISTA's 1/L steps, run through the same test, break it (the step on the
+    identified support must be 1/L_S*, not 1/L)."""
+    w = synth.paper_binf(10, 50, N=4, lam=0.5, T=300, seed=3)
+    D = w.D.astype(np.float64)
+    L = oracle.lipschitz(D)
+    Zo, _, _, dec = oracle.oista(D, w.X, w.lam, L, w.T, keep_all=True)
+    Zi = oracle.pgd(D, w.X, w.lam, np.full(w.T, 1.0 / L), keep_all=True)
+    Zstar = oracle.oista(D, w.X, w.lam, L, 3000)[0]
+    Fstar = oracle.objective(D, w.X, Zstar, w.lam, with_gap=False)
+
+    def bounds(Zall, i):
+        S = Zstar[i] != 0
+        T0 = _support_identification(Zall[:, i], S)
+        LS = oracle.support_lipschitz(D, S, L)
+        mu = np.linalg.eigvalsh(D[:, S].T @ D[:, S]).min()
+        assert mu > 0
+        F = oracle.objective(D, np.repeat(w.X[i:i + 1], w.T + 1, 0), Zall[:, i], w.lam,
+                             with_gap=False)
+        t = np.arange(T0 + 1, w.T + 1)
+        gap = F[t] - Fstar[i]
+        sub = LS * np.sum((Zstar[i] - Zall[T0, i]) ** 2) / (2 * (t - T0))
+        lin = (1 - mu / LS) ** (t - T0) * (F[T0] - Fstar[i])
+        return T0, (gap <= sub + 1e-13).all(), (gap <= lin + 1e-13).all()
+
+    for i in range(w.N):
+        T0, sub_ok, lin_ok = bounds(Zo, i)
+        assert T0 < w.T - 100 and dec[T0:, i].all()
+        assert sub_ok and lin_ok, i
+        assert not bounds(Zi, i)[2], i
+
+
+def test_oista_orthogonal_support_one_step():
+    """Prop. 3.3: if D_S*^T D_S* = L_S* Id, OISTA returns z* one iteration after
+    it identifies S*.  Here S* holds 4 orthonormal columns (L_S* = 1, so
+    z*_S* = ST(D_S*^T x, lam) by KKT) inside a 12 x 30 dictionary with L > 5;
+    ISTA's 1/L step from the same support is still far from z*."""
+    rng = np.random.default_rng(21)
+    n, m, k = 12, 30, 4
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    D = np.empty((n, m))
+    D[:, :k] = Q[:, :k]
+    for j in range(k, m):  # mostly outside span(D_S*), unit norm
+        v = Q[:, k:] @ rng.standard_normal(n - k) + 0.15 * (Q[:, :k] @ rng.standard_normal(k))
+        D[:, j] = v / np.linalg.norm(v)
+    perm = rng.permutation(m)
+    D = D[:, perm]
+    S = np.sort(np.where(perm < k)[0])
+    lam = 0.3
+    coef = np.array([2.0, -1.5, 1.8, -2.2])
+    X = np.stack([s * (D[:, S] @ coef) for s in (1.0, 0.7)])
+    L = oracle.lipschitz(D)
+    assert L > 5
+    for i in range(2):
+        zstar = np.zeros(m)
+        zstar[S] = _st_by_hand(X[i] @ D[:, S], lam)
+        assert oracle.kkt_violation(D, X[i], zstar, lam) < 1e-13
+        Zall, LS, _, dec = oracle.oista(D, X[i:i + 1], lam, L, 30, keep_all=True)
+        T0 = next(t for t in range(31) if np.array_equal(np.nonzero(Zall[t, 0])[0], S))
+        assert T0 >= 2
+        np.testing.assert_allclose(Zall[T0 + 1, 0], zstar, rtol=0, atol=1e-14)
+        assert np.abs(Zall[T0, 0] - zstar).max() > 1e-3
+        assert abs(LS[0] - 1.0) < 1e-14
+        # the same support reached with 1/L steps is not yet z*
+        Zi = oracle.pgd(D, X[i:i + 1], lam, np.full(30, 1.0 / L), keep_all=True)
+        assert np.abs(Zi[T0 + 1, 0] - zstar).max() > 0.1
+
+
+def _st_by_hand(v, theta):
+    """Soft-thresholding written out for the test (Section 1)."""
+    return np.sign(v) * np.maximum(np.abs(v) - theta, 0.0)
+
+
 def test_oista_faster_than_ista():
     """Fig. B.2: OISTA reaches F* + 1e-13 in no more iterations than ISTA
     (D 100 x 200, samples in B_inf, high regularisation)."""
