@@ -148,6 +148,28 @@ def paper_binf(n: int, m: int, N: int, lam: float, T: int, seed: int = 0) -> Wor
     return Workload("binf_%dx%d" % (n, m), D, X, float(np.float32(lam)), T, seed)
 
 
+def orthogonal_support(n: int = 12, m: int = 30, k: int = 4, N: int = 2, leak: float = 0.15,
+                       seed: int = 21, dtype=np.float32):
+    """The setting of Prop. 3.3: k of the m unit columns (positions S, sorted)
+    are orthonormal, the others lie mostly outside their span (a component of
+    relative size ~leak inside it); sample i is x_i = D_S c_i with
+    |c_i| ~ U[1.5, 2.5] and random signs.  Returns (D, X, S), D n x m and X
+    N x n in ``dtype`` (drawn in float64, rounded once)."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    D = np.empty((n, m))
+    D[:, :k] = Q[:, :k]
+    for j in range(k, m):
+        v = Q[:, k:] @ rng.standard_normal(n - k) + leak * (Q[:, :k] @ rng.standard_normal(k))
+        D[:, j] = v / np.linalg.norm(v)
+    perm = rng.permutation(m)
+    D = D[:, perm]
+    S = np.sort(np.where(perm < k)[0])
+    coef = rng.uniform(1.5, 2.5, size=(N, k)) * rng.choice([-1.0, 1.0], size=(N, k))
+    X = coef @ D[:, S].T
+    return D.astype(dtype), X.astype(dtype), S
+
+
 def step_sizes(T: int, base: float, spread: float, seed: int) -> np.ndarray:
     """T positive step sizes base * U[1 - spread, 1 + spread] (float32)."""
     rng = np.random.default_rng(seed)

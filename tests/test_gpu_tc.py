@@ -384,6 +384,33 @@ def test_oista_odd_batch(prec):
     assert np.abs(host(accg) - acco).max() <= (~safe).sum()
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_oista_orthogonal_support_one_step(prec):
+    """Prop. 3.3 on the GPU: with 4 orthonormal columns S* (L_S* = 1) inside a
+    12 x 30 dictionary (L ~ 5.5) and x_i = D_S* c_i, one layer after the
+    oracle identifies S* the codes are z*_S* = ST(D_S*^T x, lam) (KKT), while
+    ISTA's 1/L steps after as many layers are still far from it."""
+    D, X, S = synth.orthogonal_support(N=64, seed=22)
+    lam = 0.3
+    Lo = oracle.lipschitz(D)
+    Zall, _, _, _, marg = oracle.oista(D, X, lam, Lo, 30, keep_all=True, with_margin=True)
+    T0 = [next(t for t in range(31) if np.array_equal(np.nonzero(Zall[t, i])[0], S)) for i in range(len(X))]
+    T = max(T0) + 1
+    safe = marg > TC_OISTA_MARGIN
+    assert safe.sum() >= 48
+    v = X.astype(np.float64) @ D[:, S].astype(np.float64)
+    zstar = np.zeros((len(X), D.shape[1]))
+    zstar[:, S] = np.sign(v) * np.maximum(np.abs(v) - lam, 0.0)
+    zi = oracle.pgd(D, X, lam, np.full(T, 1.0 / Lo))
+    assert (np.abs(zi - zstar).max(axis=1) > 0.1).all()
+    A = api()
+    g = A.gram(dev(D), dev(X))
+    Zg, LSg, _ = A.oista(g.B, g.C, lam, g.L, T, prec=prec)
+    zt = (TOL["bf16x3"]["Z"] if prec == "bf16x3" else 2e-5) * max(1.0, float(np.abs(zstar).max()))
+    assert np.abs(host(Zg)[safe].astype(np.float64) - zstar[safe]).max() <= zt
+    np.testing.assert_allclose(host(LSg)[safe], 1.0, rtol=1e-5)
+
+
 def test_tc_unaligned_c_matches_aligned():
     """C passed at an address 4 bytes past a 16-byte boundary (a view into a
     larger buffer): the layer kernels fall back to scalar loads and give the

@@ -347,25 +347,15 @@ def test_oista_orthogonal_support_one_step():
     it identifies S*.  Here S* holds 4 orthonormal columns (L_S* = 1, so
     z*_S* = ST(D_S*^T x, lam) by KKT) inside a 12 x 30 dictionary with L > 5;
     ISTA's 1/L step from the same support is still far from z*."""
-    rng = np.random.default_rng(21)
-    n, m, k = 12, 30, 4
-    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
-    D = np.empty((n, m))
-    D[:, :k] = Q[:, :k]
-    for j in range(k, m):  # mostly outside span(D_S*), unit norm
-        v = Q[:, k:] @ rng.standard_normal(n - k) + 0.15 * (Q[:, :k] @ rng.standard_normal(k))
-        D[:, j] = v / np.linalg.norm(v)
-    perm = rng.permutation(m)
-    D = D[:, perm]
-    S = np.sort(np.where(perm < k)[0])
+    D, X, S = synth.orthogonal_support(N=3, dtype=np.float64)
+    m = D.shape[1]
     lam = 0.3
-    coef = np.array([2.0, -1.5, 1.8, -2.2])
-    X = np.stack([s * (D[:, S] @ coef) for s in (1.0, 0.7)])
     L = oracle.lipschitz(D)
     assert L > 5
-    for i in range(2):
+    for i in range(X.shape[0]):
         zstar = np.zeros(m)
         zstar[S] = _st_by_hand(X[i] @ D[:, S], lam)
+        assert (zstar[S] != 0).all()
         assert oracle.kkt_violation(D, X[i], zstar, lam) < 1e-13
         Zall, LS, _, dec = oracle.oista(D, X[i:i + 1], lam, L, 30, keep_all=True)
         T0 = next(t for t in range(31) if np.array_equal(np.nonzero(Zall[t, 0])[0], S))
