@@ -149,14 +149,22 @@ def arm_config(w, args, world: int) -> dict:
             "parallelism": "dp%d" % world if world > 1 else "single"}
 
 
-def recorded_traffic(part: str):
+TRAFFIC_KEYS = ("n", "m", "N_per_gpu", "T", "backward", "prec", "oista_prec")
+
+
+def recorded_traffic(part: str, config: dict):
     """DRAM bytes per call of a bench part from the committed ncu capture
-    (profiles/dram_traffic.json), or None when any source file of that part
-    changed since the counters were taken (sha256 recorded with them)."""
+    (profiles/dram_traffic.json), or None when the capture's workload differs
+    from ``config`` (sizes, precisions, backward mode) or any source file of
+    that part changed since the counters were taken (sha256 recorded with
+    them)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
-            rec = json.load(f)["parts"][part]
+            doc = json.load(f)
+        if any(doc["config"][k] != config[k] for k in TRAFFIC_KEYS):
+            return None
+        rec = doc["parts"][part]
         for rel, digest in rec["sources"].items():
             with open(os.path.join(ROOT, rel), "rb") as g:
                 if hashlib.sha256(g.read()).hexdigest() != digest:
@@ -372,7 +380,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(parts, key=lambda p: per_part[p])
     r = rooflines[dom]
     roofline = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
-                "unit": r["unit"], "frac": r["frac"], "traffic": recorded_traffic(dom),
+                "unit": r["unit"], "frac": r["frac"], "traffic": recorded_traffic(dom, arm_config(w, args, world)),
                 "traffic_unit": "bytes per call (dram__bytes_read.sum + dram__bytes_write.sum, profiles/dram_traffic.json)",
                 "peak_source": r["peak_source"]}
 
