@@ -79,6 +79,7 @@ extern "C" {
 #define SLISTA_FN_OISTA      4
 #define SLISTA_FN_OBJECTIVE  5
 #define SLISTA_FN_SLISTA_BWD_TRAJ 6
+#define SLISTA_FN_SUPPORT_LIPSCHITZ 7
 
 /* Message describing the last failed call on this host thread ("" if none). */
 SLISTA_API const char *slista_last_error(void);
@@ -275,10 +276,24 @@ SLISTA_API int slista_backward_batched(const slista_problem_t *problems, int cou
  * supp(z^(T-1)), the support the last layer's candidate step used;
  * accepted (T ints, nullable) = number of samples whose step t met condition
  * (star) (zeroed by the call).  Workspace: the per-sample state of the layer
- * loop (slista_workspace_bytes(SLISTA_FN_OISTA, ...)).  Only SLISTA_PREC_FP32. */
+ * loop (slista_workspace_bytes(SLISTA_FN_OISTA, ...)).  prec: SLISTA_PREC_FP32
+ * (layers on the CUDA cores) or SLISTA_PREC_BF16X3 / SLISTA_PREC_BF16 (layer
+ * products on the tensor cores); TF32 is not built.  m <= 256. */
 SLISTA_API int oista_forward(const float *B, const float *C, const float *D, int n, int m, int N,
                              float lam, const double *L, int T, int prec, float *Z, double *LS,
                              int *accepted, void *ws, size_t ws_bytes, void *stream);
+
+/* L_S = largest eigenvalue of B_SS for N given supports S_i (Eq. spca,
+ * Section 3; L_empty = L), by the eigen-solver of oista_forward's layers:
+ * Lanczos in FP32 on B_SS, or on D_S D_S^T for |S| > 64 when D (n x m,
+ * nullable; used when n <= 64) is given; |S| = 1 gives B_jj exactly; relative
+ * accuracy about 1e-6.  S: N x ceil(m/32) uint32 words, bit j % 32 of word
+ * j / 32 of row i set iff code j is in S_i (one layer of the support masks);
+ * bits of codes >= m are ignored.  L: device pointer to L (1 double).  LS: N
+ * doubles (out).  All device pointers, caller-owned.  m <= 256.  Workspace:
+ * slista_workspace_bytes(SLISTA_FN_SUPPORT_LIPSCHITZ, m, N, 0, 0, 0). */
+SLISTA_API int lasso_support_lipschitz(const float *B, const float *D, int n, int m, int N, const uint32_t *S,
+                                       const double *L, double *LS, void *ws, size_t ws_bytes, void *stream);
 
 /* Per-sample Lasso objective (Eq. lasso) evaluated from the Gram quantities,
  *     F_i = 1/2 xsq_i - c_i^T z_i + 1/2 z_i^T B z_i + lam ||z_i||_1,

@@ -34,13 +34,14 @@ FN_SLISTA_BWD = 3
 FN_OISTA = 4
 FN_OBJECTIVE = 5
 FN_SLISTA_BWD_TRAJ = 6
+FN_SUPPORT_LIPSCHITZ = 7
 
 EXPORTS = [
     "slista_last_error", "slista_device_status", "slista_workspace_bytes", "slista_ckpt_floats",
     "slista_mask_words", "lasso_gram", "lasso_lipschitz", "ista_forward", "slista_forward",
     "slista_backward", "oista_forward", "lasso_objective", "slista_forward_noalloc",
     "slista_batched_workspace_bytes", "slista_forward_batched", "slista_backward_batched",
-    "slista_traj_floats", "slista_forward_traj", "slista_backward_traj",
+    "slista_traj_floats", "slista_forward_traj", "slista_backward_traj", "lasso_support_lipschitz",
 ]
 
 
@@ -102,6 +103,7 @@ def load(path: str = LIB_PATH):
         lib.slista_backward_traj.argtypes = [vp, i, i, f, vp, i, i, vp, vp, vp, vp, vp, sz, vp]
         lib.oista_forward.argtypes = [vp, vp, vp, i, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
         lib.lasso_objective.argtypes = [vp, vp, vp, vp, i, i, f, vp, vp, vp]
+        lib.lasso_support_lipschitz.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, sz, vp]
         pp = ctypes.POINTER(Problem)
         lib.slista_batched_workspace_bytes.restype = sz
         lib.slista_batched_workspace_bytes.argtypes = [i, pp, i, i, i, i]
@@ -322,6 +324,22 @@ def oista_forward(B, C, lam, L, T, prec, Z, LS=None, accepted=None, ws=None, D=N
     wsb = 0 if ws is None else ws.numel() * ws.element_size()
     _check(load().oista_forward(_ptr(B), _ptr(C), _ptr(D), n, m, N, float(lam), _ptr(L), int(T), int(prec), _ptr(Z),
                                 _ptr(LS), _ptr(accepted), _ptr(ws), wsb, _stream(stream)), "oista_forward")
+
+
+def lasso_support_lipschitz(B, S, L, LS, ws=None, D=None, stream=None) -> None:
+    """L_S for the N supports given as rows of S (N x ceil(m/32) int32 words)."""
+    import torch
+    m = B.shape[0]
+    N = S.shape[0]
+    n = 0 if D is None else D.shape[0]
+    _need(B, torch.float32, (m, m), "B")
+    _opt(D, torch.float32, (n, m), "D")
+    _need(S, torch.int32, (N, (m + 31) // 32), "S")
+    _need(L, torch.float64, (1,), "L")
+    _need(LS, torch.float64, (N,), "LS")
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().lasso_support_lipschitz(_ptr(B), _ptr(D), n, m, N, _ptr(S), _ptr(L), _ptr(LS), _ptr(ws), wsb,
+                                          _stream(stream)), "lasso_support_lipschitz")
 
 
 def lasso_objective(B, C, xsq, Z, lam, F, gap=None, stream=None) -> None:

@@ -200,6 +200,17 @@ def oista(B, C, lam, L, T, D=None, prec="fp32", stream=None):
     return Z, LS, acc[:T]
 
 
+def support_lipschitz(B, S, L, D=None, stream=None):
+    """L_S (Eq. spca) for the N supports given as rows of S, N x ceil(m/32)
+    int32 words (bit j % 32 of word j / 32 set iff code j is in the support;
+    one layer of the support masks).  Returns LS (N doubles)."""
+    N, m = S.shape[0], B.shape[0]
+    LS = torch.empty((N,), dtype=torch.float64, device=B.device)
+    ws = workspace(_lib.slista_workspace_bytes(_lib.FN_SUPPORT_LIPSCHITZ, m, N, 0, 0), B.device, "support_ls")
+    _lib.lasso_support_lipschitz(B, S, L, LS, ws=ws, D=D, stream=stream)
+    return LS
+
+
 def objective(B, C, xsq, Z, lam, with_gap: bool = True, stream=None):
     N = C.shape[0]
     F = torch.empty((N,), dtype=torch.float64, device=C.device)

@@ -172,6 +172,7 @@ size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_ev
             if ((prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3) && tc::supported(m) && T >= 1)
                 return tc::backward_traj_ws_bytes(m, N, T);
             return 0;
+        case SLISTA_FN_SUPPORT_LIPSCHITZ: return simt::padded_mp(m) && N > 0 ? simt::support_ls_ws_bytes(m, N) : 0;
         default: return 0;
     }
 }
@@ -352,6 +353,23 @@ int oista_forward(const float *B, const float *C, const float *D, int n, int m, 
                    "oista_forward: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
     OistaArgs a{B, C, D, D ? n : 0, m, N, lam, L, T, Z, LS, accepted, prec};
     return simt::launch_oista(a, ws, as_stream(stream));
+}
+
+int lasso_support_lipschitz(const float *B, const float *D, int n, int m, int N, const uint32_t *S, const double *L,
+                            double *LS, void *ws, size_t ws_bytes, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(m >= 1 && N >= 0, SLISTA_ERR_ARG, "lasso_support_lipschitz: bad sizes m=%d N=%d", m, N);
+    SLISTA_REQUIRE(simt::padded_mp(m) != 0, SLISTA_ERR_UNSUPPORTED, "lasso_support_lipschitz: m <= 256 supported");
+    SLISTA_REQUIRE(!D || n >= 1, SLISTA_ERR_ARG, "lasso_support_lipschitz: n must be >= 1 when D is given");
+    SLISTA_REQUIRE(N == 0 || (B && S && L && LS), SLISTA_ERR_ARG,
+                   "lasso_support_lipschitz: B, S, L and LS must not be NULL");
+    const size_t need = N > 0 ? simt::support_ls_ws_bytes(m, N) : 0;
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
+                   "lasso_support_lipschitz: workspace of %zu bytes (256-byte aligned) needed, %zu given", need,
+                   ws_bytes);
+    SupportLsArgs a{B, D, D ? n : 0, m, N, S, L, LS};
+    return simt::launch_support_lipschitz(a, ws, as_stream(stream));
 }
 
 int lasso_objective(const float *B, const float *C, const double *xsq, const float *Z, int m, int N, float lam,

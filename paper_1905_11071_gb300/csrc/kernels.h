@@ -56,6 +56,15 @@ struct OistaArgs {
     int prec;            // SLISTA_PREC_FP32 (SIMT layers) or BF16 / BF16X3 (tensor-core layers)
 };
 
+struct SupportLsArgs {
+    const float *B;
+    const float *D;      // nullable: n x m dictionary, for supports larger than 64
+    int n, m, N;
+    const uint32_t *S;   // N x ceil(m/32) support words
+    const double *L;     // L_empty
+    double *LS;          // N
+};
+
 namespace simt {
 int padded_mp(int m);  // 32/64/128/256, or 0 if m > 256
 int launch_forward(const PgdArgs &a, cudaStream_t st);
@@ -64,6 +73,8 @@ size_t backward_ws_bytes(int m, int N, int T, int K);
 int launch_objective(const ObjArgs &a, cudaStream_t st);
 int launch_oista(const OistaArgs &a, void *ws, cudaStream_t st);
 size_t oista_ws_bytes(int m, int N, int T, int prec);
+int launch_support_lipschitz(const SupportLsArgs &a, void *ws, cudaStream_t st);
+size_t support_ls_ws_bytes(int m, int N);
 }  // namespace simt
 
 namespace gram {

@@ -739,7 +739,83 @@ int launch_oista_mp(const OistaArgs &a, void *wsp, cudaStream_t st)
     return SLISTA_OK;
 }
 
+// Files sample i of a standalone L_S call into the solve kernel's list of its
+// class (|S| > KMAX, SMALL_K < |S| <= KMAX, |S| <= SMALL_K), copying its
+// support words with the bits of codes >= m cleared (the solvers index B by
+// them).
+__global__ void __launch_bounds__(256) support_classify_kernel(const uint32_t *__restrict__ S, int m, OistaWs ws)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ws.N) return;
+    int k = 0;
+    for (int w = 0; w < ws.W; ++w) {
+        const int rem = m - 32 * w;
+        const uint32_t keep = rem >= 32 ? 0xffffffffu : (1u << rem) - 1u;
+        const uint32_t bits = __ldg(S + (size_t)i * ws.W + w) & keep;
+        ws.Scur[(size_t)i * ws.W + w] = bits;
+        k += __popc(bits);
+    }
+    const int cls = k > KMAX ? 0 : k > SMALL_K ? 1 : 2;
+    ws.list[(size_t)cls * ws.N + atomicAdd(ws.counter + cls, 1)] = i;
+}
+
+// Workspace of a standalone L_S call: copied supports, the solve kernel's
+// scratch (published supports, flags, class lists, counters and queue
+// positions) and D^T, each on a 256-byte boundary.
+size_t support_ls_layout(int m, int N, void *wsp, OistaWs *out)
+{
+    const size_t W = (size_t)(m + 31) / 32;
+    const size_t sizes[7] = {sizeof(uint32_t) * N * W, sizeof(uint32_t) * N * W, sizeof(int) * (size_t)N,
+                             sizeof(int) * 2 * NCLS * (size_t)N, sizeof(int) * 3 * NCLS,
+                             sizeof(float) * (size_t)m * KMAX, 0};
+    char *base = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(wsp) + 255) & ~(uintptr_t)255);
+    char *ptr[7];
+    size_t off = 0;
+    for (int s = 0; s < 7; ++s) {
+        ptr[s] = base + off;
+        off += OistaWs::a256(sizes[s]);
+    }
+    if (out) {
+        OistaWs &o = *out;
+        o = OistaWs{};
+        o.Scur = reinterpret_cast<uint32_t *>(ptr[0]);
+        o.Sprev = reinterpret_cast<uint32_t *>(ptr[1]);
+        o.valid = reinterpret_cast<int *>(ptr[2]);
+        o.list = reinterpret_cast<int *>(ptr[3]);
+        o.counter = reinterpret_cast<int *>(ptr[4]);  // 2 x NCLS counters, then NCLS queue positions
+        o.qpos = o.counter + 2 * NCLS;
+        o.Dt = reinterpret_cast<float *>(ptr[5]);
+        o.N = N;
+        o.W = (int)W;
+    }
+    return off + 256;
+}
+
 }  // namespace
+
+size_t support_ls_ws_bytes(int m, int N) { return support_ls_layout(m, N, nullptr, nullptr); }
+
+int launch_support_lipschitz(const SupportLsArgs &a, void *wsp, cudaStream_t st)
+{
+    if (a.N == 0) return SLISTA_OK;
+    OistaWs ws;
+    support_ls_layout(a.m, a.N, wsp, &ws);
+    ws.LSv = a.LS;
+    SLISTA_CUDA_TRY(cudaMemsetAsync(ws.counter, 0, sizeof(int) * 3 * NCLS, st));
+    const bool have_D = a.D != nullptr && a.n >= 1 && a.n <= KMAX;
+    if (have_D) {
+        transpose_kernel<<<ceil_div((long long)a.n * a.m, 256), 256, 0, st>>>(a.D, a.n, a.m, ws.Dt);
+        int rc = check_launch("transpose_kernel");
+        if (rc) return rc;
+    }
+    support_classify_kernel<<<ceil_div(a.N, 256), 256, 0, st>>>(a.S, a.m, ws);
+    int rc = check_launch("support_classify_kernel");
+    if (rc) return rc;
+    const size_t solve_smem = sizeof(WarpEig) * A_WARPS + sizeof(WarpEigS) * S_WARPS;
+    SLISTA_CUDA_TRY(allow_smem(oista_solve_kernel, solve_smem));
+    oista_solve_kernel<<<num_sms(), (A_WARPS + S_WARPS) * 32, solve_smem, st>>>(a.B, have_D, a.n, a.m, a.L, ws, 0);
+    return check_launch("oista_solve_kernel");
+}
 
 int launch_oista(const OistaArgs &a, void *ws, cudaStream_t st)
 {

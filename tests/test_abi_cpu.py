@@ -133,6 +133,20 @@ def test_argument_validation_without_gpu(lib):
     assert lib.lasso_objective(vp, vp, None, vp, 8, 4, 0.1, vp, None, None) == _lib.SLISTA_ERR_ARG
     assert lib.lasso_lipschitz(vp, 0, vp, None) == _lib.SLISTA_ERR_ARG
     assert lib.ista_forward(vp, vp, 8, 4, 0.1, None, 3, 0, vp, None, 0, None) == _lib.SLISTA_ERR_ARG
+    # standalone L_S: width limit, null pointers, n with D, workspace size and alignment
+    assert lib.lasso_support_lipschitz(vp, None, 0, 300, 4, vp, vp, vp, odd, 1 << 30,
+                                       None) == _lib.SLISTA_ERR_UNSUPPORTED
+    assert lib.lasso_support_lipschitz(vp, None, 0, 8, 4, None, vp, vp, odd, 1 << 30, None) == _lib.SLISTA_ERR_ARG
+    assert lib.lasso_support_lipschitz(vp, vp, 0, 8, 4, vp, vp, vp, odd, 1 << 30, None) == _lib.SLISTA_ERR_ARG
+    need = _lib.slista_workspace_bytes(_lib.FN_SUPPORT_LIPSCHITZ, 40, 1000, 0, 0)
+    assert need >= 4 * (2 * 1000 * 2 + 1000 + 6 * 1000)
+    assert lib.lasso_support_lipschitz(vp, None, 0, 40, 1000, vp, vp, vp, ctypes.c_void_p(0x1000), need - 1,
+                                       None) == _lib.SLISTA_ERR_WORKSPACE
+    assert lib.lasso_support_lipschitz(vp, None, 0, 40, 1000, vp, vp, vp, odd, need,
+                                       None) == _lib.SLISTA_ERR_WORKSPACE
+    assert _lib.slista_workspace_bytes(_lib.FN_SUPPORT_LIPSCHITZ, 300, 1000, 0, 0) == 0
+    # N = 0 needs no workspace and launches nothing
+    assert lib.lasso_support_lipschitz(vp, None, 0, 40, 0, None, None, None, None, 0, None) == _lib.SLISTA_OK
 
 
 def test_python_binding_rejects_cpu_tensors(lib):

@@ -233,6 +233,57 @@ def test_oista_parity_64x256(with_D):
     assert np.abs(host(accg) - acco).max() <= (~safe).sum()
 
 
+def _pack_supports(mask):
+    """Rows of a boolean N x m support array as N x ceil(m/32) int32 words
+    (bit j % 32 of word j / 32 set iff code j is in the support)."""
+    N, m = mask.shape
+    words = np.zeros((N, (m + 31) // 32), dtype=np.uint32)
+    for j in range(m):
+        words[:, j // 32] |= mask[:, j].astype(np.uint32) << np.uint32(j % 32)
+    return words.view(np.int32)
+
+
+@pytest.mark.parametrize("with_D", [True, False])
+def test_support_lipschitz_parity(with_D):
+    """lasso_support_lipschitz (Eq. spca) on seeded supports of every solver
+    class (|S| = 0, 1, <= 32, 33 - 64, > 64 on D_S D_S^T or from B) against
+    the oracle's Jacobi value; L_empty = L."""
+    w = synth.slista_64x256(N=8, T=1)
+    rng = np.random.default_rng(31)
+    sizes = [0, 1, 2, 3, 5, 9, 17, 31, 32, 33, 40, 57, 63, 64, 65, 80, 100, 140, 256]
+    reps = [4 if k <= 64 else 2 for k in sizes]
+    mask = np.zeros((sum(reps), w.m), dtype=bool)
+    r = 0
+    for k, c in zip(sizes, reps):
+        for _ in range(c):
+            mask[r, rng.choice(w.m, size=k, replace=False)] = True
+            r += 1
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    LSg = host(A.support_lipschitz(g.B, dev(_pack_supports(mask)), g.L, D=dev(w.D) if with_D else None))
+    Lo = oracle.lipschitz(w.D)
+    LSo = np.array([oracle.support_lipschitz(w.D, mask[i], Lo) for i in range(len(mask))])
+    np.testing.assert_allclose(LSg, LSo, rtol=EIG_TOL)
+    assert LSg[0] == host(g.L)[0]  # empty support: L itself
+
+
+def test_support_lipschitz_ignores_bits_past_m():
+    """Bits of codes >= m in the last support word are not part of S."""
+    w = synth.paper_binf(10, 50, N=8, lam=0.5, T=1, seed=2)
+    rng = np.random.default_rng(32)
+    mask = rng.random((64, 50)) < 0.3
+    words = _pack_supports(mask).view(np.uint32).copy()
+    dirty = words.copy()
+    dirty[:, 1] |= np.uint32(0xFFFC0000)  # codes 50 .. 63
+    A = api()
+    g = A.gram(dev(w.D), dev(w.X))
+    clean = host(A.support_lipschitz(g.B, dev(words.view(np.int32)), g.L))
+    noisy = host(A.support_lipschitz(g.B, dev(dirty.view(np.int32)), g.L))
+    assert np.array_equal(clean, noisy)
+    Lo = oracle.lipschitz(w.D)
+    np.testing.assert_allclose(clean, [oracle.support_lipschitz(w.D, mask[i], Lo) for i in range(64)], rtol=EIG_TOL)
+
+
 def test_objective_and_gap_parity():
     """Objective/gap kernel on codes drawn by the test (not by the GPU)."""
     w = synth.slista_64x256(N=500, T=1)

@@ -9,7 +9,9 @@ oracle:
 * Learned steps (Section 4, Appendix E): Step-LISTA trained on 10 x 20,
   lam = 0.2, N = 1000 (T = 20) lowers the unsupervised loss monotonically and
   learns steps larger than ISTA's 1/L in the later layers (the supports of
-  late layers are small, and 1/L_S > 1/L on them).
+  late layers are small, and 1/L_S > 1/L on them).  As in Fig. 4, the
+  learned alpha_t follow the distribution of 1/L_S(x, t) over the training
+  samples, S(x, t) = supp z^(t)(x), with L_S from lasso_support_lipschitz.
 """
 import numpy as np
 import pytest
@@ -73,3 +75,35 @@ def test_learned_steps_10x20():
     Zi = oracle.ista(w.D, w.X, w.lam, oracle.lipschitz(w.D), T)
     F_ista = oracle.objective(w.D, w.X, Zi, w.lam, with_gap=False).sum()
     assert abs(hist[0] - F_ista) <= 1e-5 * abs(F_ista)
+
+
+def _rank(v):
+    r = np.empty(len(v))
+    r[np.argsort(v, kind="stable")] = np.arange(len(v))
+    return r
+
+
+def test_learned_steps_follow_support_steps_10x20():
+    """Fig. 4: the steps learned on 10 x 20 (lam = 0.2, T = 20, N = 1000) grow
+    with the per-layer distribution of 1/L_S(x, t): their rank correlation
+    with its median is high, and in the second half of the network every
+    alpha_t lies between that median and its maximum."""
+    from paper_1905_11071_gb300 import api as A
+    T = 20
+    w = synth.paper_binf(10, 20, N=1000, lam=0.2, T=T, seed=0)
+    g = A.gram(dev(w.D), dev(w.X))
+    L = float(host(g.L)[0])
+    alpha0 = torch.full((T,), 1.0 / L, dtype=torch.float32, device="cuda")
+    alpha, _ = A.train_step_sizes(alpha0, g, w.lam, steps=60)
+    _, st = A.slista(g.B, g.C, w.lam, alpha, keep_for_backward=True)
+    masks = st.masks.view(T, w.N, -1)
+    med, top = [1.0 / L], [1.0 / L]  # layer 0 acts on z^(0) = 0: S empty, L_empty = L
+    for t in range(1, T):
+        inv = 1.0 / host(A.support_lipschitz(g.B, masks[t - 1].contiguous(), g.L))
+        med.append(float(np.median(inv)))
+        top.append(float(inv.max()))
+    a = host(alpha).astype(np.float64)
+    med, top = np.array(med), np.array(top)
+    assert np.corrcoef(_rank(a), _rank(med))[0, 1] >= 0.8
+    h = T // 2
+    assert (med[h:] <= a[h:]).all() and (a[h:] <= top[h:]).all()

@@ -368,6 +368,44 @@ def test_oista_orthogonal_support_one_step():
         assert np.abs(Zi[T0 + 1, 0] - zstar).max() > 0.1
 
 
+def test_learned_steps_follow_support_steps_10x20():
+    """Fig. 4 / Appendix E on the oracle: Step-LISTA (T = 20) trained by
+    sub-gradient descent with backtracking on 10 x 20, lam = 0.2, N = 1000
+    lowers the loss, and its steps alpha_t follow the distribution of
+    1/L_S(x, t), S(x, t) = supp z^(t)(x): high rank correlation with its
+    median, and median <= alpha_t <= maximum in the second half."""
+    T = 20
+    w = synth.paper_binf(10, 20, N=1000, lam=0.2, T=T, seed=0)
+    D = w.D.astype(np.float64)
+    L = oracle.lipschitz(D)
+    alpha = np.full(T, 1.0 / L)
+    grad, loss = oracle.slista_grad(D, w.X, w.lam, alpha)
+    loss0 = loss
+    lr = 0.1 * alpha.max() / np.abs(grad).max()
+    for _ in range(60):
+        for _h in range(20):
+            trial = np.maximum(alpha - lr * grad, 1e-6)
+            gt, lt = oracle.slista_grad(D, w.X, w.lam, trial)
+            if lt <= loss:
+                alpha, loss, grad = trial, lt, gt
+                lr *= 1.2
+                break
+            lr *= 0.5
+    assert loss < loss0
+    Zall = oracle.pgd(D, w.X, w.lam, alpha, keep_all=True)
+    med, top = [], []
+    for t in range(T):
+        inv = np.array([1.0 / oracle.support_lipschitz(D, Zall[t, i] != 0, L) for i in range(w.N)])
+        med.append(np.median(inv))
+        top.append(inv.max())
+    med, top = np.array(med), np.array(top)
+    rank = lambda v: np.argsort(np.argsort(v, kind="stable"), kind="stable")
+    assert np.corrcoef(rank(alpha), rank(med))[0, 1] >= 0.8
+    h = T // 2
+    assert (med[h:] <= alpha[h:]).all() and (alpha[h:] <= top[h:]).all()
+    assert alpha[h:].mean() > 2.0 / L
+
+
 def _st_by_hand(v, theta):
     """Soft-thresholding written out for the test (Section 1)."""
     return np.sign(v) * np.maximum(np.abs(v) - theta, 0.0)
