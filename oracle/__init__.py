@@ -63,6 +63,7 @@ def _load():
             lib.orc_support_lipschitz.argtypes = [dp, i, i, up, d]
             lib.orc_support_lipschitz.restype = d
             lib.orc_pgd.argtypes = [dp, i, i, dp, i, d, dp, i, dp, dp]
+            lib.orc_lista.argtypes = [dp, i, i, dp, i, d, dp, dp, dp, i, dp]
             lib.orc_oista.argtypes = [dp, i, i, dp, i, d, d, i, dp, dp, ip, up, dp, dp]
             lib.orc_slista_grad.argtypes = [dp, i, i, dp, i, d, dp, i, dp, dp]
             lib.orc_lasso_bruteforce.argtypes = [dp, i, i, dp, d, dp]
@@ -157,6 +158,20 @@ def pgd(D, X, lam, alpha, keep_all: bool = False):
     _load().orc_pgd(_p(D), n, m, _p(X), N, float(lam), _p(alpha), T, _p(Z),
                     _p(Zall) if keep_all else None)
     return Zall if keep_all else Z
+
+
+def lista(D, X, lam, W, alpha, beta):
+    """T layers of coupled LISTA (Eq. lista_layer) from z^(0) = 0:
+    z <- ST(z - alpha_t W_t^T (D z - x), beta_t lam).  W: T x n x m (one
+    matrix per layer), alpha, beta: T positive scalars.  Returns z^(T) (N x m)."""
+    D = _f64(D); X = _f64(X); W = _f64(W); alpha = _f64(np.atleast_1d(alpha)); beta = _f64(np.atleast_1d(beta))
+    n, m = D.shape
+    N = X.shape[0]
+    T = alpha.shape[0]
+    assert W.shape == (T, n, m) and beta.shape == (T,)
+    Z = np.empty((N, m))
+    _load().orc_lista(_p(D), n, m, _p(X), N, float(lam), _p(W), _p(alpha), _p(beta), T, _p(Z))
+    return Z
 
 
 def ista(D, X, lam, L, T):

@@ -299,6 +299,30 @@ void orc_pgd(const double *D, int n, int m, const double *X, int N, double lam,
     free(work);
 }
 
+/* T layers of coupled LISTA (Eq. lista_layer, Section 4) from z^(0) = 0:
+ *   z^(t+1) = ST(z^(t) - alpha_t W_t^T (D z^(t) - x), beta_t lam),
+ * W_t = W + t*n*m (n x m, row-major like D), alpha_t, beta_t > 0.  Z: N x m. */
+void orc_lista(const double *D, int n, int m, const double *X, int N, double lam,
+               const double *W, const double *alpha, const double *beta, int T, double *Z)
+{
+    double *z = (double *)malloc(sizeof(double) * (size_t)m);
+    double *v = (double *)malloc(sizeof(double) * (size_t)m);
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int s = 0; s < N; ++s) {
+        const double *x = X + (size_t)s * n;
+        for (int j = 0; j < m; ++j) z[j] = 0.0;
+        for (int t = 0; t < T; ++t) {
+            residual_Dz_minus_x(D, n, m, z, x, r);
+            Dt_times(W + (size_t)t * n * m, n, m, r, v);
+            for (int j = 0; j < m; ++j) z[j] = orc_st(z[j] - alpha[t] * v[j], beta[t] * lam);
+        }
+        memcpy(Z + (size_t)s * m, z, sizeof(double) * (size_t)m);
+    }
+    free(z);
+    free(v);
+    free(r);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Oracle-ISTA (Algorithm 1, Section 3).                                     */
 /* ------------------------------------------------------------------------ */

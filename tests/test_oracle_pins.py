@@ -252,6 +252,40 @@ def test_pgd_step_sequence_is_layerwise():
         np.testing.assert_allclose(Zall[t + 1], want, atol=1e-13)
 
 
+def test_lista_reduces_to_ista_and_step_lista():
+    """Coupled LISTA (Eq. lista_layer): W = D with alpha = beta = 1/L is ISTA
+    (Section 4); a layer (W, alpha, beta) is the Step-LISTA layer of step beta
+    when (alpha / beta) W = D (Section 4, after Eq. steprec), and not in
+    general otherwise; from z = 0 one layer returns 0 iff
+    |alpha W^T x|_inf <= beta lam (ST's closed form)."""
+    w = synth.ista_10x20(N=30, T=12)
+    D = w.D.astype(np.float64)
+    L = oracle.lipschitz(D)
+    T = w.T
+    Ws = np.repeat(D[None], T, axis=0)
+    ista = oracle.ista(D, w.X, w.lam, L, T)
+    np.testing.assert_allclose(oracle.lista(D, w.X, w.lam, Ws, np.full(T, 1 / L), np.full(T, 1 / L)), ista,
+                               rtol=0, atol=1e-14)
+    rng = np.random.default_rng(41)
+    alpha = rng.uniform(0.3, 2.0, T) / L
+    beta = rng.uniform(0.3, 1.5, T) / L
+    Wc = Ws * (beta / alpha)[:, None, None]
+    want = oracle.pgd(D, w.X, w.lam, beta)
+    assert np.abs(want).max() > 0.1
+    np.testing.assert_allclose(oracle.lista(D, w.X, w.lam, Wc, alpha, beta), want, rtol=0, atol=1e-12)
+    Wp = Wc + 0.05 * rng.standard_normal(Wc.shape)
+    assert np.abs(oracle.lista(D, w.X, w.lam, Wp, alpha, beta) - want).max() > 1e-4
+    # one layer from 0: u = alpha W^T x
+    W1 = rng.standard_normal((1, D.shape[0], D.shape[1]))
+    a1, b1 = np.array([0.7]), np.array([0.4])
+    top = np.abs(a1[0] * (w.X.astype(np.float64) @ W1[0])).max(axis=1)
+    lam0 = top.max() / b1[0] * 1.0001
+    assert not oracle.lista(D, w.X, lam0, W1, a1, b1).any()
+    i = int(np.argmax(top))
+    z = oracle.lista(D, w.X[i:i + 1], top[i] / b1[0] * 0.9999, W1, a1, b1)
+    assert np.count_nonzero(z) == 1
+
+
 # --------------------------------------------------------------------------
 # Objective and duality gap (Eq. lasso; gap: standard Lasso dual)
 # --------------------------------------------------------------------------
