@@ -155,3 +155,12 @@ def test_python_binding_rejects_cpu_tensors(lib):
     X = torch.zeros(3, 4)
     with pytest.raises(ValueError):
         _lib.lasso_gram(D, X, torch.zeros(8, 8), torch.zeros(3, 8), torch.zeros(3, dtype=torch.float64))
+
+
+def test_support_lipschitz_binding_rejects_host_tensors(lib):
+    """The binding of lasso_support_lipschitz refuses host tensors before any
+    call into the library."""
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError, match="CUDA"):
+        _lib.lasso_support_lipschitz(torch.zeros(40, 40), torch.zeros(5, 2, dtype=torch.int32),
+                                     torch.ones(1, dtype=torch.float64), torch.zeros(5, dtype=torch.float64))
