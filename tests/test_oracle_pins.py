@@ -188,6 +188,25 @@ def test_bruteforce_matches_ista_limit_and_gap(seed):
     assert (Fs[1:] - F[0] <= L * (zstar @ zstar) / (2 * t) + 1e-14).all()
 
 
+def test_ista_linear_rate_strongly_convex():
+    """The classical linear rate quoted with Prop. 3.2: with m < n, D^T D has
+    smallest eigenvalue mu > 0 and ISTA satisfies
+    F(z^t) - F* <= (1 - mu/L)^t (F(0) - F*)."""
+    rng = np.random.default_rng(51)
+    D = synth.gaussian_dictionary(30, 12, rng).astype(np.float64)
+    X = rng.standard_normal((5, 30))
+    lam = 0.2 * np.abs(X @ D).max()
+    L = oracle.lipschitz(D)
+    mu = np.linalg.eigvalsh(D.T @ D).min()
+    assert mu > 0.05
+    T = 200
+    Zall = oracle.pgd(D, X, lam, np.full(T, 1.0 / L), keep_all=True)
+    Fstar = oracle.objective(D, X, oracle.ista(D, X, lam, L, 5000), lam, with_gap=False)
+    F = np.stack([oracle.objective(D, X, Zall[t], lam, with_gap=False) for t in range(T + 1)])
+    t = np.arange(T + 1)[:, None]
+    assert (F - Fstar <= (1 - mu / L) ** t * (F[0] - Fstar) + 1e-13).all()
+
+
 def test_stability_closed_form():
     """Lemma 4.2: for unit columns, c = max_{l != j} |D_l^T D_j| and
     x = D_j + eps with eps orthogonal to D_j, ||eps|| < lam (1 - c), the Lasso
