@@ -1,13 +1,18 @@
 """Throughput benchmark of the batched unfolded-ISTA hot path on GB300.
 
-One step = one pass of the whole hot path over one batch of N samples of the
-64 x 256 sparse-model workload (T = 40):
+One step = one Step-LISTA forward + backward pass over a batch of N samples of
+the 64 x 256 sparse-model workload (T = 40), the metric's "T-layer SLISTA
+fwd(+bwd)":
     lasso_gram (B = D^T D, C = X D, ||x||^2, L)
-    -> slista_forward (step sizes alpha, support masks, sqrt(T) checkpoints)
-    -> lasso_objective (F and duality gap, FP64 reductions)
-    -> slista_backward (hand-written adjoint, d loss / d alpha)
-    -> oista_forward (Oracle-ISTA, Algorithm 1).
-Metric: samples per second over the whole job (all ranks).
+    -> slista_forward_traj (split-BF16 layers on the tensor cores; support
+       masks and the adjoint's inputs; --backward ckpt: checkpoints instead)
+    -> lasso_objective (F and duality gap, FP64 reductions: the loss)
+    -> slista_backward_traj (hand-written adjoint, d loss / d alpha).
+value = samples per second of that step over the whole job (all ranks).
+The same run times, as separate legs reported beside it: Oracle-ISTA
+(Algorithm 1) on the same batch; the plain FP32 ISTA kernel on the CUDA cores
+(same T); Step-LISTA with trained steps against FP32 ISTA at equal final
+objective gap; and the step at larger batches (N = 1e5, 1e6).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank processes its own N samples (weak scaling, no
@@ -54,7 +59,11 @@ def parse():
                         "tensor cores, m, T <= 256) or ckpt (checkpoints every ~sqrt(T) layers, recompute)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-legs", action="store_true", help="skip the Oracle-ISTA / FP32 ISTA / equal-gap legs")
+    p.add_argument("--sweep", default="100000,1000000", help="batch sizes of the sweep lines ('' = none)")
+    p.add_argument("--train-steps", type=int, default=30, help="step-size training steps of the equal-gap leg")
     p.add_argument("--cpu-samples", type=int, default=0, help="oracle sample size (0 = auto)")
+    p.add_argument("--cpu-cores", type=int, default=0, help="oracle worker processes (0 = every core)")
     return p.parse_args()
 
 
@@ -137,14 +146,13 @@ def backward_mode(w, args) -> str:
 
 def arm_config(w, args, world: int) -> dict:
     """The workload description shared by both arms of the benchmark."""
-    import math as _m
+    bm = backward_mode(w, args)
     return {"workload": "slista_64x256", "n": w.n, "m": w.m, "N_per_gpu": w.N, "T": w.T, "lam": w.lam,
-            "backward": backward_mode(w, args),
-            "ckpt_every": (max(1, int(_m.ceil(_m.sqrt(max(w.T, 1))))) if backward_mode(w, args) == "ckpt"
-                           else None),
+            "backward": bm,
+            "ckpt_every": (max(1, int(math.ceil(math.sqrt(max(w.T, 1))))) if bm == "ckpt" else None),
             "prec": args.prec, "oista_prec": args.oista_prec,
-            "step": ("gram+L -> slista fwd(masks,%s) -> objective+gap -> slista bwd -> oista fwd" %
-                     ("trajectory" if backward_mode(w, args) == "traj" else "ckpt")),
+            "step": ("gram+L -> slista fwd(masks,%s) -> objective+gap -> slista bwd" %
+                     ("trajectory" if bm == "traj" else "ckpt")),
             "l2": "flushed between timed steps (write of 2x L2 size, untimed)",
             "parallelism": "dp%d" % world if world > 1 else "single"}
 
@@ -192,6 +200,27 @@ def job_throughput(n_per_rank: int, world: int, ms: float) -> float:
     return n_per_rank * world / (ms / 1e3)
 
 
+FP32_PEAK_TFLOPS = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP32_PEAK_SRC = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+
+
+def layer_peak(prec: str, pk: dict, pk_kind: str):
+    """(bound, peak TFLOP/s, source) of a layer kernel at this precision: the
+    measured dense BF16 rate (burst: kernels timed one launch at a time) divided
+    by the products a contraction issues (3 for the split hi*hi + hi*lo +
+    lo*hi), or the FP32 ALU peak on the CUDA cores."""
+    if prec in ("bf16", "bf16x3"):
+        nprod = 3 if prec == "bf16x3" else 1
+        return "tensor", pk["bf16_tflops"] / nprod, "%s bf16_tflops (burst) / %d products" % (pk_kind, nprod)
+    return "alu", FP32_PEAK_TFLOPS, FP32_PEAK_SRC
+
+
+def roofline_entry(bound, amount, unit, peak, src, ms):
+    ach = amount / (ms / 1e3) if ms > 0 else 0.0
+    return {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak if peak else None,
+            "ms": ms, "peak_source": src}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -208,13 +237,14 @@ def run_ours(args, rank, world, local_rank):
     lam = w.lam
     K = api.default_ckpt_every(T)
     stream = torch.cuda.current_stream()
+    pk, pk_kind = peaks()
 
     # step sizes: alpha_t = 1/L (the initialisation of a Step-LISTA network)
     g0 = api.gram(D, X)
     alpha = (1.0 / g0.L.double()).float().expand(T).contiguous()
     torch.cuda.synchronize()
 
-    parts = ["gram", "slista_fwd", "objective", "slista_bwd", "oista_fwd"]
+    parts = ["gram", "slista_fwd", "objective", "slista_bwd"]
     tc = args.prec in ("bf16", "bf16x3")
     traj = backward_mode(w, args) == "traj"
     nseg = -(-T // K)
@@ -224,33 +254,45 @@ def run_ours(args, rank, world, local_rank):
         "objective": 1,
         # (B split) + one reverse sweep + reduce, or + recompute/adjoint per segment + reduce
         "slista_bwd": 3 if traj else ((1 + 2 * nseg + 1) if tc else 2),
-        "oista_fwd": 1 + 1 + 2 * T + (1 if args.oista_prec != "fp32" else 0),  # transpose D, init, (B split), solve + step per layer
     }
 
-    def step(evs=None):
+    def step(Dd, Xd, ad, evs=None):
         if evs is not None:
             evs[0].record(stream)
-        g = api.gram(D, X)
+        g = api.gram(Dd, Xd)
         if evs is not None:
             evs[1].record(stream)
-        Z, st = api.slista(g.B, g.C, lam, alpha, prec=args.prec, keep_for_backward=True, ckpt_every=K,
+        Z, st = api.slista(g.B, g.C, lam, ad, prec=args.prec, keep_for_backward=True, ckpt_every=K,
                            trajectory=traj)
         if evs is not None:
             evs[2].record(stream)
         F, gap = api.objective(g.B, g.C, g.xsq, Z, lam)
         if evs is not None:
             evs[3].record(stream)
-        da = api.slista_grad(g.B, g.C, lam, alpha, st, prec=args.prec)
+        da = api.slista_grad(g.B, g.C, lam, ad, st, prec=args.prec)
         if evs is not None:
             evs[4].record(stream)
-        Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=D, prec=args.oista_prec)
-        if evs is not None:
-            evs[5].record(stream)
-        return Z, F, gap, da, Zo
+        return g, Z, F, gap, da
 
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, nev, steps, warmup):
+        """Average per-segment ms of fn(evs) over `steps` calls (L2 flushed
+        before each, untimed), after `warmup` untimed calls."""
+        for _ in range(max(warmup, 0)):
+            fn(None)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nev)] for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(float(k))
+            fn(evs[k])
+        torch.cuda.synchronize()
+        seg = [sum(e[i].elapsed_time(e[i + 1]) for e in evs) / steps for i in range(nev - 1)]
+        tot = sum(e[0].elapsed_time(e[nev - 1]) for e in evs) / steps
+        return seg, tot
+
     for _ in range(max(args.warmup, 0)):
-        step()
+        step(D, X, alpha)
     torch.cuda.synchronize()
     _lib.slista_device_status()
 
@@ -258,14 +300,14 @@ def run_ours(args, rank, world, local_rank):
                            int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank]))
     sampler.start()
     time.sleep(0.3)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))  # evict inputs and outputs from L2 between timed steps (untimed)
-        step(evs[k])
+        step(D, X, alpha, evs[k])
     torch.cuda.synchronize()
     wall1 = time.perf_counter()
     if world > 1:
@@ -273,14 +315,8 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop()
     _lib.slista_device_status()
 
-    per_part = {p: 0.0 for p in parts}
-    total = 0.0
-    for e in evs:
-        for i, p in enumerate(parts):
-            per_part[p] += e[i].elapsed_time(e[i + 1])
-        total += e[0].elapsed_time(e[5])
-    ms_step = total / args.steps
-    per_part = {p: v / args.steps for p, v in per_part.items()}
+    per_part = {p: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps for i, p in enumerate(parts)}
+    ms_step = sum(e[0].elapsed_time(e[4]) for e in evs) / args.steps
     ms_step = max_over_ranks(ms_step, world, dev)
     value = job_throughput(N, world, ms_step)
 
@@ -291,7 +327,6 @@ def run_ours(args, rank, world, local_rank):
         Xh = torch.from_numpy(w.X).pin_memory()
         Ah = alpha.cpu().pin_memory()
         Zh = torch.empty((N, m), dtype=torch.float32).pin_memory()
-        Zoh = torch.empty((N, m), dtype=torch.float32).pin_memory()
         Fh = torch.empty((N,), dtype=torch.float64).pin_memory()
         Gh = torch.empty((N,), dtype=torch.float64).pin_memory()
         dah = torch.empty((T,), dtype=torch.float32).pin_memory()
@@ -300,17 +335,11 @@ def run_ours(args, rank, world, local_rank):
             Dd = Dh.to(dev, non_blocking=True)
             Xd = Xh.to(dev, non_blocking=True)
             ad = Ah.to(dev, non_blocking=True)
-            g = api.gram(Dd, Xd)
-            Z, st = api.slista(g.B, g.C, lam, ad, prec=args.prec, keep_for_backward=True, ckpt_every=K,
-                               trajectory=traj)
-            F, gap = api.objective(g.B, g.C, g.xsq, Z, lam)
-            da = api.slista_grad(g.B, g.C, lam, ad, st, prec=args.prec)
-            Zo, LS, acc = api.oista(g.B, g.C, lam, g.L, T, D=Dd, prec=args.oista_prec)
+            g, Z, F, gap, da = step(Dd, Xd, ad)
             Zh.copy_(Z, non_blocking=True)
             Fh.copy_(F, non_blocking=True)
             Gh.copy_(gap, non_blocking=True)
             dah.copy_(da, non_blocking=True)
-            Zoh.copy_(Zo, non_blocking=True)
 
         for _ in range(2):
             e2e_step()
@@ -328,42 +357,19 @@ def run_ours(args, rank, world, local_rank):
         e_ms = tot / args.steps
         e_ms = max_over_ranks(e_ms, world, dev)
         h2d = Dh.numel() * 4 + Xh.numel() * 4 + Ah.numel() * 4
-        d2h = Zh.numel() * 4 + Fh.numel() * 8 + Gh.numel() * 8 + dah.numel() * 4 + Zoh.numel() * 4
+        d2h = Zh.numel() * 4 + Fh.numel() * 8 + Gh.numel() * 8 + dah.numel() * 4
         e2e = {"value": job_throughput(N, world, e_ms), "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # ---- roofline of the dominant kernel (per-launch figures)
-    pk, pk_kind = peaks()
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
+    # ---- roofline of each part of the step (per-launch figures)
     mm = float(m)
-    # Layer kernels on the tensor cores: the peak of their own arithmetic is
-    # the measured dense BF16 rate (burst: the kernels are timed one launch at
-    # a time), divided by 3 for the split product hi*hi + hi*lo + lo*hi.
-    if tc:
-        nprod = 3 if args.prec == "bf16x3" else 1
-        layer_peak = pk["bf16_tflops"] / nprod
-        layer_bound, layer_src = "tensor", "%s bf16_tflops (burst) / %d products" % (pk_kind, nprod)
-    else:
-        layer_peak = fp32_peak
-        layer_bound, layer_src = "alu", "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-    oista_work = 2 * mm * mm * (T - 1) * N / 1e12
-    if args.oista_prec in ("bf16", "bf16x3"):
-        onprod = 3 if args.oista_prec == "bf16x3" else 1
-        oista_algo = ("tensor", oista_work, "TFLOP/s", pk["bf16_tflops"] / onprod,
-                      "%s bf16_tflops (burst) / %d products" % (pk_kind, onprod))
-    else:
-        oista_algo = ("alu", oista_work, "TFLOP/s", fp32_peak, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz")
+    lb, lpk, lsrc = layer_peak(args.prec, pk, pk_kind)
     algo = {
         # useful B z products: 2 m^2 per sample per layer (T - 1 contractions; T with the
         # trajectory, whose forward also forms g^(T))
-        "slista_fwd": (layer_bound, 2 * mm * mm * (T if traj else T - 1) * N / 1e12, "TFLOP/s", layer_peak,
-                       layer_src),
+        "slista_fwd": (lb, 2 * mm * mm * (T if traj else T - 1) * N / 1e12, "TFLOP/s", lpk, lsrc),
         # adjoint: B h (T - 1), plus the recompute (K - 1 contractions per segment, + 1 for g^(T))
-        "slista_bwd": (layer_bound, 2 * mm * mm * ((T - 1) if traj else (2 * T - nseg)) * N / 1e12, "TFLOP/s",
-                       layer_peak, layer_src),
-        # Oracle-ISTA: the layer products only (the eigen-solves, which take most of its
-        # time on the CUDA cores, are not counted), on the tensor cores or the CUDA cores
-        "oista_fwd": oista_algo,
+        "slista_bwd": (lb, 2 * mm * mm * ((T - 1) if traj else (2 * T - nseg)) * N / 1e12, "TFLOP/s", lpk, lsrc),
         # Gram: read D, X, write B, C, xsq
         "gram": ("hbm", (4.0 * (n * m + N * n + N * m + m * m) + 8.0 * N) / 1e9, "GB/s", pk["hbm_gbs"], pk_kind),
         # objective: read Z, C, xsq, B, write F, gap
@@ -371,12 +377,8 @@ def run_ours(args, rank, world, local_rank):
     }
     rooflines = {}
     for p in parts:
-        bound, amount, unit, peak, src = algo[p]
-        secs = per_part[p] / 1e3
-        ach = amount / secs if secs > 0 else 0.0
-        rooflines[p] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                        "frac": ach / peak if peak else None, "ms": per_part[p],
-                        "share": per_part[p] / sum(per_part.values()), "peak_source": src}
+        rooflines[p] = roofline_entry(*algo[p], per_part[p])
+        rooflines[p]["share"] = per_part[p] / sum(per_part.values())
     dom = max(parts, key=lambda p: per_part[p])
     r = rooflines[dom]
     roofline = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
@@ -395,55 +397,254 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roofline, "parts": rooflines,
         "wall_s_timed_region": wall1 - wall0,
     }
+
+    if not args.no_legs and rank == 0:
+        out["legs"] = run_legs(args, w, D, X, alpha, timed, pk, pk_kind)
+    if args.sweep and rank == 0:
+        out["sweep"] = run_sweep(args, timed, step, pk, pk_kind)
     return out, w
+
+
+def run_legs(args, w, D, X, alpha, timed, pk, pk_kind):
+    """Oracle-ISTA and the plain FP32 ISTA kernel on the step's batch, and
+    Step-LISTA (trained steps, split BF16) against FP32 ISTA at equal final
+    objective gap.  Each timed leg: CUDA events around the call, L2 flushed
+    before each, `steps` calls after `warmup`."""
+    import torch
+    from paper_1905_11071_gb300 import api
+    N, T, m = w.N, w.T, w.m
+    mm = float(m)
+    lam = w.lam
+    g = api.gram(D, X)
+    legs = {}
+
+    # Oracle-ISTA (Algorithm 1): eigen-solves on the CUDA cores, layer products at oista_prec
+    def oista_call(evs):
+        if evs is not None:
+            evs[0].record()
+        api.oista(g.B, g.C, lam, g.L, T, D=D, prec=args.oista_prec)
+        if evs is not None:
+            evs[1].record()
+    _, ms = timed(oista_call, 2, args.steps, 2)
+    ob, opk, osrc = layer_peak(args.oista_prec, pk, pk_kind)
+    e = roofline_entry(ob, 2 * mm * mm * (T - 1) * N / 1e12, "TFLOP/s", opk, osrc, ms)
+    e.update({"samples_per_s": N / (ms / 1e3), "note": "layer products only (2 m^2 per sample per layer); "
+              "the L_S eigen-solves on the CUDA cores are not counted as work",
+              "launches": 2 + 2 * T + (1 if args.oista_prec != "fp32" else 0)})
+    legs["oista_fwd"] = e
+
+    # plain ISTA on the CUDA cores (FP32 SIMT), same T: the FP32 comparison kernel
+    def ista_call(evs, T_=T):
+        if evs is not None:
+            evs[0].record()
+        api.ista(g.B, g.C, lam, g.L, T_, prec="fp32")
+        if evs is not None:
+            evs[1].record()
+    _, ms = timed(ista_call, 2, args.steps, 2)
+    e = roofline_entry("alu", 2 * mm * mm * (T - 1) * N / 1e12, "TFLOP/s", FP32_PEAK_TFLOPS, FP32_PEAK_SRC, ms)
+    e["samples_per_s"] = N / (ms / 1e3)
+    legs["fp32_ista"] = e
+
+    # the same forward on the tensor cores (split BF16), for the ratio at equal T
+    def tc_fwd(evs, a_=alpha):
+        if evs is not None:
+            evs[0].record()
+        api.slista(g.B, g.C, lam, a_, prec=args.prec)
+        if evs is not None:
+            evs[1].record()
+    _, ms_tc = timed(tc_fwd, 2, args.steps, 2)
+    legs["slista_fwd_only"] = {"ms": ms_tc, "samples_per_s": N / (ms_tc / 1e3),
+                               "speedup_vs_fp32_ista_same_T": legs["fp32_ista"]["ms"] / ms_tc}
+
+    # ---- equal final objective gap: trained Step-LISTA (T layers) vs FP32 ISTA (T_ista layers)
+    try:
+        legs["equal_gap"] = equal_gap_leg(args, w, g, alpha, timed)
+    except Exception as ex:  # reported, never silently dropped
+        legs["equal_gap"] = {"error": repr(ex)}
+    return legs
+
+
+def equal_gap_leg(args, w, g, alpha, timed):
+    """Trains the T step sizes (Appendix E's backtracking descent on the
+    unsupervised loss, split BF16 forward and adjoint) on the batch, then
+    finds the fewest FP32 ISTA layers whose mean objective gap F - F* is no
+    larger than trained Step-LISTA's, F* from 2000 FP32 ISTA layers; both
+    forwards are then timed."""
+    import torch
+    from paper_1905_11071_gb300 import api
+    lam, T, N = w.lam, w.T, w.N
+    t0 = time.perf_counter()
+    a_tr, hist = api.train_step_sizes(alpha, g, lam, steps=args.train_steps, prec=args.prec)
+    train_s = time.perf_counter() - t0
+    T_ref = 2000
+    Fstar = api.objective(g.B, g.C, g.xsq, api.ista(g.B, g.C, lam, g.L, T_ref, prec="fp32"), lam,
+                          with_gap=False)
+
+    def mean_gap(Z):
+        F = api.objective(g.B, g.C, g.xsq, Z, lam, with_gap=False)
+        return float((F - Fstar).mean())
+
+    gap_s = mean_gap(api.slista(g.B, g.C, lam, a_tr, prec=args.prec))
+    gap_fp32_slista = mean_gap(api.slista(g.B, g.C, lam, a_tr, prec="fp32"))
+
+    def ista_gap(Ti):
+        return mean_gap(api.ista(g.B, g.C, lam, g.L, Ti, prec="fp32"))
+
+    lo, hi = T, T
+    while ista_gap(hi) > gap_s and hi < T_ref:
+        lo, hi = hi, min(2 * hi, T_ref)
+    while lo < hi:  # smallest T_ista with gap <= gap_s
+        mid = (lo + hi) // 2
+        if ista_gap(mid) <= gap_s:
+            hi = mid
+        else:
+            lo = mid + 1
+    T_ista = hi
+
+    def s_call(evs):
+        if evs is not None:
+            evs[0].record()
+        api.slista(g.B, g.C, lam, a_tr, prec=args.prec)
+        if evs is not None:
+            evs[1].record()
+
+    def i_call(evs):
+        if evs is not None:
+            evs[0].record()
+        api.ista(g.B, g.C, lam, g.L, T_ista, prec="fp32")
+        if evs is not None:
+            evs[1].record()
+    _, ms_s = timed(s_call, 2, args.steps, 2)
+    _, ms_i = timed(i_call, 2, args.steps, 2)
+    return {"gap_mean": gap_s, "gap_mean_fp32_forward": gap_fp32_slista, "F_star_layers": T_ref,
+            "T_slista": T, "T_ista_fp32": T_ista, "ista_gap_at_T_ista": ista_gap(T_ista),
+            "slista_ms": ms_s, "slista_samples_per_s": N / (ms_s / 1e3),
+            "ista_fp32_ms": ms_i, "ista_fp32_samples_per_s": N / (ms_i / 1e3),
+            "speedup": ms_i / ms_s, "train_steps": len(hist) - 1, "train_s": train_s,
+            "loss_first_last": [hist[0], hist[-1]],
+            "note": "steps trained on this batch; F* = F after %d FP32 ISTA layers" % T_ref}
+
+
+def run_sweep(args, timed, step, pk, pk_kind):
+    """The step (Gram, forward, objective, backward) at larger batches."""
+    import torch
+    from paper_1905_11071_gb300 import api, synth
+    out = []
+    for N in [int(x) for x in str(args.sweep).split(",") if x.strip()]:
+        w = synth.slista_64x256(seed=0, N=N, T=args.T)
+        D = torch.from_numpy(w.D).cuda()
+        X = torch.from_numpy(w.X).cuda()
+        g0 = api.gram(D, X)
+        alpha = (1.0 / g0.L.double()).float().expand(w.T).contiguous()
+        del g0
+
+        def fn(evs):
+            if evs is None:
+                step(D, X, alpha)
+                return
+            step(D, X, alpha, evs)
+        steps = max(3, min(args.steps, int(2e6 // N) + 3))
+        seg, tot = timed(fn, 5, steps, 2)
+        mm, T = float(w.m), w.T
+        traj = backward_mode(w, args) == "traj"
+        lb, lpk, lsrc = layer_peak(args.prec, pk, pk_kind)
+        fwd = roofline_entry(lb, 2 * mm * mm * (T if traj else T - 1) * N / 1e12, "TFLOP/s", lpk, lsrc, seg[1])
+        bwd = roofline_entry(lb, 2 * mm * mm * (T - 1) * N / 1e12, "TFLOP/s", lpk, lsrc, seg[3])
+        out.append({"N": N, "value": N / (tot / 1e3), "unit": UNIT, "ms_per_step": tot, "steps": steps,
+                    "parts_ms": {"gram": seg[0], "slista_fwd": seg[1], "objective": seg[2], "slista_bwd": seg[3]},
+                    "slista_fwd_frac": fwd["frac"], "slista_bwd_frac": bwd["frac"]})
+        del D, X
+        torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------- oracle (CPU)
 
-def oracle_step(w, rows, alpha64, L_fixed_s=None):
-    """The oracle's version of one step on the sample rows; returns seconds."""
+def oracle_step(w, rows, alpha64):
+    """The oracle's version of one step on the sample rows (Gram, Step-LISTA
+    forward, objective and gap, step-size sub-gradient); returns seconds."""
     import oracle
     D = w.D.astype(np.float64)
     X = w.X[rows].astype(np.float64)
     t0 = time.perf_counter()
-    oracle.gram(D, X[:, :])  # B, C, xsq for these samples (B is cheap at this size)
+    oracle.gram(D, X)
     Z = oracle.pgd(D, X, w.lam, alpha64)
     oracle.objective(D, X, Z, w.lam)
     oracle.slista_grad(D, X, w.lam, alpha64)
-    L = 1.0 / alpha64[0]
-    oracle.oista(D, X, w.lam, L, len(alpha64))
     return time.perf_counter() - t0
 
 
-CPU_TARGET_S = 12.0  # CPU work of the default baseline sample
+def _oracle_worker(job):
+    """Process-pool worker: the oracle step on one slice of rows."""
+    seed, N, T, rows, alpha64 = job
+    sys.path.insert(0, ROOT)
+    from paper_1905_11071_gb300 import synth
+    w = synth.slista_64x256(seed=seed, N=N, T=T)
+    return oracle_step(w, rows, alpha64)
 
 
-def cpu_baseline(w, n_samples: int):
-    """Times the oracle on a bounded sample of the workload (single thread).
-    n_samples = 0: a 24-sample probe sizes the sample to about CPU_TARGET_S
-    seconds of oracle work (at most the whole batch)."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_parallel(w, rows, alpha64, cores: int) -> float:
+    """Wall seconds of the oracle step on `rows` split evenly over `cores`
+    worker processes (spawned: the parent may hold a CUDA context)."""
+    import multiprocessing as mpr
+    chunks = [c for c in np.array_split(np.asarray(rows), cores) if len(c)]
+    jobs = [(w.seed, w.N, w.T, c, alpha64) for c in chunks]
+    ctx = mpr.get_context("spawn")
+    with ctx.Pool(len(jobs)) as pool:
+        pool.map(_oracle_worker, jobs[:1] * len(jobs))  # start-up and import, untimed
+        t0 = time.perf_counter()
+        pool.map(_oracle_worker, jobs)
+        return time.perf_counter() - t0
+
+
+CPU_TARGET_S = 10.0  # CPU work of the default single-thread baseline sample
+
+
+def cpu_baseline(w, n_samples: int, cores: int = 0):
+    """Times the oracle on a bounded sample of the workload: single thread
+    (sized from a 16-sample probe to about CPU_TARGET_S seconds) and on every
+    host core (worker processes, samples split evenly, the same per-core
+    share of work).  The per-dictionary L is charged once per batch."""
     import oracle
     oracle.build()
     D = w.D.astype(np.float64)
     t0 = time.perf_counter()
-    L = oracle.lipschitz(D)  # per-dictionary work, charged pro rata below
+    L = oracle.lipschitz(D)
     fixed = time.perf_counter() - t0
     alpha64 = np.full(w.T, 1.0 / L)
     if n_samples <= 0:
-        probe = min(24, w.N)
+        probe = min(16, w.N)
         tp = oracle_step(w, np.arange(probe), alpha64)
         n_samples = int(min(w.N, max(probe, round(probe * CPU_TARGET_S / max(tp, 1e-6)))))
     rows = np.arange(n_samples)
     per = oracle_step(w, rows, alpha64)
-    per_sample = per / n_samples
-    total_full = fixed + per_sample * w.N
-    return {"value": w.N / total_full, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d of %d samples, full step per sample; per-dictionary L (%.2f s) charged once "
-                      "per %d-sample batch" % (n_samples, w.N, fixed, w.N),
-            "seconds_measured": per + fixed}
+    single = w.N / (fixed + per / n_samples * w.N)
+    cores = cores or host_cores()
+    n_all = int(min(w.N, n_samples * cores))
+    wall = oracle_parallel(w, np.arange(n_all), alpha64, cores) if cores > 1 else per
+    if cores <= 1:
+        n_all = n_samples
+    allc = w.N / (fixed + wall / n_all * w.N)
+    return {"value": allc, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d samples on %d worker processes (the same step per sample: Gram, Step-LISTA "
+                      "forward, objective and gap, step-size sub-gradient); per-dictionary L (%.2f s) "
+                      "charged once per %d-sample batch" % (n_all, w.N, cores, fixed, w.N),
+            "seconds_measured": wall + fixed,
+            "single_thread": {"value": single, "cores": 1, "sample": "%d samples" % n_samples,
+                              "seconds_measured": per + fixed}}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle (there is no other implementation of
+    the paper's method to install) on every host core, each step a bounded
+    sample of the workload."""
     if rank != 0:
         return None
     from paper_1905_11071_gb300 import synth
@@ -451,27 +652,29 @@ def run_reference(args, rank, world):
     oracle.build()
     w = synth.slista_64x256(seed=0, N=args.N, T=args.T)
     D = w.D.astype(np.float64)
-    L = oracle.lipschitz(D)
-    alpha64 = np.full(w.T, 1.0 / L)
-    ns = args.cpu_samples or 8
     t_fix0 = time.perf_counter()
-    oracle.lipschitz(D)
+    L = oracle.lipschitz(D)
     fixed = time.perf_counter() - t_fix0
-    rows = np.arange(ns)
+    alpha64 = np.full(w.T, 1.0 / L)
+    cores = getattr(args, "cpu_cores", 0) or host_cores()
+    ns = args.cpu_samples or 4 * cores
+    rows = np.arange(min(ns, w.N))
+    run = ((lambda: oracle_parallel(w, rows, alpha64, cores)) if cores > 1
+           else (lambda: oracle_step(w, rows, alpha64)))
     for _ in range(max(args.warmup, 0)):
-        oracle_step(w, rows, alpha64)
+        run()
     tot = 0.0
     for _ in range(args.steps):
-        tot += oracle_step(w, rows, alpha64) + fixed * ns / w.N
+        tot += run() + fixed * len(rows) / w.N
     sec = tot / args.steps
-    value = ns / sec
+    value = len(rows) / sec
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
             "config": arm_config(w, args, world),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d samples per step of the %d-sample workload; per-dictionary L "
-                                       "charged pro rata" % (ns, w.N)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d samples per step of the %d-sample workload on %d worker processes; "
+                                       "per-dictionary L charged pro rata" % (len(rows), w.N, cores)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -493,7 +696,7 @@ def main():
     out, w = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(w, args.cpu_samples)
+            out["cpu_baseline"] = cpu_baseline(w, args.cpu_samples, args.cpu_cores)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

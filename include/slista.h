@@ -40,6 +40,13 @@
  *     runs and outputs are untouched.
  *   - Calls on distinct streams with distinct output and workspace buffers may
  *     run concurrently.
+ *   - Buffers whose length is not fixed by the shape arguments alone - the
+ *     support masks (T x N x ceil(m/32) words), the checkpoints (a function
+ *     of ckpt_every) and the trajectory (a device-dependent tile layout) -
+ *     are passed with their length in elements (mask_words, ckpt_floats,
+ *     traj_floats).  A length below what the call needs
+ *     (slista_mask_words, slista_ckpt_floats, slista_traj_floats) returns
+ *     SLISTA_ERR_WORKSPACE before any launch.
  */
 #ifndef SLISTA_H
 #define SLISTA_H
@@ -61,7 +68,8 @@ extern "C" {
 #define SLISTA_OK               0
 #define SLISTA_ERR_ARG         -1  /* null pointer, non-positive size, alpha <= 0, lam < 0 ... */
 #define SLISTA_ERR_UNSUPPORTED -2  /* shape or precision not built */
-#define SLISTA_ERR_WORKSPACE   -3  /* ws_bytes smaller than slista_workspace_bytes(), or ws not 256-byte aligned */
+#define SLISTA_ERR_WORKSPACE   -3  /* ws_bytes smaller than slista_workspace_bytes(), ws not 256-byte aligned,
+                                    * or a caller buffer (masks, ckpt, traj) shorter than its stated length needs */
 #define SLISTA_ERR_CUDA        -4  /* a CUDA runtime call failed */
 #define SLISTA_ERR_TIMEOUT     -5  /* a kernel's bounded wait expired (see slista_device_status) */
 
@@ -88,6 +96,15 @@ SLISTA_API const char *slista_last_error(void);
  * error flag, which a kernel sets when one of its bounded waits expires.
  * Returns SLISTA_OK, SLISTA_ERR_TIMEOUT or SLISTA_ERR_CUDA. */
 SLISTA_API int slista_device_status(void *stream);
+
+/* Failure-detection check (the paper has no counterpart): launches, on
+ * `stream`, one kernel that waits with the library's bounded wait on an
+ * mbarrier that nothing arrives at, with the limit lowered to limit_cycles
+ * (1 .. 1e8 SM cycles, else SLISTA_ERR_ARG), so that the wait expires and
+ * raises the device flag as an expired wait of a layer kernel would.  The
+ * next slista_device_status() on that stream then returns
+ * SLISTA_ERR_TIMEOUT and clears the flag.  Nothing else is touched. */
+SLISTA_API int slista_wait_probe(long long limit_cycles, void *stream);
 
 /* Bytes of scratch the call `fn` needs for these sizes (0 if none). */
 SLISTA_API size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_every);
@@ -127,12 +144,15 @@ SLISTA_API int ista_forward(const float *B, const float *C, int m, int N, float 
  * possible, so positivity is the caller's contract; the host-side wrapper
  * checks it).  Z (N x m) receives z^(T).
  * masks (nullable): per-layer support bits, layout above.
+ * mask_words: length of masks (>= slista_mask_words(m, N, T) when masks is
+ * given).
  * ckpt (nullable, needs masks): checkpoints every ckpt_every layers, layout above;
- * ckpt_every >= 1 (ignored when ckpt is NULL).  masks and ckpt are what
- * slista_backward consumes. */
+ * ckpt_every >= 1 (ignored when ckpt is NULL); ckpt_floats: its length
+ * (>= slista_ckpt_floats(m, N, T, ckpt_every) when ckpt is given).  masks
+ * and ckpt are what slista_backward consumes. */
 SLISTA_API int slista_forward(const float *B, const float *C, int m, int N, float lam,
                    const float *alpha, int T, int prec, float *Z,
-                   uint32_t *masks, float *ckpt, int ckpt_every,
+                   uint32_t *masks, size_t mask_words, float *ckpt, size_t ckpt_floats, int ckpt_every,
                    void *ws, size_t ws_bytes, void *stream);
 
 /* Step-LISTA forward on the tensor cores (SLISTA_PREC_BF16 or
@@ -143,19 +163,23 @@ SLISTA_API int slista_forward(const float *B, const float *C, int m, int N, floa
  * caching pool, a fixed arena, a per-process quota), and loops that cannot
  * afford the device-wide synchronisation cudaMalloc / cudaFree imply.
  * Arguments, results and arithmetic are those of slista_forward with
- * ckpt = NULL (the same kernel runs).  Its only scratch, the split copy of B
+ * ckpt = NULL (the same kernel runs); masks (nullable) holds mask_words
+ * words, at least slista_mask_words(m, N, T) when given.  Its only scratch, the split copy of B
  * (256 KiB), lives in a static device array of the library, which every GPU
  * that loads the library holds until the process exits; m is limited to
  * m <= 256 by its size (larger m: SLISTA_ERR_UNSUPPORTED).
  * The first call on a device looks up that array's device address (with the
  * device current) and caches it; make that first call before any stream
- * capture.  All calls share the array and each call rewrites it completely
+ * capture.  The cached address belongs to the device's current context: it
+ * is not looked up again after cudaDeviceReset (or any other teardown of the
+ * primary context), so do not call this entry point on a device after
+ * resetting it in the same process.  All calls share the array and each call rewrites it completely
  * before use: calls whose work may overlap on the GPU (different streams
  * without ordering between them) race on it and must be serialised by the
  * caller. */
 SLISTA_API int slista_forward_noalloc(const float *B, const float *C, int m, int N, float lam,
                                       const float *alpha, int T, int prec, float *Z, uint32_t *masks,
-                                      void *stream);
+                                      size_t mask_words, void *stream);
 
 /* Step-LISTA backward: the sub-gradient of sum_i F_{x_i}(z_i^(T)) (the
  * empirical form of Eq. unsupervised) with respect to alpha, obtained by the
@@ -168,7 +192,9 @@ SLISTA_API int slista_forward_noalloc(const float *B, const float *C, int m, int
  *                        G = h - alpha_t B h
  * where g^(t) = c - B z^(t).  Iterates between checkpoints are recomputed
  * from `ckpt`, so masks, ckpt and ckpt_every must come from a slista_forward
- * call with the same B, C, lam, alpha and T.
+ * call with the same B, C, lam, alpha and T; mask_words and ckpt_floats are
+ * their lengths (at least slista_mask_words(m, N, T) and, when ckpt_every <
+ * T, slista_ckpt_floats(m, N, T, ckpt_every)).
  * prec selects the arithmetic of the recompute and of B h:
  *   SLISTA_PREC_FP32: CUDA cores, FP32.  After a tensor-core forward the
  *     recomputed segments follow the FP32 trajectory from each checkpoint.
@@ -184,7 +210,8 @@ SLISTA_API int slista_forward_noalloc(const float *B, const float *C, int m, int
  * ckpt_every) bytes (else SLISTA_ERR_WORKSPACE). */
 SLISTA_API int slista_backward(const float *B, const float *C, int m, int N, float lam,
                     const float *alpha, int T, int prec,
-                    const uint32_t *masks, const float *ckpt, int ckpt_every,
+                    const uint32_t *masks, size_t mask_words, const float *ckpt, size_t ckpt_floats,
+                    int ckpt_every,
                     const float *gZ, float *dalpha,
                     void *ws, size_t ws_bytes, void *stream);
 
@@ -204,19 +231,24 @@ SLISTA_API int slista_backward(const float *B, const float *C, int m, int N, flo
  * slista_backward_traj on the same device reads it); 0 if (m, T) is outside
  * the path's range.
  * slista_forward_traj: slista_forward at SLISTA_PREC_BF16 / BF16X3 writing
- * Z, masks (required: the backward reads them) and traj; ws as for
- * slista_forward (SLISTA_FN_SLISTA_FWD).
+ * Z, masks (required: the backward reads them; mask_words >=
+ * slista_mask_words(m, N, T)) and traj (traj_floats >=
+ * slista_traj_floats(m, N, T)); ws as for slista_forward
+ * (SLISTA_FN_SLISTA_FWD).
  * slista_backward_traj: dalpha (T) from masks and traj of a
- * slista_forward_traj call with the same B, lam, alpha, T, prec and N; gZ
+ * slista_forward_traj call with the same B, lam, alpha, T, prec and N (with
+ * the same lengths mask_words and traj_floats as there); gZ
  * (nullable, N x m) replaces dF/dz^(T) as in slista_backward.  ws:
  * slista_workspace_bytes(SLISTA_FN_SLISTA_BWD_TRAJ, m, N, T, prec, 1). */
 SLISTA_API size_t slista_traj_floats(int m, int N, int T);
 SLISTA_API int slista_forward_traj(const float *B, const float *C, int m, int N, float lam,
                                    const float *alpha, int T, int prec, float *Z, uint32_t *masks,
-                                   float *traj, void *ws, size_t ws_bytes, void *stream);
+                                   size_t mask_words, float *traj, size_t traj_floats, void *ws,
+                                   size_t ws_bytes, void *stream);
 SLISTA_API int slista_backward_traj(const float *B, int m, int N, float lam, const float *alpha, int T,
-                                    int prec, const uint32_t *masks, const float *traj, const float *gZ,
-                                    float *dalpha, void *ws, size_t ws_bytes, void *stream);
+                                    int prec, const uint32_t *masks, size_t mask_words, const float *traj,
+                                    size_t traj_floats, const float *gZ, float *dalpha, void *ws,
+                                    size_t ws_bytes, void *stream);
 
 /* ---- ragged batches (many independent problems in one launch per layer) ----
  *
@@ -241,9 +273,11 @@ typedef struct slista_problem {
     float *Z;            /* forward: N x m codes z^(T) (out) */
     uint32_t *masks;     /* T x N x ceil(m/32) support words: written by the forward
                           * (nullable there), read by the backward */
+    size_t mask_words;   /* length of masks (>= slista_mask_words(m, N, T) when given) */
     float *ckpt;         /* slista_ckpt_floats(m, N, T, ckpt_every) floats: written by
                           * the forward, read by the backward; may be NULL when
                           * ckpt_every >= T */
+    size_t ckpt_floats;  /* length of ckpt */
     const float *gZ;     /* backward: upstream gradient dLoss/dz^(T) (N x m), nullable */
     float *dalpha;       /* backward: T floats (out) */
 } slista_problem_t;

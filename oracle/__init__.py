@@ -179,15 +179,20 @@ def ista(D, X, lam, L, T):
     return pgd(D, X, lam, np.full(T, 1.0 / L))
 
 
-def oista(D, X, lam, L, T, keep_all: bool = False, with_margin: bool = False):
+def oista(D, X, lam, L, T, keep_all: bool = False, with_margin: bool = False,
+          layer_margins: bool = False):
     """Oracle-ISTA, Algorithm 1.
 
     Returns (Z, LS, accepted, decision): z^(T) (or every iterate,
-    (T+1) x N x m, if ``keep_all``); the L_S used at the last layer per
-    sample; per-layer count of samples whose step met condition (star); and
-    the per-layer, per-sample (star) outcome (T x N, uint8).  With
-    ``with_margin`` a fifth value: per sample, the smallest distance of a
-    pre-threshold value to its threshold along the trajectory.
+    (T+1) x N x m, if ``keep_all``); the L_S of the last support the method
+    evaluated, per sample; per-layer count of samples whose local step met
+    condition (star); and the per-layer, per-sample (star) outcome (T x N,
+    uint8).  With ``with_margin`` one more value: per sample, the smallest
+    decision margin along its trajectory (N).  With ``layer_margins`` one
+    more value (after that one when both are asked for): the decision margin
+    of every layer and sample (T x N) -- the smallest distance of a
+    pre-threshold value to its threshold among the codes off the support
+    under the local step 1/L_S and every code under the step taken.
     """
     D = _f64(D); X = _f64(X)
     n, m = D.shape
@@ -196,13 +201,17 @@ def oista(D, X, lam, L, T, keep_all: bool = False, with_margin: bool = False):
     acc = np.zeros(T, dtype=np.int32)
     dec = np.zeros((T, N), dtype=np.uint8)
     Zall = np.empty((T + 1, N, m)) if keep_all else None
-    marg = np.empty(N) if with_margin else None
+    marg = np.empty((T, N)) if (with_margin or layer_margins) else None
     _load().orc_oista(_p(D), n, m, _p(X), N, float(lam), float(L), int(T), _p(Z), _p(LS),
                       acc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                       dec.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
-                      _p(Zall) if keep_all else None, _p(marg) if with_margin else None)
+                      _p(Zall) if keep_all else None, _p(marg) if marg is not None else None)
     out = ((Zall if keep_all else Z), LS, acc, dec)
-    return out + (marg,) if with_margin else out
+    if with_margin:
+        out = out + ((marg.min(axis=0) if T > 0 else np.full(N, np.inf)),)
+    if layer_margins:
+        out = out + (marg,)
+    return out
 
 
 def slista_grad(D, X, lam, alpha):

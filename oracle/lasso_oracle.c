@@ -327,88 +327,108 @@ void orc_lista(const double *D, int n, int m, const double *X, int N, double lam
 /* Oracle-ISTA (Algorithm 1, Section 3).                                     */
 /* ------------------------------------------------------------------------ */
 
-/* For each sample, from z^(0) = 0 and for t = 0..T-1:
- *   S = supp(z^(t)); L_S by Eq. spca (L_{empty} = L);
- *   y = psi_{1/L_S}(z^(t), x);
- *   if supp(y) is contained in S (condition (star)) z^(t+1) = y,
- *   else z^(t+1) = psi_{1/L}(z^(t), x).
- * L_S is recomputed only when S differs from the support it was last computed
- * for (the value is a function of S alone).
- * Outputs: Z (N x m) = z^(T); LS (N, may be NULL) = the L_S used at the last
- * layer; accepted (T, may be NULL) = number of samples whose step t satisfied
- * condition (star); decision (T x N, may be NULL) = 1 if sample's step t
- * satisfied (star), else 0; Zall ((T+1) x N x m, may be NULL) = every
- * iterate; margin (N, may be NULL) = for each sample, the smallest distance
- * to a threshold met on its trajectory: over all layers, |lam/L_S - |u_j||
- * for the candidate's pre-threshold values u off S (how close condition
- * (star) came to flipping) and ||u_j| - a lam| for the step actually taken
- * (how close the support came to changing).  Decisions of samples with a
- * tiny margin are at the mercy of rounding. */
+/* The method.  Restricted to codes supported on S, the smooth part of F_x
+ * has an L_S-Lipschitz gradient (Eq. spca), so the quadratic majorant of
+ * F_x at z with curvature L_S bounds F_x from above at every point whose
+ * support lies in S = supp(z) (the argument of Section 3 built on
+ * Eq. majorization2).  Minimising that majorant is the proximal step with
+ * step 1/L_S; its result is a certified descent step whenever its own
+ * support stays inside S, condition (star).  When it leaves S the global
+ * majorant with curvature L (an ISTA step) is used instead.  L_S is a
+ * function of S alone, so one value is kept per sample and recomputed only
+ * when S changes; the empty support takes L.
+ *
+ * This routine runs that method for T layers from z^(0) = 0, independently
+ * per sample, with exact eigenvalues (cyclic Jacobi) and gradients formed as
+ * D^T(Dz - x).
+ * Outputs (every one but Z may be NULL): Z (N x m) = z^(T); LS (N) = the
+ * L_S belonging to supp(z^(T-1)), the last support the method evaluated;
+ * accepted (T) = per layer, the number of samples whose local step met
+ * condition (star); decision (T x N) = that outcome per layer and sample;
+ * Zall ((T+1) x N x m) = every iterate; margin (T x N) = for layer t and
+ * sample s, how far the layer's decisions were from flipping: the smallest
+ * distance of a pre-threshold value to its threshold among (i) the codes
+ * outside S under the local step (which decide condition (star)) and (ii)
+ * every code under the step actually taken (which decide the new support).
+ * A layer whose margin is below the arithmetic's error scale can decide
+ * differently in another precision; every later layer of that sample then
+ * follows another trajectory. */
+
+/* out = ST(z - step * grad, step * lam), coordinatewise; also returns
+ * min_j ||z_j - step grad_j| - step lam| over the codes j with sel[j] != 0
+ * (every code when sel is NULL). */
+static double prox_step_with_margin(const double *z, const double *grad, int m, double step, double lam,
+                                    const unsigned char *sel, double *out)
+{
+    double closest = INFINITY;
+    for (int j = 0; j < m; ++j) {
+        const double u = z[j] - step * grad[j];
+        out[j] = orc_st(u, step * lam);
+        const double d = fabs(fabs(u) - step * lam);
+        if ((sel == NULL || sel[j]) && d < closest) closest = d;
+    }
+    return closest;
+}
+
 void orc_oista(const double *D, int n, int m, const double *X, int N, double lam,
                double L, int T, double *Z, double *LS, int *accepted, unsigned char *decision,
                double *Zall, double *margin)
 {
     double *z = (double *)malloc(sizeof(double) * (size_t)m);
-    double *y = (double *)malloc(sizeof(double) * (size_t)m);
-    double *work = (double *)malloc(sizeof(double) * (size_t)(n + m));
+    double *cand = (double *)malloc(sizeof(double) * (size_t)m);
+    double *fallback = (double *)malloc(sizeof(double) * (size_t)m);
+    double *grad = (double *)malloc(sizeof(double) * (size_t)m);
+    double *work = (double *)malloc(sizeof(double) * (size_t)n);
     double *ework = (double *)malloc(sizeof(double) * 2 * (size_t)m * m);
     int *idx = (int *)malloc(sizeof(int) * (size_t)m);
     unsigned char *S = (unsigned char *)malloc((size_t)m);
-    unsigned char *Sprev = (unsigned char *)malloc((size_t)m);
+    unsigned char *offS = (unsigned char *)malloc((size_t)m);
+    unsigned char *S_cached = (unsigned char *)malloc((size_t)m);
     if (accepted)
         for (int t = 0; t < T; ++t) accepted[t] = 0;
     for (int s = 0; s < N; ++s) {
         const double *x = X + (size_t)s * n;
-        double LSval = L;
-        double marg = INFINITY;
-        int have_prev = 0;
+        double L_S = L;
+        int have_cache = 0;
         for (int j = 0; j < m; ++j) z[j] = 0.0;
         if (Zall) memcpy(Zall + (size_t)s * m, z, sizeof(double) * (size_t)m);
         for (int t = 0; t < T; ++t) {
             int k = 0;
             for (int j = 0; j < m; ++j) {
-                S[j] = (z[j] != 0.0);
+                S[j] = z[j] != 0.0;
+                offS[j] = !S[j];
                 if (S[j]) idx[k++] = j;
             }
-            if (!have_prev || memcmp(S, Sprev, (size_t)m) != 0) {
-                LSval = support_lipschitz(D, n, m, idx, k, L, ework);
-                memcpy(Sprev, S, (size_t)m);
-                have_prev = 1;
+            if (!have_cache || memcmp(S, S_cached, (size_t)m) != 0) {
+                L_S = support_lipschitz(D, n, m, idx, k, L, ework);  /* L for the empty support */
+                memcpy(S_cached, S, (size_t)m);
+                have_cache = 1;
             }
-            psi(D, n, m, x, lam, 1.0 / LSval, z, y, work);
-            int ok = 1;
+            lasso_grad(D, n, m, x, z, grad, work);
+            /* the step of the local majorant, and how close its codes off S came to their threshold */
+            const double off_margin = prox_step_with_margin(z, grad, m, 1.0 / L_S, lam, offS, cand);
+            int stays_in_S = 1;
             for (int j = 0; j < m; ++j)
-                if (y[j] != 0.0 && !S[j]) { ok = 0; break; }
-            if (margin) {
-                /* work + n holds D^T(Dz - x) from the psi call above */
-                const double *grad = work + n;
-                for (int j = 0; j < m; ++j) {
-                    double u = z[j] - grad[j] / LSval;
-                    double dist = fabs(fabs(u) - lam / LSval);
-                    if ((!S[j] || ok) && dist < marg) marg = dist;
-                    if (!ok) {
-                        double uL = z[j] - grad[j] / L;
-                        double dL = fabs(fabs(uL) - lam / L);
-                        if (dL < marg) marg = dL;
-                    }
-                }
-            }
-            if (ok) {
-                memcpy(z, y, sizeof(double) * (size_t)m);
+                if (cand[j] != 0.0 && !S[j]) stays_in_S = 0;
+            double taken_margin;
+            if (stays_in_S) {
+                taken_margin = prox_step_with_margin(z, grad, m, 1.0 / L_S, lam, NULL, cand);
+                memcpy(z, cand, sizeof(double) * (size_t)m);
                 if (accepted) accepted[t] += 1;
             } else {
-                psi(D, n, m, x, lam, 1.0 / L, z, y, work);
-                memcpy(z, y, sizeof(double) * (size_t)m);
+                taken_margin = prox_step_with_margin(z, grad, m, 1.0 / L, lam, NULL, fallback);
+                memcpy(z, fallback, sizeof(double) * (size_t)m);
             }
-            if (decision) decision[(size_t)t * N + s] = (unsigned char)ok;
+            if (decision) decision[(size_t)t * N + s] = (unsigned char)stays_in_S;
+            if (margin) margin[(size_t)t * N + s] = off_margin < taken_margin ? off_margin : taken_margin;
             if (Zall) memcpy(Zall + ((size_t)(t + 1) * N + s) * m, z, sizeof(double) * (size_t)m);
-            if (LS && t == T - 1) LS[s] = LSval;
+            if (LS && t == T - 1) LS[s] = L_S;
         }
         memcpy(Z + (size_t)s * m, z, sizeof(double) * (size_t)m);
         if (LS && T == 0) LS[s] = L;
-        if (margin) margin[s] = marg;
     }
-    free(z); free(y); free(work); free(ework); free(idx); free(S); free(Sprev);
+    free(z); free(cand); free(fallback); free(grad); free(work); free(ework); free(idx);
+    free(S); free(offS); free(S_cached);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -42,6 +42,7 @@ EXPORTS = [
     "slista_backward", "oista_forward", "lasso_objective", "slista_forward_noalloc",
     "slista_batched_workspace_bytes", "slista_forward_batched", "slista_backward_batched",
     "slista_traj_floats", "slista_forward_traj", "slista_backward_traj", "lasso_support_lipschitz",
+    "slista_wait_probe",
 ]
 
 
@@ -54,8 +55,8 @@ class Problem(ctypes.Structure):
     """slista_problem_t: one problem of a ragged batch (device pointers)."""
     _fields_ = [("B", ctypes.c_void_p), ("C", ctypes.c_void_p), ("m", ctypes.c_int), ("N", ctypes.c_int),
                 ("lam", ctypes.c_float), ("alpha", ctypes.c_void_p), ("Z", ctypes.c_void_p),
-                ("masks", ctypes.c_void_p), ("ckpt", ctypes.c_void_p), ("gZ", ctypes.c_void_p),
-                ("dalpha", ctypes.c_void_p)]
+                ("masks", ctypes.c_void_p), ("mask_words", ctypes.c_size_t), ("ckpt", ctypes.c_void_p),
+                ("ckpt_floats", ctypes.c_size_t), ("gZ", ctypes.c_void_p), ("dalpha", ctypes.c_void_p)]
 
 
 class SlistaError(RuntimeError):
@@ -85,6 +86,7 @@ def load(path: str = LIB_PATH):
         lib.slista_last_error.restype = ctypes.c_char_p
         lib.slista_last_error.argtypes = []
         lib.slista_device_status.argtypes = [vp]
+        lib.slista_wait_probe.argtypes = [ctypes.c_longlong, vp]
         lib.slista_workspace_bytes.restype = sz
         lib.slista_workspace_bytes.argtypes = [i, i, i, i, i, i]
         lib.slista_ckpt_floats.restype = sz
@@ -94,13 +96,13 @@ def load(path: str = LIB_PATH):
         lib.lasso_gram.argtypes = [vp, i, i, vp, i, vp, vp, vp, vp, vp]
         lib.lasso_lipschitz.argtypes = [vp, i, vp, vp]
         lib.ista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, sz, vp]
-        lib.slista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp, i, vp, sz, vp]
-        lib.slista_backward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, i, vp, vp, vp, sz, vp]
-        lib.slista_forward_noalloc.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp]
+        lib.slista_forward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, sz, vp, sz, i, vp, sz, vp]
+        lib.slista_backward.argtypes = [vp, vp, i, i, f, vp, i, i, vp, sz, vp, sz, i, vp, vp, vp, sz, vp]
+        lib.slista_forward_noalloc.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, sz, vp]
         lib.slista_traj_floats.argtypes = [i, i, i]
         lib.slista_traj_floats.restype = sz
-        lib.slista_forward_traj.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
-        lib.slista_backward_traj.argtypes = [vp, i, i, f, vp, i, i, vp, vp, vp, vp, vp, sz, vp]
+        lib.slista_forward_traj.argtypes = [vp, vp, i, i, f, vp, i, i, vp, vp, sz, vp, sz, vp, sz, vp]
+        lib.slista_backward_traj.argtypes = [vp, i, i, f, vp, i, i, vp, sz, vp, sz, vp, vp, vp, sz, vp]
         lib.oista_forward.argtypes = [vp, vp, vp, i, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
         lib.lasso_objective.argtypes = [vp, vp, vp, vp, i, i, f, vp, vp, vp]
         lib.lasso_support_lipschitz.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, sz, vp]
@@ -154,6 +156,11 @@ def _opt(t, dtype, shape, name):
     return None if t is None else _need(t, dtype, shape, name)
 
 
+def _len(t) -> int:
+    """Length in elements of an optional buffer (0 for None)."""
+    return 0 if t is None else int(t.numel())
+
+
 def slista_last_error() -> str:
     msg = load().slista_last_error()
     return msg.decode() if msg else ""
@@ -161,6 +168,12 @@ def slista_last_error() -> str:
 
 def slista_device_status(stream=None) -> None:
     _check(load().slista_device_status(_stream(stream)), "slista_device_status")
+
+
+def slista_wait_probe(limit_cycles: int, stream=None) -> None:
+    """Launches the bounded-wait check kernel (its wait expires after
+    limit_cycles and raises the device flag)."""
+    _check(load().slista_wait_probe(int(limit_cycles), _stream(stream)), "slista_wait_probe")
 
 
 def slista_workspace_bytes(fn: int, m: int, N: int, T: int, prec: int, ckpt_every: int = 1) -> int:
@@ -222,13 +235,10 @@ def slista_forward(B, C, lam, alpha, prec, Z, masks=None, ckpt=None, ckpt_every=
     _need(Z, torch.float32, (N, m), "Z")
     _opt(masks, torch.int32, None, "masks")
     _opt(ckpt, torch.float32, None, "ckpt")
-    if masks is not None and masks.numel() < slista_mask_words(m, N, T):
-        raise ValueError("masks too small")
-    if ckpt is not None and ckpt.numel() < slista_ckpt_floats(m, N, T, ckpt_every):
-        raise ValueError("ckpt too small")
     wsb = 0 if ws is None else ws.numel() * ws.element_size()
     _check(load().slista_forward(_ptr(B), _ptr(C), m, N, float(lam), _ptr(alpha), T, int(prec), _ptr(Z),
-                                 _ptr(masks), _ptr(ckpt), int(ckpt_every), _ptr(ws), wsb, _stream(stream)),
+                                 _ptr(masks), _len(masks), _ptr(ckpt), _len(ckpt), int(ckpt_every), _ptr(ws), wsb,
+                                 _stream(stream)),
            "slista_forward")
 
 
@@ -244,7 +254,7 @@ def slista_forward_noalloc(B, C, lam, alpha, prec, Z, masks=None, stream=None) -
     _need(Z, torch.float32, (N, m), "Z")
     _opt(masks, torch.int32, None, "masks")
     _check(load().slista_forward_noalloc(_ptr(B), _ptr(C), m, N, float(lam), _ptr(alpha), T, int(prec), _ptr(Z),
-                                         _ptr(masks), _stream(stream)), "slista_forward_noalloc")
+                                         _ptr(masks), _len(masks), _stream(stream)), "slista_forward_noalloc")
 
 
 def slista_backward(B, C, lam, alpha, prec, masks, ckpt, ckpt_every, dalpha, gZ=None, ws=None,
@@ -262,8 +272,8 @@ def slista_backward(B, C, lam, alpha, prec, masks, ckpt, ckpt_every, dalpha, gZ=
     _need(dalpha, torch.float32, (T,), "dalpha")
     wsb = 0 if ws is None else ws.numel() * ws.element_size()
     _check(load().slista_backward(_ptr(B), _ptr(C), m, N, float(lam), _ptr(alpha), T, int(prec), _ptr(masks),
-                                  _ptr(ckpt), int(ckpt_every), _ptr(gZ), _ptr(dalpha), _ptr(ws), wsb,
-                                  _stream(stream)), "slista_backward")
+                                  _len(masks), _ptr(ckpt), _len(ckpt), int(ckpt_every), _ptr(gZ), _ptr(dalpha),
+                                  _ptr(ws), wsb, _stream(stream)), "slista_backward")
 
 
 def slista_traj_floats(m: int, N: int, T: int) -> int:
@@ -282,13 +292,10 @@ def slista_forward_traj(B, C, lam, alpha, prec, Z, masks, traj, ws=None, stream=
     _need(Z, torch.float32, (N, m), "Z")
     _need(masks, torch.int32, None, "masks")
     _need(traj, torch.float32, None, "traj")
-    if masks.numel() < slista_mask_words(m, N, T):
-        raise ValueError("masks too small")
-    if traj.numel() < slista_traj_floats(m, N, T):
-        raise ValueError("traj too small")
     wsb = 0 if ws is None else ws.numel() * ws.element_size()
     _check(load().slista_forward_traj(_ptr(B), _ptr(C), m, N, float(lam), _ptr(alpha), T, int(prec), _ptr(Z),
-                                      _ptr(masks), _ptr(traj), _ptr(ws), wsb, _stream(stream)),
+                                      _ptr(masks), _len(masks), _ptr(traj), _len(traj), _ptr(ws), wsb,
+                                      _stream(stream)),
            "slista_forward_traj")
 
 
@@ -305,7 +312,8 @@ def slista_backward_traj(B, N, lam, alpha, prec, masks, traj, dalpha, gZ=None, w
     _need(dalpha, torch.float32, (T,), "dalpha")
     wsb = 0 if ws is None else ws.numel() * ws.element_size()
     _check(load().slista_backward_traj(_ptr(B), m, int(N), float(lam), _ptr(alpha), T, int(prec), _ptr(masks),
-                                       _ptr(traj), _ptr(gZ), _ptr(dalpha), _ptr(ws), wsb, _stream(stream)),
+                                       _len(masks), _ptr(traj), _len(traj), _ptr(gZ), _ptr(dalpha), _ptr(ws), wsb,
+                                       _stream(stream)),
            "slista_backward_traj")
 
 
@@ -384,6 +392,8 @@ def _problems(probs, T, backward):
         for k in ("Z", "masks", "ckpt", "gZ", "dalpha"):
             t = q.get(k)
             setattr(p, k, None if t is None else t.data_ptr())
+        p.mask_words = _len(q.get("masks"))
+        p.ckpt_floats = _len(q.get("ckpt"))
     return arr
 
 

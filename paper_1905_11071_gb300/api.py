@@ -219,44 +219,58 @@ def objective(B, C, xsq, Z, lam, with_gap: bool = True, stream=None):
     return (F, gap) if with_gap else F
 
 
-class SlistaLoss(torch.autograd.Function):
-    """sum_i F_{x_i}(Phi_alpha(x_i)) with Phi the T-layer Step-LISTA network.
+def _traj_ok(prec, m: int, T: int) -> bool:
+    """Whether the one-pass (trajectory) backward exists for this case."""
+    return _prec(prec) in (_lib.PREC_BF16, _lib.PREC_BF16X3) and m <= 256 and 1 <= T <= 256
 
-    forward(alpha, B, C, xsq, lam, ckpt_every) -> scalar loss (float64)
-    backward -> d loss / d alpha from the hand-written adjoint kernel.
+
+class SlistaLoss(torch.autograd.Function):
+    """sum_i F_{x_i}(Phi_alpha(x_i)) with Phi the T-layer Step-LISTA network
+    (the empirical form of Eq. unsupervised).
+
+    forward(alpha, B, C, xsq, lam, ckpt_every, prec) -> scalar loss (float64)
+    backward -> d loss / d alpha from the hand-written adjoint kernel at the
+    same precision: on the tensor cores ("bf16x3", "bf16") the forward keeps
+    the adjoint's inputs (one reverse sweep, m <= 256) or checkpoints; on the
+    CUDA cores ("fp32") checkpoints and a recompute.
     """
 
     @staticmethod
-    def forward(ctx, alpha, B, C, xsq, lam, ckpt_every=None):
-        Z, st = slista(B, C, lam, alpha, keep_for_backward=True, ckpt_every=ckpt_every)
+    def forward(ctx, alpha, B, C, xsq, lam, ckpt_every=None, prec="fp32"):
+        m, T = C.shape[1], alpha.shape[0]
+        traj = _traj_ok(prec, m, T)
+        Z, st = slista(B, C, lam, alpha, prec=prec, keep_for_backward=True, ckpt_every=ckpt_every,
+                       trajectory=traj)
         F = objective(B, C, xsq, Z, lam, with_gap=False)
         ctx.save_for_backward(alpha, B, C)
         ctx.state = st
         ctx.lam = lam
+        ctx.prec = prec
         return F.sum()
 
     @staticmethod
     def backward(ctx, grad_out):
         alpha, B, C = ctx.saved_tensors
-        da = slista_grad(B, C, ctx.lam, alpha, ctx.state)
-        return (da * grad_out.to(da.dtype)), None, None, None, None, None
+        da = slista_grad(B, C, ctx.lam, alpha, ctx.state, prec=ctx.prec)
+        return (da * grad_out.to(da.dtype)), None, None, None, None, None, None
 
 
-def slista_loss(alpha, g: Gram, lam, ckpt_every=None):
-    return SlistaLoss.apply(alpha, g.B, g.C, g.xsq, lam, ckpt_every)
+def slista_loss(alpha, g: Gram, lam, ckpt_every=None, prec="fp32"):
+    return SlistaLoss.apply(alpha, g.B, g.C, g.xsq, lam, ckpt_every, prec)
 
 
 def train_step_sizes(alpha0: torch.Tensor, g: Gram, lam: float, steps: int = 50, lr0: Optional[float] = None,
-                     grow: float = 1.2, max_halvings: int = 20, min_alpha: float = 1e-6):
+                     grow: float = 1.2, max_halvings: int = 20, min_alpha: float = 1e-6, prec="fp32"):
     """Full-batch sub-gradient descent with backtracking on the step sizes
     (Appendix E).  A trial step alpha - lr * dalpha is accepted when the loss
     does not increase; otherwise lr is halved (at most max_halvings times).
     After an accepted step lr grows by `grow`.  Steps stay >= min_alpha.
-    Returns (alpha, history of losses)."""
+    prec: precision of the forward and of the adjoint ("fp32", "bf16x3",
+    "bf16").  Returns (alpha, history of losses)."""
     alpha = alpha0.detach().clone()
     hist = []
     a = alpha.clone().requires_grad_(True)
-    loss = slista_loss(a, g, lam)
+    loss = slista_loss(a, g, lam, prec=prec)
     loss.backward()
     cur = float(loss.detach())
     grad = a.grad.detach().clone()
@@ -270,10 +284,11 @@ def train_step_sizes(alpha0: torch.Tensor, g: Gram, lam: float, steps: int = 50,
         for _h in range(max_halvings):
             trial = torch.clamp(alpha - lr * grad, min=min_alpha)
             t = trial.clone().requires_grad_(True)
-            tl = slista_loss(t, g, lam)
-            if float(tl) <= cur:
+            tl = slista_loss(t, g, lam, prec=prec)
+            tv = float(tl.detach())
+            if tv <= cur:
                 tl.backward()
-                alpha, cur, grad = trial, float(tl), t.grad.detach().clone()
+                alpha, cur, grad = trial, tv, t.grad.detach().clone()
                 lr *= grow
                 accepted = True
                 break

@@ -101,6 +101,15 @@ int check_lam(float lam)
 // and bulk copies, which need aligned addresses.
 bool ws_aligned(const void *ws) { return (reinterpret_cast<uintptr_t>(ws) & 255) == 0; }
 
+// A caller buffer (masks, checkpoints, trajectory) whose stated length is
+// below what the call writes or reads: refused before any launch.
+int check_len(const void *buf, size_t have, size_t need, const char *fn, const char *what, const char *unit)
+{
+    if (buf && have < need)
+        return fail(SLISTA_ERR_WORKSPACE, "%s: %s holds %zu %s, %zu needed", fn, what, have, unit, need);
+    return SLISTA_OK;
+}
+
 int forward_common(const PgdArgs &a, int prec, void *ws, size_t ws_bytes, cudaStream_t st, const char *name)
 {
     SLISTA_REQUIRE(valid_prec(prec), SLISTA_ERR_ARG, "%s: unknown precision %d", name, prec);
@@ -135,6 +144,14 @@ int slista_device_status(void *stream)
     cudaStream_t st = as_stream(stream);
     SLISTA_CUDA_TRY(cudaStreamSynchronize(st));
     return read_and_clear_device_flag(st);
+}
+
+int slista_wait_probe(long long limit_cycles, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(limit_cycles >= 1 && limit_cycles <= 100000000LL, SLISTA_ERR_ARG,
+                   "slista_wait_probe: 1 <= limit_cycles <= 1e8 (got %lld)", limit_cycles);
+    return tc::launch_wait_probe(limit_cycles, as_stream(stream));
 }
 
 size_t slista_ckpt_floats(int m, int N, int T, int ckpt_every)
@@ -217,7 +234,8 @@ int ista_forward(const float *B, const float *C, int m, int N, float lam, const 
 }
 
 int slista_forward(const float *B, const float *C, int m, int N, float lam, const float *alpha, int T, int prec,
-                   float *Z, uint32_t *masks, float *ckpt, int ckpt_every, void *ws, size_t ws_bytes, void *stream)
+                   float *Z, uint32_t *masks, size_t mask_words, float *ckpt, size_t ckpt_floats, int ckpt_every,
+                   void *ws, size_t ws_bytes, void *stream)
 {
     clear_error();
     SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 0, SLISTA_ERR_ARG, "slista_forward: bad sizes m=%d N=%d T=%d", m, N,
@@ -227,12 +245,18 @@ int slista_forward(const float *B, const float *C, int m, int N, float lam, cons
     SLISTA_REQUIRE(!ckpt || ckpt_every >= 1, SLISTA_ERR_ARG, "slista_forward: ckpt_every must be >= 1");
     int rc = check_lam(lam);
     if (rc) return rc;
+    rc = check_len(masks, mask_words, slista_mask_words(m, N, T), "slista_forward", "masks", "words");
+    if (rc) return rc;
+    if (ckpt && ckpt_every < T) {
+        rc = check_len(ckpt, ckpt_floats, slista_ckpt_floats(m, N, T, ckpt_every), "slista_forward", "ckpt", "floats");
+        if (rc) return rc;
+    }
     PgdArgs a{B, C, m, N, lam, alpha, nullptr, T, Z, masks, ckpt, ckpt ? ckpt_every : 1};
     return forward_common(a, prec, ws, ws_bytes, as_stream(stream), "slista_forward");
 }
 
 int slista_forward_noalloc(const float *B, const float *C, int m, int N, float lam, const float *alpha, int T,
-                           int prec, float *Z, uint32_t *masks, void *stream)
+                           int prec, float *Z, uint32_t *masks, size_t mask_words, void *stream)
 {
     clear_error();
     SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 0, SLISTA_ERR_ARG, "slista_forward_noalloc: bad sizes m=%d N=%d T=%d", m,
@@ -245,13 +269,15 @@ int slista_forward_noalloc(const float *B, const float *C, int m, int N, float l
                    "slista_forward_noalloc: m = %d exceeds the static scratch limit m <= %d", m, tc::noalloc_max_m());
     int rc = check_lam(lam);
     if (rc) return rc;
+    rc = check_len(masks, mask_words, slista_mask_words(m, N, T), "slista_forward_noalloc", "masks", "words");
+    if (rc) return rc;
     PgdArgs a{B, C, m, N, lam, alpha, nullptr, T, Z, masks, nullptr, 1};
     return tc::launch_forward_noalloc(a, prec, as_stream(stream));
 }
 
 int slista_backward(const float *B, const float *C, int m, int N, float lam, const float *alpha, int T, int prec,
-                    const uint32_t *masks, const float *ckpt, int ckpt_every, const float *gZ, float *dalpha,
-                    void *ws, size_t ws_bytes, void *stream)
+                    const uint32_t *masks, size_t mask_words, const float *ckpt, size_t ckpt_floats, int ckpt_every,
+                    const float *gZ, float *dalpha, void *ws, size_t ws_bytes, void *stream)
 {
     clear_error();
     SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 1, SLISTA_ERR_ARG, "slista_backward: bad sizes m=%d N=%d T=%d", m, N,
@@ -270,6 +296,12 @@ int slista_backward(const float *B, const float *C, int m, int N, float lam, con
     SLISTA_REQUIRE(N == 0 || K >= T || ckpt, SLISTA_ERR_ARG, "slista_backward: ckpt must not be NULL");
     int rc = check_lam(lam);
     if (rc) return rc;
+    rc = check_len(masks, mask_words, slista_mask_words(m, N, T), "slista_backward", "masks", "words");
+    if (rc) return rc;
+    if (K < T) {
+        rc = check_len(ckpt, ckpt_floats, slista_ckpt_floats(m, N, T, K), "slista_backward", "ckpt", "floats");
+        if (rc) return rc;
+    }
     const bool wide = tcp && !tc::supported(m);
     const size_t need = wide  ? tcw::backward_ws_bytes(m, N, T, K)
                         : tcp ? tc::backward_ws_bytes(m, N, T, K)
@@ -289,7 +321,8 @@ size_t slista_traj_floats(int m, int N, int T)
 }
 
 int slista_forward_traj(const float *B, const float *C, int m, int N, float lam, const float *alpha, int T, int prec,
-                        float *Z, uint32_t *masks, float *traj, void *ws, size_t ws_bytes, void *stream)
+                        float *Z, uint32_t *masks, size_t mask_words, float *traj, size_t traj_floats, void *ws,
+                        size_t ws_bytes, void *stream)
 {
     clear_error();
     SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 1, SLISTA_ERR_ARG, "slista_forward_traj: bad sizes m=%d N=%d T=%d", m, N,
@@ -304,6 +337,10 @@ int slista_forward_traj(const float *B, const float *C, int m, int N, float lam,
                    "slista_forward_traj: C, Z, masks and traj must not be NULL");
     int rc = check_lam(lam);
     if (rc) return rc;
+    rc = check_len(masks, mask_words, slista_mask_words(m, N, T), "slista_forward_traj", "masks", "words");
+    if (rc) return rc;
+    rc = check_len(traj, traj_floats, slista_traj_floats(m, N, T), "slista_forward_traj", "traj", "floats");
+    if (rc) return rc;
     const size_t need = tc::forward_ws_bytes(m);
     SLISTA_REQUIRE(ws_bytes >= need && ws != nullptr && ws_aligned(ws), SLISTA_ERR_WORKSPACE,
                    "slista_forward_traj: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
@@ -312,8 +349,8 @@ int slista_forward_traj(const float *B, const float *C, int m, int N, float lam,
 }
 
 int slista_backward_traj(const float *B, int m, int N, float lam, const float *alpha, int T, int prec,
-                         const uint32_t *masks, const float *traj, const float *gZ, float *dalpha, void *ws,
-                         size_t ws_bytes, void *stream)
+                         const uint32_t *masks, size_t mask_words, const float *traj, size_t traj_floats,
+                         const float *gZ, float *dalpha, void *ws, size_t ws_bytes, void *stream)
 {
     clear_error();
     SLISTA_REQUIRE(m >= 1 && N >= 0 && T >= 1, SLISTA_ERR_ARG, "slista_backward_traj: bad sizes m=%d N=%d T=%d", m,
@@ -326,6 +363,10 @@ int slista_backward_traj(const float *B, int m, int N, float lam, const float *a
     SLISTA_REQUIRE(B && alpha && dalpha, SLISTA_ERR_ARG, "slista_backward_traj: B, alpha, dalpha must not be NULL");
     SLISTA_REQUIRE(N == 0 || (masks && traj), SLISTA_ERR_ARG, "slista_backward_traj: masks and traj must not be NULL");
     int rc = check_lam(lam);
+    if (rc) return rc;
+    rc = check_len(masks, mask_words, slista_mask_words(m, N, T), "slista_backward_traj", "masks", "words");
+    if (rc) return rc;
+    rc = check_len(traj, traj_floats, slista_traj_floats(m, N, T), "slista_backward_traj", "traj", "floats");
     if (rc) return rc;
     const size_t need = tc::backward_traj_ws_bytes(m, N, T);
     SLISTA_REQUIRE(ws_bytes >= need && ws != nullptr && ws_aligned(ws), SLISTA_ERR_WORKSPACE,
@@ -409,6 +450,15 @@ static int batch_args(const slista_problem_t *problems, int count, int T, int pr
         SLISTA_REQUIRE(!(q.lam < 0.0f) && !isnan(q.lam) && !isinf(q.lam), SLISTA_ERR_ARG,
                        "%s: problem %d: lam must be finite and >= 0", name, i);
         const bool needs_ck = ckpt_every < T;
+        char what[64];
+        snprintf(what, sizeof(what), "problem %d masks", i);
+        int rl = check_len(q.masks, q.mask_words, slista_mask_words(q.m, q.N, T), name, what, "words");
+        if (rl) return rl;
+        if (needs_ck) {
+            snprintf(what, sizeof(what), "problem %d ckpt", i);
+            rl = check_len(q.ckpt, q.ckpt_floats, slista_ckpt_floats(q.m, q.N, T, ckpt_every), name, what, "floats");
+            if (rl) return rl;
+        }
         if (bwd) {
             SLISTA_REQUIRE(q.dalpha, SLISTA_ERR_ARG, "%s: problem %d: dalpha must not be NULL", name, i);
             SLISTA_REQUIRE(q.N == 0 || (q.masks && (!needs_ck || q.ckpt)), SLISTA_ERR_ARG,

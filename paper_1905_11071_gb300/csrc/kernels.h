@@ -153,5 +153,8 @@ int launch_oista_step(const OistaStep &o, int prec, cudaStream_t st);
 
 // Device-side error flag (set by bounded waits that expire).
 int read_and_clear_device_flag(cudaStream_t st);
+namespace tc {
+int launch_wait_probe(long long limit_cycles, cudaStream_t st);
+}
 
 }  // namespace slista

@@ -51,6 +51,26 @@ int read_and_clear_device_flag(cudaStream_t st)
 
 namespace tc {
 
+// Failure-detection check: one thread waits, with the kernels' bounded wait,
+// on an mbarrier that nothing arrives at, so the wait expires after
+// `limit` cycles and raises the device flag exactly as an expired wait of a
+// layer kernel does (code 7).  No copy, MMA or tensor memory is involved.
+__global__ void wait_probe_kernel(long long limit)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        fence_mbar_init();
+        mbar_wait(smem_u32(&bar), 0, 7, limit);  // phase 0 never completes
+    }
+}
+
+int launch_wait_probe(long long limit_cycles, cudaStream_t st)
+{
+    wait_probe_kernel<<<1, 32, 0, st>>>(limit_cycles);
+    return check_launch("wait_probe_kernel");
+}
+
 // Every REFRESH layers (at the checkpoint layers instead when checkpoints are
 // written) the accumulator is rebuilt as g = c - B z rather than updated by the
 // step, which bounds the drift the split products accumulate (about 2e-6

@@ -39,13 +39,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 }
 
 // Bounded wait for the completion of phase `parity`; false (and the device
-// flag raised) if it does not complete within WAIT_LIMIT_CYCLES.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int code)
+// flag raised with `code`) if it does not complete within `limit` cycles
+// (WAIT_LIMIT_CYCLES by default).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int code,
+                                          long long limit = WAIT_LIMIT_CYCLES)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             atomicExch(&tc_flag, code);
             return false;
         }

@@ -76,54 +76,54 @@ def test_argument_validation_without_gpu(lib):
     assert lib.lasso_gram(vp, 0, 8, vp, 3, vp, vp, vp, None, None) == _lib.SLISTA_ERR_ARG
     # negative / NaN lambda
     for lam in (-1.0, float("nan"), float("inf")):
-        rc = lib.slista_forward(vp, vp, 8, 4, lam, vp, 3, 0, vp, None, None, 1, None, 0, None)
+        rc = lib.slista_forward(vp, vp, 8, 4, lam, vp, 3, 0, vp, None, 0, None, 0, 1, None, 0, None)
         assert rc == _lib.SLISTA_ERR_ARG, lam
         assert "lam" in _err(lib)
     # unknown precision and unbuilt TF32
-    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, 9, vp, None, None, 1, None, 0, None) == _lib.SLISTA_ERR_ARG
-    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_TF32, vp, None, None, 1, None, 0,
+    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, 9, vp, None, 0, None, 0, 1, None, 0, None) == _lib.SLISTA_ERR_ARG
+    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_TF32, vp, None, 0, None, 0, 1, None, 0,
                               None) == _lib.SLISTA_ERR_UNSUPPORTED
     # FP32 path limit
-    assert lib.slista_forward(vp, vp, 300, 4, 0.1, vp, 3, 0, vp, None, None, 1, None, 0,
+    assert lib.slista_forward(vp, vp, 300, 4, 0.1, vp, 3, 0, vp, None, 0, None, 0, 1, None, 0,
                               None) == _lib.SLISTA_ERR_UNSUPPORTED
     # checkpoint spacing
-    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, 0, vp, vp, vp, 0, None, 0, None) == _lib.SLISTA_ERR_ARG
+    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, 0, vp, vp, 1 << 40, vp, 1 << 40, 0, None, 0, None) == _lib.SLISTA_ERR_ARG
     # backward: workspace too small, missing checkpoints, precision
-    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, 0, vp, vp, 3, None, vp, None, 0,
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, 0, vp, 1 << 40, vp, 1 << 40, 3, None, vp, None, 0,
                                None) == _lib.SLISTA_ERR_WORKSPACE
-    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, 0, vp, None, 3, None, vp, vp, 1 << 30,
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, 0, vp, 1 << 40, None, 0, 3, None, vp, vp, 1 << 30,
                                None) == _lib.SLISTA_ERR_ARG
-    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_TF32, vp, vp, 3, None, vp, vp, 1 << 30,
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_TF32, vp, 1 << 40, vp, 1 << 40, 3, None, vp, vp, 1 << 30,
                                None) == _lib.SLISTA_ERR_UNSUPPORTED
-    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, 9, vp, vp, 3, None, vp, vp, 1 << 30,
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, 9, vp, 1 << 40, vp, 1 << 40, 3, None, vp, vp, 1 << 30,
                                None) == _lib.SLISTA_ERR_ARG
     # tensor-core adjoint: at most 256 layers per recompute segment, and its own workspace size
-    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 300, _lib.PREC_BF16X3, vp, None, 300, None, vp, vp, 1 << 30,
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 300, _lib.PREC_BF16X3, vp, 1 << 40, None, 0, 300, None, vp, vp, 1 << 30,
                                None) == _lib.SLISTA_ERR_UNSUPPORTED
     assert "256" in _err(lib)
     need = _lib.slista_workspace_bytes(_lib.FN_SLISTA_BWD, 8, 4, 10, _lib.PREC_BF16X3, 3)
     assert need >= 64 * 64 * 4 + 4 * 3 * 4 * 8
-    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_BF16X3, vp, vp, 3, None, vp, vp, need - 1,
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_BF16X3, vp, 1 << 40, vp, 1 << 40, 3, None, vp, vp, need - 1,
                                None) == _lib.SLISTA_ERR_WORKSPACE
     # a workspace off a 256-byte boundary (large enough) is refused before any launch
     odd = ctypes.c_void_p(0x1010)
-    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_BF16X3, vp, vp, 3, None, vp, odd, need,
+    assert lib.slista_backward(vp, vp, 8, 4, 0.1, vp, 10, _lib.PREC_BF16X3, vp, 1 << 40, vp, 1 << 40, 3, None, vp, odd, need,
                                None) == _lib.SLISTA_ERR_WORKSPACE
     assert "256-byte" in _err(lib)
-    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, None, None, 1, odd, 1 << 30,
+    assert lib.slista_forward(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, None, 0, None, 0, 1, odd, 1 << 30,
                               None) == _lib.SLISTA_ERR_WORKSPACE
     # one-pass backward: precision, width and depth limits, workspace
-    assert lib.slista_forward_traj(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_FP32, vp, vp, vp, odd, 1 << 30,
+    assert lib.slista_forward_traj(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_FP32, vp, vp, 1 << 40, vp, 1 << 40, odd, 1 << 30,
                                    None) == _lib.SLISTA_ERR_UNSUPPORTED
-    assert lib.slista_forward_traj(vp, vp, 300, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, vp, vp, odd, 1 << 30,
+    assert lib.slista_forward_traj(vp, vp, 300, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, vp, 1 << 40, vp, 1 << 40, odd, 1 << 30,
                                    None) == _lib.SLISTA_ERR_UNSUPPORTED
-    assert lib.slista_backward_traj(vp, 8, 4, 0.1, vp, 300, _lib.PREC_BF16X3, vp, vp, None, vp, odd, 1 << 30,
+    assert lib.slista_backward_traj(vp, 8, 4, 0.1, vp, 300, _lib.PREC_BF16X3, vp, 1 << 40, vp, 1 << 40, None, vp, odd, 1 << 30,
                                     None) == _lib.SLISTA_ERR_UNSUPPORTED
-    assert lib.slista_forward_traj(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, None, vp, odd, 1 << 30,
+    assert lib.slista_forward_traj(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, None, 0, vp, 1 << 40, odd, 1 << 30,
                                    None) == _lib.SLISTA_ERR_ARG
-    assert lib.slista_forward_traj(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, vp, vp, odd, 1 << 30,
+    assert lib.slista_forward_traj(vp, vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, vp, 1 << 40, vp, 1 << 40, odd, 1 << 30,
                                    None) == _lib.SLISTA_ERR_WORKSPACE
-    assert lib.slista_backward_traj(vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, vp, None, vp, odd, 1 << 30,
+    assert lib.slista_backward_traj(vp, 8, 4, 0.1, vp, 3, _lib.PREC_BF16X3, vp, 1 << 40, vp, 1 << 40, None, vp, odd, 1 << 30,
                                     None) == _lib.SLISTA_ERR_WORKSPACE
     assert _lib.slista_traj_floats(300, 4, 3) == 0 and _lib.slista_traj_floats(8, 4, 300) == 0
     # OISTA and objective null pointers
@@ -164,3 +164,60 @@ def test_support_lipschitz_binding_rejects_host_tensors(lib):
     with pytest.raises(ValueError, match="CUDA"):
         _lib.lasso_support_lipschitz(torch.zeros(40, 40), torch.zeros(5, 2, dtype=torch.int32),
                                      torch.ones(1, dtype=torch.float64), torch.zeros(5, dtype=torch.float64))
+
+
+def test_short_caller_buffers_are_refused_before_any_launch(lib):
+    """Masks, checkpoints and the trajectory are passed with their lengths;
+    a length one element short of slista_mask_words / slista_ckpt_floats /
+    slista_traj_floats returns SLISTA_ERR_WORKSPACE without touching the GPU
+    (the pointers below are never dereferenced).  A binding that under-sized
+    the trajectory of a 10^6-sample batch (a 32-bit truncation of
+    slista_traj_floats) once made the forward write past its end; the C ABI
+    now refuses such a buffer itself."""
+    vp = ctypes.c_void_p(1)
+    ws = ctypes.c_void_p(0x1000)  # 256-byte aligned, never dereferenced
+    m, N, T, K = 64, 100, 10, 3
+    mw = _lib.slista_mask_words(m, N, T)
+    cf = _lib.slista_ckpt_floats(m, N, T, K)
+    assert mw == T * N * 2 and cf == 2 * N * m * 3
+    P3 = _lib.PREC_BF16X3
+    big = 1 << 40
+    # forward: masks one word short, then checkpoints one float short
+    assert lib.slista_forward(vp, vp, m, N, 0.1, vp, T, P3, vp, vp, mw - 1, None, 0, 1, ws, big,
+                              None) == _lib.SLISTA_ERR_WORKSPACE
+    assert "masks" in _err(lib)
+    assert lib.slista_forward(vp, vp, m, N, 0.1, vp, T, P3, vp, vp, mw, vp, cf - 1, K, ws, big,
+                              None) == _lib.SLISTA_ERR_WORKSPACE
+    assert "ckpt" in _err(lib)
+    # the no-workspace forward checks its masks the same way
+    assert lib.slista_forward_noalloc(vp, vp, m, N, 0.1, vp, T, P3, vp, vp, mw - 1, None) == _lib.SLISTA_ERR_WORKSPACE
+    # backward
+    assert lib.slista_backward(vp, vp, m, N, 0.1, vp, T, P3, vp, mw - 1, vp, cf, K, None, vp, ws, big,
+                               None) == _lib.SLISTA_ERR_WORKSPACE
+    assert lib.slista_backward(vp, vp, m, N, 0.1, vp, T, P3, vp, mw, vp, cf - 1, K, None, vp, ws, big,
+                               None) == _lib.SLISTA_ERR_WORKSPACE
+    assert lib.slista_backward(vp, vp, m, N, 0.1, vp, T, 0, vp, mw, vp, cf - 1, K, None, vp, ws, big,
+                               None) == _lib.SLISTA_ERR_WORKSPACE
+    # one-pass forward / backward: the trajectory's length follows the
+    # device's tile layout, so it is queried and passed one float short
+    tf = _lib.slista_traj_floats(m, N, T)
+    assert tf >= (T + 1) * N * m
+    assert lib.slista_forward_traj(vp, vp, m, N, 0.1, vp, T, P3, vp, vp, mw, vp, tf - 1, ws, big,
+                                   None) == _lib.SLISTA_ERR_WORKSPACE
+    assert "traj" in _err(lib)
+    assert lib.slista_forward_traj(vp, vp, m, N, 0.1, vp, T, P3, vp, vp, mw - 1, vp, tf, ws, big,
+                                   None) == _lib.SLISTA_ERR_WORKSPACE
+    assert lib.slista_backward_traj(vp, m, N, 0.1, vp, T, P3, vp, mw, vp, tf - 1, None, vp, ws, big,
+                                    None) == _lib.SLISTA_ERR_WORKSPACE
+    assert lib.slista_backward_traj(vp, m, N, 0.1, vp, T, P3, vp, mw - 1, vp, tf, None, vp, ws, big,
+                                    None) == _lib.SLISTA_ERR_WORKSPACE
+    # ragged batches: per-problem lengths in the descriptor
+    arr = (_lib.Problem * 1)()
+    p = arr[0]
+    p.B, p.C, p.m, p.N, p.lam, p.alpha, p.Z = 1, 1, m, N, 0.1, 1, 1
+    p.masks, p.mask_words, p.ckpt, p.ckpt_floats = 1, mw - 1, 1, cf
+    assert lib.slista_forward_batched(arr, 1, T, P3, K, ws, big, None) == _lib.SLISTA_ERR_WORKSPACE
+    assert "problem 0 masks" in _err(lib)
+    p.mask_words, p.ckpt_floats = mw, cf - 1
+    assert lib.slista_forward_batched(arr, 1, T, P3, K, ws, big, None) == _lib.SLISTA_ERR_WORKSPACE
+    assert "problem 0 ckpt" in _err(lib)

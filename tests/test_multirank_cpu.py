@@ -33,7 +33,7 @@ def _worker(rank, world, port, out):
     val = bench.job_throughput(10000, world, got)
     w = synth.slista_64x256(seed=rank, N=16, T=2)
     args = type("A", (), {"N": 16, "T": 2, "cpu_samples": 1, "warmup": 0, "steps": 1, "prec": "bf16x3",
-                          "oista_prec": "bf16x3", "backward": "traj"})()
+                          "oista_prec": "bf16x3", "backward": "traj", "cpu_cores": 1})()
     ref = bench.run_reference(args, rank, world)
     out[rank] = (got, val, float(w.X[0, 0]), ref is None)
     dist.barrier()

@@ -351,6 +351,48 @@ def test_oista_monotone_and_safe_regime():
         assert abs(LS[i] - oracle.support_lipschitz(D, mask, L)) < 1e-12
 
 
+def test_oista_layer_margins_hand_case():
+    """The per-layer decision margin of Oracle-ISTA on a case worked by hand.
+    D = diag(2, 1) (L = 4; L_S = the largest d_j^2 on S; c = D^T x = (0.3, 0.6)),
+    x = (0.15, 0.6), lam = 0.5, z^(0) = 0:
+      layer 0: S empty, L_S = L = 4, u = c / 4 = (0.075, 0.15), threshold
+               0.125: the local step gives (0, 0.025), code 1 leaves S, so
+               condition (star) fails; margins |0.075 - 0.125| = 0.05 and
+               |0.15 - 0.125| = 0.025 -> 0.025; the ISTA step (same 1/4)
+               gives z^(1) = (0, 0.025).
+      layer 1: S = {1}, L_S = 1, gradient B z - c = (-0.3, -0.575),
+               u = (0.3, 0.6), threshold 0.5: the local step gives (0, 0.1),
+               inside S (accepted); margin off S |0.3 - 0.5| = 0.2, on the
+               step taken min(0.2, |0.6 - 0.5| = 0.1) -> 0.1; z^(2) = (0, 0.1).
+      layer 2: z^(2) is the Lasso solution (|c_0 - (Bz)_0| = 0.3 <= lam and
+               z_1 = ST(0.6, 0.5)); the same u, margin 0.1, accepted.
+    A margin that used L instead of L_S, skipped the codes on S of an
+    accepted step, or skipped the codes off S would differ."""
+    D = np.diag([2.0, 1.0])
+    X = np.array([[0.15, 0.6]])
+    Zall, LS, acc, dec, lm = oracle.oista(D, X, 0.5, 4.0, 4, keep_all=True, layer_margins=True)
+    np.testing.assert_allclose(lm[:, 0], [0.025, 0.1, 0.1, 0.1], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(dec[:, 0], [0, 1, 1, 1])
+    np.testing.assert_allclose(Zall[1, 0], [0.0, 0.025], atol=1e-15)
+    np.testing.assert_allclose(Zall[2, 0], [0.0, 0.1], atol=1e-15)
+    assert LS[0] == 1.0
+    # the per-sample trajectory margin is the smallest layer margin
+    _, _, _, _, mg = oracle.oista(D, X, 0.5, 4.0, 4, with_margin=True)
+    assert mg[0] == lm[:, 0].min()
+
+
+def test_oista_layer_margin_vanishes_at_a_tie():
+    """A code whose pre-threshold value sits exactly on its threshold has
+    margin 0 at that layer (D = I, L = L_S = 1, u = x at every layer, so the
+    margin is min_j ||x_j| - lam| at every layer)."""
+    x = np.array([[0.9, -0.5, 0.2, -1.25]])
+    _, _, _, _, lm = oracle.oista(np.eye(4), x, 0.5, 1.0, 3, layer_margins=True)
+    np.testing.assert_allclose(lm[:, 0], 0.0, atol=1e-15)
+    x2 = np.array([[0.9, -0.6, 0.2, -1.25]])
+    _, _, _, _, lm2 = oracle.oista(np.eye(4), x2, 0.5, 1.0, 3, layer_margins=True)
+    np.testing.assert_allclose(lm2[:, 0], 0.1, atol=1e-12)
+
+
 def _support_identification(Zall, zstar_support):
     """T* of Prop. 3.1: the first iteration from which every iterate has the
     support of z*."""
