@@ -203,7 +203,7 @@ int lasso_gram(const float *D, int n, int m, const float *X, int N, float *B, fl
     SLISTA_REQUIRE(N == 0 || (X && C && xsq), SLISTA_ERR_ARG, "lasso_gram: X, C, xsq must not be NULL");
     SLISTA_REQUIRE(m <= 1024, SLISTA_ERR_UNSUPPORTED, "lasso_gram: m <= 1024 supported (got %d)", m);
     cudaStream_t st = as_stream(stream);
-    int rc = gram::launch_gram(D, n, m, X, N, B, C, xsq, st);
+    int rc = tcg::launch_gram(D, n, m, X, N, B, C, xsq, st);
     if (rc) return rc;
     if (L) {
         if ((n <= m ? n : m) <= 128) return gram::launch_lipschitz_from_D(D, n, m, L, st);
@@ -425,6 +425,7 @@ int lasso_objective(const float *B, const float *C, const double *xsq, const flo
     int rc = check_lam(lam);
     if (rc) return rc;
     ObjArgs a{B, C, xsq, Z, m, N, lam, F, gap};
+    if (tcg::objective_supported(m)) return tcg::launch_objective(a, as_stream(stream));
     return simt::launch_objective(a, as_stream(stream));
 }
 

@@ -123,7 +123,7 @@ __device__ inline float tridiag_max_eig_warp(const float *d, const float *e, flo
 // dimension lda; with lda = vec_ld(k) and 16-byte aligned A and q the rows
 // are read as 16-byte vectors, and columns k .. 4 ceil(k/4) - 1 of A must then
 // hold finite values (zeros).  j0 replaces LANCZOS_J0 (j0 >= k: the full
-// dimension, at most LANCZOS_JMAX steps).
+// dimension, at most LANCZOS_JMAX steps) and dj LANCZOS_DJ.
 // q, qp: 4 ceil(k/4) floats; al, be, e2: LANCZOS_JMAX floats of warp scratch.
 // RPL = rows per lane (>= ceil(k / 32)).
 constexpr int LANCZOS_J0 = 10;
@@ -132,7 +132,7 @@ constexpr int LANCZOS_JMAX = 64;
 
 template <int RPL>
 __device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q, float *qp, float *al, float *be,
-                                       float *e2, int j0 = LANCZOS_J0)
+                                       float *e2, int j0 = LANCZOS_J0, int dj = LANCZOS_DJ)
 {
     constexpr int JMAX = LANCZOS_JMAX;
     const int lane = threadIdx.x & 31;
@@ -260,7 +260,7 @@ __device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q,
         theta = tridiag_max_eig_warp(al, be, e2, j, ref, theta + 2e-7f * fabsf(theta), &conv, &ref);
         if (done || conv) break;  // exhausted, or moved by less than 2e-7 since the last check
         if (j >= JMAX || j >= k) break;
-        target = min(min(j + LANCZOS_DJ, k), JMAX);
+        target = min(min(j + dj, k), JMAX);
     }
     return (double)theta;
 }

@@ -78,11 +78,18 @@ size_t support_ls_ws_bytes(int m, int N);
 }  // namespace simt
 
 namespace gram {
-int launch_gram(const float *D, int n, int m, const float *X, int N, float *B, float *C, double *xsq,
-                cudaStream_t st);
 int launch_lipschitz_from_D(const float *D, int n, int m, double *L, cudaStream_t st);
 int launch_lipschitz_from_B(const float *B, int m, double *L, cudaStream_t st);
 }  // namespace gram
+
+namespace tcg {
+// tcgen05 products with the FP32-class six-product BF16 split: B = D^T D,
+// C = X D and ||x||^2 (n >= 1, m <= 1024); the objective and gap (m <= 256).
+int launch_gram(const float *D, int n, int m, const float *X, int N, float *B, float *C, double *xsq,
+                cudaStream_t st);
+bool objective_supported(int m);
+int launch_objective(const ObjArgs &a, cudaStream_t st);
+}  // namespace tcg
 
 namespace tc {
 // tcgen05 forward (SLISTA_PREC_BF16 / SLISTA_PREC_BF16X3).

@@ -224,67 +224,10 @@ __global__ void reduce_partials_kernel(const float *__restrict__ partial, int nb
 //   F = xsq/2 - c.z + z.w/2 + lam |z|_1,  r2 = xsq - 2 c.z + z.w,
 //   xr = xsq - c.z,  s = min(1, lam / |c - w|_inf),  gap = F - (s xr - s^2 r2 / 2).
 // ---------------------------------------------------------------------------
-template <int MP, int NB>
-__global__ void __launch_bounds__(NT) objective_kernel(
-    const float *__restrict__ B, const float *__restrict__ C, const double *__restrict__ xsq,
-    const float *__restrict__ Z, int m, int N, float lam, double *__restrict__ F,
-    double *__restrict__ gap)
-{
-    using TL = Tile<MP, NB>;
-    extern __shared__ float4 smem4[];
-    float *A_s = reinterpret_cast<float *>(smem4);
-    float *B_s = A_s + TL::A_FLOATS;
-    const Idx<TL> ix;
-    const int row0 = blockIdx.x * NB;
-
-    float z[TL::RM][TL::RN], w[TL::RM][TL::RN];
-    load_rows<TL>(z, Z, row0, N, m, m);
-#pragma unroll
-    for (int i = 0; i < TL::RM; ++i)
-#pragma unroll
-        for (int j = 0; j < TL::RN; ++j) w[i][j] = 0.0f;
-    store_tile<TL>(A_s, z);
-    gemm_acc<TL>(w, A_s, TL::LDA, B, m, m, m, B_s);
-
-    float c[TL::RM][TL::RN];
-    load_rows<TL>(c, C, row0, N, m, m);
-#pragma unroll
-    for (int i = 0; i < TL::RM; ++i) {
-        double cz = 0.0, zw = 0.0, l1 = 0.0;
-        float cinf = 0.0f;
-#pragma unroll
-        for (int j = 0; j < TL::RN; ++j) {
-            cz = fma((double)c[i][j], (double)z[i][j], cz);
-            zw = fma((double)z[i][j], (double)w[i][j], zw);
-            l1 += (double)fabsf(z[i][j]);
-            cinf = fmaxf(cinf, fabsf(c[i][j] - w[i][j]));
-        }
-        // reduce over the TXN lanes that share this row
-#pragma unroll
-        for (int o = TL::TXN / 2; o > 0; o >>= 1) {
-            cz += __shfl_xor_sync(0xffffffffu, cz, o);
-            zw += __shfl_xor_sync(0xffffffffu, zw, o);
-            l1 += __shfl_xor_sync(0xffffffffu, l1, o);
-            cinf = fmaxf(cinf, __shfl_xor_sync(0xffffffffu, cinf, o));
-        }
-        const int r = row0 + ix.row(i);
-        if (ix.tx == 0 && r < N) {
-            const double xx = xsq[r];
-            const double Fv = 0.5 * xx - cz + 0.5 * zw + (double)lam * l1;
-            F[r] = Fv;
-            if (gap) {
-                const double r2 = xx - 2.0 * cz + zw;
-                const double xr = xx - cz;
-                const double s = (double)cinf > (double)lam ? (double)lam / (double)cinf : 1.0;
-                gap[r] = Fv - (s * xr - 0.5 * s * s * r2);
-            }
-        }
-    }
-}
 
 // Objective and gap for wide dictionaries (256 < m <= 1024): the sample
 // rows z (all m codes) sit in A_s, w = z B is formed 256 columns at a time
-// by the tile engine, and the per-row sums of objective_kernel accumulate
+// by the tile engine, and the per-row sums (c.z, z.w, |z|_1, |c - w|_inf) accumulate
 // over the column blocks in registers.
 template <int NB>
 __global__ void __launch_bounds__(NT) objective_wide_kernel(
@@ -418,19 +361,6 @@ size_t backward_ws_mp(int N, int T, int K)
     return sizeof(float) * ((size_t)K * grid * NB * MP + (size_t)T * grid);
 }
 
-template <int MP>
-int launch_objective_mp(const ObjArgs &a, cudaStream_t st)
-{
-    constexpr int NB = Choice<MP>::NB;
-    using TL = Tile<MP, NB>;
-    const size_t smem = (size_t)TL::SMEM_FLOATS * sizeof(float);
-    auto k = objective_kernel<MP, NB>;
-    SLISTA_CUDA_TRY(allow_smem(k, smem));
-    const int grid = ceil_div(a.N, NB);
-    if (grid == 0) return SLISTA_OK;
-    k<<<grid, NT, smem, st>>>(a.B, a.C, a.xsq, a.Z, a.m, a.N, a.lam, a.F, a.gap);
-    return check_launch("objective_kernel");
-}
 
 }  // namespace
 
@@ -476,14 +406,10 @@ size_t backward_ws_bytes(int m, int N, int T, int K)
     return 0;
 }
 
+// The objective for wide dictionaries (256 < m <= 1024); narrower ones run on
+// the tensor cores (tc_gemm.cu).
 int launch_objective(const ObjArgs &a, cudaStream_t st)
 {
-    switch (padded_mp(a.m)) {
-        case 32: return launch_objective_mp<32>(a, st);
-        case 64: return launch_objective_mp<64>(a, st);
-        case 128: return launch_objective_mp<128>(a, st);
-        case 256: return launch_objective_mp<256>(a, st);
-    }
     if (a.m <= 1024) {
         constexpr int NB = 32;
         const int lda = ((a.m + 15) / 16) * 16 + 4;

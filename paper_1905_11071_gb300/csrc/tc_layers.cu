@@ -616,8 +616,9 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
 {
     using CF = Cfg<MP, SPLIT>;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ float part_s[ADJ_KMAX];
-    __shared__ float red[CF::NT / 32];
+    // per-warp sums of dalpha_t over this CTA's tiles, reduced once at the end
+    // (a warp writes only its own column: no barrier per layer)
+    __shared__ float part_w[ADJ_KMAX][CF::NT / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, cbase = (warp >> 2) * CF::CW;
     const int N = p.N, m = p.m, TR = p.TR;
@@ -629,13 +630,15 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
     float *__restrict__ Gbuf = p.Gbuf;
     TcEngine<MP, SPLIT> E;
     E.init(smem_raw, p.Bsplit, blockIdx.x < ntiles);
-    for (int i = tid; i < ADJ_KMAX; i += CF::NT) part_s[i] = 0.0f;
-    __syncthreads();
+    if (lane == 0)
+        for (int t = 0; t < p.t1 - p.t0; ++t) part_w[t][warp] = 0.0f;
 
 #pragma unroll 1
     for (int tile = blockIdx.x; tile < ntiles && !E.failed; tile += gridDim.x) {
         const int row = tile * TR + quad * 32 + lane;
         const bool row_ok = (quad * 32 + lane < TR) && row < N;
+        // the warp's rows hold samples: its q and mask lines are worth prefetching
+        const bool quad_live = quad * 32 < TR && tile * TR + quad * 32 < N;
         float G[CF::CW];
         if (p.Ginit) {
 #pragma unroll
@@ -678,19 +681,12 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
                 store_split16(E, col0, hv);
             }
             tmem_st_wait();
-            // dalpha_t partial: block sum
+            // dalpha_t partial: warp sum into this warp's slot
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) red[warp] = part;
-            __syncthreads();
-            if (tid == 0) {
-                float sum = 0.0f;
-#pragma unroll
-                for (int w = 0; w < CF::NT / 32; ++w) sum += red[w];
-                part_s[t - p.t0] += sum;
-            }
+            if (lane == 0) part_w[t - p.t0][warp] += part;
             if (t == 0) break;  // G^(0) is not needed
-            if (t - 1 >= p.t0) {
+            if (t - 1 >= p.t0 && quad_live) {
                 // q_{t-1} of this warp's codes into L2 while the products run
                 // (one 128-byte line per code: the warp's 32 rows)
                 const float *qn = qbuf + lane_index<MP>(t - 1 - p.t0, p.ntiles, tile, quad, 0, 0);
@@ -717,7 +713,12 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
         E.tile_done();
     }
     __syncthreads();
-    for (int t = p.t0 + tid; t < p.t1; t += CF::NT) p.partial[(size_t)t * gridDim.x + blockIdx.x] = part_s[t - p.t0];
+    for (int t = p.t0 + tid; t < p.t1; t += CF::NT) {
+        float sum = 0.0f;  // the warps' sums in a fixed order
+#pragma unroll
+        for (int w = 0; w < CF::NT / 32; ++w) sum += part_w[t - p.t0][w];
+        p.partial[(size_t)t * gridDim.x + blockIdx.x] = sum;
+    }
     E.finish();
 }
 
