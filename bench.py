@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-legs", action="store_true", help="skip the Oracle-ISTA / FP32 ISTA / equal-gap legs")
+    p.add_argument("--no-tune", action="store_true",
+                   help="run the fixed schedule (--backward, tiles spread over the SMs) instead of the autotuned one")
     p.add_argument("--sweep", default="100000,1000000", help="batch sizes of the sweep lines ('' = none)")
     p.add_argument("--train-steps", type=int, default=30, help="step-size training steps of the equal-gap leg")
     p.add_argument("--cpu-samples", type=int, default=0, help="oracle sample size (0 = auto)")
@@ -145,19 +147,16 @@ def backward_mode(w, args) -> str:
 
 
 def arm_config(w, args, world: int) -> dict:
-    """The workload description shared by both arms of the benchmark."""
-    bm = backward_mode(w, args)
+    """The workload description shared by both arms of the benchmark (the
+    GPU arm's schedule - tile rows, backward mode - is reported beside it)."""
     return {"workload": "slista_64x256", "n": w.n, "m": w.m, "N_per_gpu": w.N, "T": w.T, "lam": w.lam,
-            "backward": bm,
-            "ckpt_every": (max(1, int(math.ceil(math.sqrt(max(w.T, 1))))) if bm == "ckpt" else None),
             "prec": args.prec, "oista_prec": args.oista_prec,
-            "step": ("gram+L -> slista fwd(masks,%s) -> objective+gap -> slista bwd" %
-                     ("trajectory" if bm == "traj" else "ckpt")),
+            "step": "gram+L -> slista fwd(masks, adjoint inputs) -> objective+gap -> slista bwd",
             "l2": "flushed between timed steps (write of 2x L2 size, untimed)",
             "parallelism": "dp%d" % world if world > 1 else "single"}
 
 
-TRAFFIC_KEYS = ("n", "m", "N_per_gpu", "T", "backward", "prec", "oista_prec")
+TRAFFIC_KEYS = ("n", "m", "N_per_gpu", "T", "backward", "tile_rows", "prec", "oista_prec")
 
 
 def recorded_traffic(part: str, config: dict):
@@ -246,7 +245,10 @@ def run_ours(args, rank, world, local_rank):
 
     parts = ["gram", "slista_fwd", "objective", "slista_bwd"]
     tc = args.prec in ("bf16", "bf16x3")
-    traj = backward_mode(w, args) == "traj"
+    schedule = choose_schedule(args, w, g0, alpha)
+    traj = schedule["backward"] == "traj"
+    K = schedule["ckpt_every"]
+    _lib.slista_set_tile_rows(schedule["tile_rows"])
     nseg = -(-T // K)
     launches_per_step = {
         "gram": 3,                                            # D^T D, X D (+ ||x||^2), L
@@ -381,8 +383,9 @@ def run_ours(args, rank, world, local_rank):
         rooflines[p]["share"] = per_part[p] / sum(per_part.values())
     dom = max(parts, key=lambda p: per_part[p])
     r = rooflines[dom]
+    traffic_cfg = dict(arm_config(w, args, world), backward=schedule["backward"], tile_rows=schedule["tile_rows"])
     roofline = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
-                "unit": r["unit"], "frac": r["frac"], "traffic": recorded_traffic(dom, arm_config(w, args, world)),
+                "unit": r["unit"], "frac": r["frac"], "traffic": recorded_traffic(dom, traffic_cfg),
                 "traffic_unit": "bytes per call (dram__bytes_read.sum + dram__bytes_write.sum, profiles/dram_traffic.json)",
                 "peak_source": r["peak_source"]}
 
@@ -391,18 +394,46 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else args.prec,
         "data": "synthetic (seeded; D 64x256 unit-norm Gaussian, x = D z0 + 0.01 noise)",
-        "config": arm_config(w, args, world),
+        "config": arm_config(w, args, world), "schedule": schedule,
         "clocks": clocks, "e2e": e2e,
         "gpu_launches": int(sum(launches_per_step.values()) * args.steps),
         "roofline": roofline, "parts": rooflines,
         "wall_s_timed_region": wall1 - wall0,
     }
 
+    _lib.slista_set_tile_rows(0)
     if not args.no_legs and rank == 0:
         out["legs"] = run_legs(args, w, D, X, alpha, timed, pk, pk_kind)
     if args.sweep and rank == 0:
-        out["sweep"] = run_sweep(args, timed, step, pk, pk_kind)
+        out["sweep"] = run_sweep(args, timed, pk, pk_kind)
     return out, w
+
+
+def default_schedule(w, args) -> dict:
+    """The fixed schedule: tiles spread over the SMs, the requested backward."""
+    bm = backward_mode(w, args)
+    return {"tile_rows": 0, "backward": bm,
+            "ckpt_every": w.T if bm == "traj" else max(1, int(math.ceil(math.sqrt(max(w.T, 1))))),
+            "tuned": False}
+
+
+def choose_schedule(args, w, g, alpha) -> dict:
+    """The autotuned schedule (tile rows, backward mode) for this workload on
+    this device, from the cache or timed now (before the timed region), with
+    the candidates' times; the fixed schedule with --no-tune or fp32."""
+    base = default_schedule(w, args)
+    if args.no_tune or args.prec not in ("bf16", "bf16x3"):
+        return base
+    from paper_1905_11071_gb300 import tune
+    best, tried = tune.tune(g.B, g.C, w.lam, alpha, prec=args.prec)
+    out = {"tile_rows": best.tile_rows, "backward": best.backward, "ckpt_every": best.ckpt_every,
+           "tuned": True, "tuned_ms": best.ms,
+           "candidates": [{"tile_rows": s.tile_rows, "backward": s.backward, "ckpt_every": s.ckpt_every,
+                           "ms": s.ms} for s in tried]}
+    fixed = [c for c in out["candidates"] if c["tile_rows"] == 0 and c["backward"] == base["backward"]
+             and c["ckpt_every"] == base["ckpt_every"]]
+    out["fixed_ms"] = fixed[0]["ms"] if fixed else None
+    return out
 
 
 def run_legs(args, w, D, X, alpha, timed, pk, pk_kind):
@@ -461,7 +492,62 @@ def run_legs(args, w, D, X, alpha, timed, pk, pk_kind):
         legs["equal_gap"] = equal_gap_leg(args, w, g, alpha, timed)
     except Exception as ex:  # reported, never silently dropped
         legs["equal_gap"] = {"error": repr(ex)}
+    # ---- the ragged batch of 64 problems, forward + backward, replayed as a CUDA graph
+    try:
+        legs["ragged_batch"] = ragged_leg(args, timed, pk, pk_kind)
+    except Exception as ex:
+        legs["ragged_batch"] = {"error": repr(ex)}
     return legs
+
+
+def ragged_leg(args, timed, pk, pk_kind):
+    """64 independent Lasso problems (n ~ U{32..128}, m = 4n, N ~ logU[100,
+    20000], lam = 0.1 lam_max each, T = 30), Step-LISTA forward and backward
+    (split BF16) through the persistent batch kernels - one forward launch,
+    one backward launch and its reduction, plus the B splits - captured once
+    in a CUDA graph and replayed."""
+    import torch
+    from paper_1905_11071_gb300 import api, synth
+    probs = synth.ragged_problems(seed=0)
+    T = probs[0].T
+    qs = []
+    for w in probs:
+        g = api.gram(torch.from_numpy(w.D).cuda(), torch.from_numpy(w.X).cuda())
+        a = (1.0 / g.L.double()).float().expand(T).contiguous()
+        qs.append({"B": g.B, "C": g.C, "lam": w.lam, "alpha": a})
+    prec = "bf16x3"
+
+    def run():
+        Zs, st, K = api.slista_batched(qs, prec=prec, keep_for_backward=True)
+        return api.slista_grad_batched(st, K, prec=prec)
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        run()
+    torch.cuda.synchronize()
+
+    def call(evs):
+        if evs is not None:
+            evs[0].record()
+        graph.replay()
+        if evs is not None:
+            evs[1].record()
+    _, ms = timed(call, 2, args.steps, 2)
+    N_tot = sum(w.N for w in probs)
+    flop = sum(2.0 * w.m * w.m * w.N * ((T - 1) + (2 * T - -(-T // api.default_ckpt_every(T))))
+               for w in probs) / 1e12
+    lb, lpk, lsrc = layer_peak(prec, pk, pk_kind)
+    e = roofline_entry(lb, flop, "TFLOP/s", lpk, lsrc, ms)
+    e.update({"samples": N_tot, "problems": len(probs), "T": T, "samples_per_s": N_tot / (ms / 1e3),
+              "m_range": [min(w.m for w in probs), max(w.m for w in probs)],
+              "N_range": [min(w.N for w in probs), max(w.N for w in probs)],
+              "launches_per_step": "B splits (one per problem, x2), 1 persistent forward, 1 persistent "
+                                   "backward, 1 reduction, 2 queue resets",
+              "note": "forward + backward (checkpoints every ceil(sqrt T) layers, recompute), CUDA-graph replay; "
+                      "work counted: forward T-1 products, backward recompute + adjoint"})
+    return e
 
 
 def equal_gap_leg(args, w, g, alpha, timed):
@@ -525,10 +611,11 @@ def equal_gap_leg(args, w, g, alpha, timed):
             "note": "steps trained on this batch; F* = F after %d FP32 ISTA layers" % T_ref}
 
 
-def run_sweep(args, timed, step, pk, pk_kind):
-    """The step (Gram, forward, objective, backward) at larger batches."""
+def run_sweep(args, timed, pk, pk_kind):
+    """The step (Gram, forward, objective, backward) at larger batches, each
+    with its own autotuned schedule."""
     import torch
-    from paper_1905_11071_gb300 import api, synth
+    from paper_1905_11071_gb300 import api, synth, _lib
     out = []
     for N in [int(x) for x in str(args.sweep).split(",") if x.strip()]:
         w = synth.slista_64x256(seed=0, N=N, T=args.T)
@@ -536,21 +623,42 @@ def run_sweep(args, timed, step, pk, pk_kind):
         X = torch.from_numpy(w.X).cuda()
         g0 = api.gram(D, X)
         alpha = (1.0 / g0.L.double()).float().expand(w.T).contiguous()
+        sched = choose_schedule(args, w, g0, alpha)
         del g0
+        _lib.slista_set_tile_rows(sched["tile_rows"])
+        traj = sched["backward"] == "traj"
+        K = sched["ckpt_every"]
 
         def fn(evs):
-            if evs is None:
-                step(D, X, alpha)
-                return
-            step(D, X, alpha, evs)
+            if evs is not None:
+                evs[0].record()
+            g = api.gram(D, X)
+            if evs is not None:
+                evs[1].record()
+            Z, st = api.slista(g.B, g.C, w.lam, alpha, prec=args.prec, keep_for_backward=True, ckpt_every=K,
+                               trajectory=traj)
+            if evs is not None:
+                evs[2].record()
+            api.objective(g.B, g.C, g.xsq, Z, w.lam)
+            if evs is not None:
+                evs[3].record()
+            api.slista_grad(g.B, g.C, w.lam, alpha, st, prec=args.prec)
+            if evs is not None:
+                evs[4].record()
         steps = max(3, min(args.steps, int(2e6 // N) + 3))
         seg, tot = timed(fn, 5, steps, 2)
+        _lib.slista_set_tile_rows(0)
         mm, T = float(w.m), w.T
-        traj = backward_mode(w, args) == "traj"
+        nseg = -(-T // K)
         lb, lpk, lsrc = layer_peak(args.prec, pk, pk_kind)
         fwd = roofline_entry(lb, 2 * mm * mm * (T if traj else T - 1) * N / 1e12, "TFLOP/s", lpk, lsrc, seg[1])
-        bwd = roofline_entry(lb, 2 * mm * mm * (T - 1) * N / 1e12, "TFLOP/s", lpk, lsrc, seg[3])
+        bwd = roofline_entry(lb, 2 * mm * mm * ((T - 1) if traj else (2 * T - nseg)) * N / 1e12, "TFLOP/s", lpk,
+                             lsrc, seg[3])
+        sched_short = {k: sched[k] for k in ("tile_rows", "backward", "ckpt_every", "tuned")}
+        if "fixed_ms" in sched:
+            sched_short.update(tuned_ms=sched["tuned_ms"], fixed_ms=sched["fixed_ms"])
         out.append({"N": N, "value": N / (tot / 1e3), "unit": UNIT, "ms_per_step": tot, "steps": steps,
+                    "schedule": sched_short,
                     "parts_ms": {"gram": seg[0], "slista_fwd": seg[1], "objective": seg[2], "slista_bwd": seg[3]},
                     "slista_fwd_frac": fwd["frac"], "slista_bwd_frac": bwd["frac"]})
         del D, X

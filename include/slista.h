@@ -106,6 +106,18 @@ SLISTA_API int slista_device_status(void *stream);
  * SLISTA_ERR_TIMEOUT and clears the flag.  Nothing else is touched. */
 SLISTA_API int slista_wait_probe(long long limit_cycles, void *stream);
 
+/* Tuning of the tensor-core layer kernels for m <= 256 (the paper has no
+ * counterpart): rows of the batch per tile of the persistent forward /
+ * adjoint kernels.  0 (the default) spreads the batch evenly over the SMs
+ * (ceil(N / (rounds x SMs)) rows, at most 128); 32 <= rows <= 128 fixes it.
+ * The tile layout decides the sizes of slista_traj_floats and of the
+ * backward workspaces, so a setting applies to buffers sized after it and
+ * must stay unchanged between a forward and the backward that reads its
+ * trajectory or checkpoints.  Process-wide; results do not depend on it
+ * (samples are independent).  slista_get_tile_rows returns the setting. */
+SLISTA_API int slista_set_tile_rows(int rows);
+SLISTA_API int slista_get_tile_rows(void);
+
 /* Bytes of scratch the call `fn` needs for these sizes (0 if none). */
 SLISTA_API size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_every);
 
@@ -218,10 +230,12 @@ SLISTA_API int slista_backward(const float *B, const float *C, int m, int N, flo
 /* ---- one-pass backward (tensor cores, m <= 256, 1 <= T <= 256) -----------
  *
  * The same sub-gradient as slista_backward without the recompute: the
- * forward also writes the adjoint's inputs, the trajectory
- *     q_t = g^(t) - lam sign(z^(t+1))  for t = 0 .. T-1,   dF/dz^(T)
- * (Eq. steprec and the adjoint of slista_backward), and the backward is a
- * single reverse sweep over them.  Memory for speed: the trajectory holds
+ * forward also writes the adjoint's inputs, the trajectory: for every layer
+ * t = 0 .. T-1 either
+ *     q_t = g^(t) - lam sign(z^(t+1))      (layers that rebuild g from C)
+ * or the step z^(t) - z^(t+1), which is -alpha_t q_t on the support of
+ * z^(t+1), the only codes the adjoint reads (Eq. steprec); then dF/dz^(T).
+ * The backward is a single reverse sweep over them.  Memory for speed: the trajectory holds
  * (T + 1) x N x m floats (plus tile padding) against the checkpoints'
  * ceil(T/K) - 1 pairs of N x m.
  *
@@ -328,6 +342,20 @@ SLISTA_API int oista_forward(const float *B, const float *C, const float *D, int
  * slista_workspace_bytes(SLISTA_FN_SUPPORT_LIPSCHITZ, m, N, 0, 0, 0). */
 SLISTA_API int lasso_support_lipschitz(const float *B, const float *D, int n, int m, int N, const uint32_t *S,
                                        const double *L, double *LS, void *ws, size_t ws_bytes, void *stream);
+
+/* Coupled LISTA (Eq. lista_layer, Section 4): T layers from z^(0) = 0,
+ *     z^(t+1) = ST(z^(t) - alpha_t W_t^T (D z^(t) - x), beta_t lam),
+ * with one n x m matrix W_t and two positive scalars per layer; W_t = D and
+ * alpha_t = beta_t = 1/L is ISTA.  D: n x m, X: N x n, W: T x n x m (layer t
+ * at W + t n m), alpha, beta: T floats, Z: N x m (out), all device memory.
+ * Each layer is two tensor-core products with the FP32-class split of the
+ * Gram products (R = Z D^T - X, then R W_t finished into the soft-threshold).
+ * ws: lista_workspace_bytes(n, m, N) bytes (the residual R, N x n floats).
+ * n, m <= 1024. */
+SLISTA_API size_t lista_workspace_bytes(int n, int m, int N);
+SLISTA_API int lista_forward(const float *D, int n, int m, const float *X, int N, const float *W,
+                             const float *alpha, const float *beta, float lam, int T, float *Z, void *ws,
+                             size_t ws_bytes, void *stream);
 
 /* Per-sample Lasso objective (Eq. lasso) evaluated from the Gram quantities,
  *     F_i = 1/2 xsq_i - c_i^T z_i + 1/2 z_i^T B z_i + lam ||z_i||_1,

@@ -12,5 +12,5 @@ from ._lib import (  # noqa: F401
     FN_GRAM, FN_ISTA, FN_SLISTA_FWD, FN_SLISTA_BWD, FN_OISTA, FN_OBJECTIVE,
     slista_last_error, slista_device_status, slista_workspace_bytes, slista_ckpt_floats,
     slista_mask_words, lasso_gram, lasso_lipschitz, ista_forward, slista_forward, slista_backward,
-    oista_forward, lasso_objective, slista_forward_noalloc,
+    oista_forward, lasso_objective, slista_forward_noalloc, lista_forward, lista_workspace_bytes,
 )

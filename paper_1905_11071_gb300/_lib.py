@@ -42,13 +42,14 @@ EXPORTS = [
     "slista_backward", "oista_forward", "lasso_objective", "slista_forward_noalloc",
     "slista_batched_workspace_bytes", "slista_forward_batched", "slista_backward_batched",
     "slista_traj_floats", "slista_forward_traj", "slista_backward_traj", "lasso_support_lipschitz",
-    "slista_wait_probe",
+    "slista_wait_probe", "lista_workspace_bytes", "lista_forward", "slista_set_tile_rows",
+    "slista_get_tile_rows",
 ]
 
 
 # entry points that return a size (size_t): every other one returns an int status
 SIZE_RETURNING = ("slista_workspace_bytes", "slista_ckpt_floats", "slista_mask_words",
-                  "slista_batched_workspace_bytes", "slista_traj_floats")
+                  "slista_batched_workspace_bytes", "slista_traj_floats", "lista_workspace_bytes")
 
 
 class Problem(ctypes.Structure):
@@ -87,6 +88,8 @@ def load(path: str = LIB_PATH):
         lib.slista_last_error.argtypes = []
         lib.slista_device_status.argtypes = [vp]
         lib.slista_wait_probe.argtypes = [ctypes.c_longlong, vp]
+        lib.slista_set_tile_rows.argtypes = [i]
+        lib.slista_get_tile_rows.argtypes = []
         lib.slista_workspace_bytes.restype = sz
         lib.slista_workspace_bytes.argtypes = [i, i, i, i, i, i]
         lib.slista_ckpt_floats.restype = sz
@@ -106,6 +109,9 @@ def load(path: str = LIB_PATH):
         lib.oista_forward.argtypes = [vp, vp, vp, i, i, i, f, vp, i, i, vp, vp, vp, vp, sz, vp]
         lib.lasso_objective.argtypes = [vp, vp, vp, vp, i, i, f, vp, vp, vp]
         lib.lasso_support_lipschitz.argtypes = [vp, vp, i, i, i, vp, vp, vp, vp, sz, vp]
+        lib.lista_workspace_bytes.restype = sz
+        lib.lista_workspace_bytes.argtypes = [i, i, i]
+        lib.lista_forward.argtypes = [vp, i, i, vp, i, vp, vp, vp, f, i, vp, vp, sz, vp]
         pp = ctypes.POINTER(Problem)
         lib.slista_batched_workspace_bytes.restype = sz
         lib.slista_batched_workspace_bytes.argtypes = [i, pp, i, i, i, i]
@@ -174,6 +180,15 @@ def slista_wait_probe(limit_cycles: int, stream=None) -> None:
     """Launches the bounded-wait check kernel (its wait expires after
     limit_cycles and raises the device flag)."""
     _check(load().slista_wait_probe(int(limit_cycles), _stream(stream)), "slista_wait_probe")
+
+
+def slista_set_tile_rows(rows: int) -> None:
+    """Rows per tile of the persistent layer kernels (0: even spread)."""
+    _check(load().slista_set_tile_rows(int(rows)), "slista_set_tile_rows")
+
+
+def slista_get_tile_rows() -> int:
+    return int(load().slista_get_tile_rows())
 
 
 def slista_workspace_bytes(fn: int, m: int, N: int, T: int, prec: int, ckpt_every: int = 1) -> int:
@@ -348,6 +363,27 @@ def lasso_support_lipschitz(B, S, L, LS, ws=None, D=None, stream=None) -> None:
     wsb = 0 if ws is None else ws.numel() * ws.element_size()
     _check(load().lasso_support_lipschitz(_ptr(B), _ptr(D), n, m, N, _ptr(S), _ptr(L), _ptr(LS), _ptr(ws), wsb,
                                           _stream(stream)), "lasso_support_lipschitz")
+
+
+def lista_workspace_bytes(n: int, m: int, N: int) -> int:
+    return int(load().lista_workspace_bytes(int(n), int(m), int(N)))
+
+
+def lista_forward(D, X, W, alpha, beta, lam, Z, ws=None, stream=None) -> None:
+    """Coupled LISTA layers (Eq. lista_layer): W is T x n x m."""
+    import torch
+    n, m = D.shape
+    N = X.shape[0]
+    T = alpha.shape[0]
+    _need(D, torch.float32, (n, m), "D")
+    _need(X, torch.float32, (N, n), "X")
+    _need(W, torch.float32, (T, n, m), "W")
+    _need(alpha, torch.float32, (T,), "alpha")
+    _need(beta, torch.float32, (T,), "beta")
+    _need(Z, torch.float32, (N, m), "Z")
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().lista_forward(_ptr(D), n, m, _ptr(X), N, _ptr(W), _ptr(alpha), _ptr(beta), float(lam), T,
+                                _ptr(Z), _ptr(ws), wsb, _stream(stream)), "lista_forward")
 
 
 def lasso_objective(B, C, xsq, Z, lam, F, gap=None, stream=None) -> None:

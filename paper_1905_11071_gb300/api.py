@@ -83,6 +83,7 @@ class ForwardState:
     ckpt: Optional[torch.Tensor]
     ckpt_every: int
     traj: Optional[torch.Tensor] = None
+    tile_rows: int = 0   # the layer kernels' tile setting the buffers were laid out for
 
 
 def slista(B, C, lam, alpha, prec="fp32", keep_for_backward: bool = False,
@@ -107,13 +108,13 @@ def slista(B, C, lam, alpha, prec="fp32", keep_for_backward: bool = False,
             raise ValueError("trajectory forward: m <= 256 and 1 <= T <= 256 on the tensor cores")
         traj = torch.empty((nt,), dtype=torch.float32, device=dev)
         _lib.slista_forward_traj(B, C, lam, alpha, p, Z, masks, traj, ws=ws, stream=stream)
-        return Z, ForwardState(masks, None, T, traj)
+        return Z, ForwardState(masks, None, T, traj, _lib.slista_get_tile_rows())
     K = ckpt_every or default_ckpt_every(T)
     masks = torch.empty((max(1, _lib.slista_mask_words(m, N, T)),), dtype=torch.int32, device=dev)
     nck = _lib.slista_ckpt_floats(m, N, T, K)
     ckpt = torch.empty((nck,), dtype=torch.float32, device=dev) if nck > 0 else None
     _lib.slista_forward(B, C, lam, alpha, p, Z, masks=masks, ckpt=ckpt, ckpt_every=K, ws=ws, stream=stream)
-    return Z, ForwardState(masks, ckpt, K)
+    return Z, ForwardState(masks, ckpt, K, None, _lib.slista_get_tile_rows())
 
 
 def slista_grad(B, C, lam, alpha, state: ForwardState, gZ=None, prec="fp32", stream=None) -> torch.Tensor:
@@ -121,6 +122,8 @@ def slista_grad(B, C, lam, alpha, state: ForwardState, gZ=None, prec="fp32", str
     N, m = C.shape
     T = alpha.shape[0]
     p = _prec(prec)
+    if state.tile_rows != _lib.slista_get_tile_rows():
+        raise ValueError("the layer kernels' tile setting changed between the forward and the backward")
     dalpha = torch.empty((T,), dtype=torch.float32, device=C.device)
     if state.traj is not None:
         ws = workspace(_lib.slista_workspace_bytes(_lib.FN_SLISTA_BWD_TRAJ, m, N, T, p, 1), C.device, "bwd")
@@ -209,6 +212,17 @@ def support_lipschitz(B, S, L, D=None, stream=None):
     ws = workspace(_lib.slista_workspace_bytes(_lib.FN_SUPPORT_LIPSCHITZ, m, N, 0, 0), B.device, "support_ls")
     _lib.lasso_support_lipschitz(B, S, L, LS, ws=ws, D=D, stream=stream)
     return LS
+
+
+def lista(D, X, W, alpha, beta, lam, stream=None) -> torch.Tensor:
+    """Coupled LISTA (Eq. lista_layer): T layers with per-layer (W_t, alpha_t,
+    beta_t); W is T x n x m.  Returns z^(T) (N x m)."""
+    n, m = D.shape
+    N = X.shape[0]
+    Z = torch.empty((N, m), dtype=torch.float32, device=D.device)
+    ws = workspace(_lib.lista_workspace_bytes(n, m, N), D.device, "lista")
+    _lib.lista_forward(D, X, W, alpha, beta, lam, Z, ws=ws, stream=stream)
+    return Z
 
 
 def objective(B, C, xsq, Z, lam, with_gap: bool = True, stream=None):

@@ -146,6 +146,16 @@ int slista_device_status(void *stream)
     return read_and_clear_device_flag(st);
 }
 
+int slista_set_tile_rows(int rows)
+{
+    clear_error();
+    SLISTA_REQUIRE(rows == 0 || (rows >= 32 && rows <= 128), SLISTA_ERR_ARG,
+                   "slista_set_tile_rows: 0 or 32 <= rows <= 128 (got %d)", rows);
+    return tc::set_tile_rows(rows);
+}
+
+int slista_get_tile_rows(void) { return tc::tile_rows(); }
+
 int slista_wait_probe(long long limit_cycles, void *stream)
 {
     clear_error();
@@ -396,6 +406,31 @@ int oista_forward(const float *B, const float *C, const float *D, int n, int m, 
     return simt::launch_oista(a, ws, as_stream(stream));
 }
 
+size_t lista_workspace_bytes(int n, int m, int N)
+{
+    if (n < 1 || m < 1 || N < 0) return 0;
+    return tcg::lista_ws_bytes(n, N);
+}
+
+int lista_forward(const float *D, int n, int m, const float *X, int N, const float *W, const float *alpha,
+                  const float *beta, float lam, int T, float *Z, void *ws, size_t ws_bytes, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(n >= 1 && m >= 1 && N >= 0 && T >= 0, SLISTA_ERR_ARG, "lista_forward: bad sizes n=%d m=%d N=%d T=%d",
+                   n, m, N, T);
+    SLISTA_REQUIRE(m <= 1024 && n <= 1024, SLISTA_ERR_UNSUPPORTED, "lista_forward: n, m <= 1024 supported");
+    SLISTA_REQUIRE(D && (T == 0 || (W && alpha && beta)), SLISTA_ERR_ARG,
+                   "lista_forward: D, W, alpha and beta must not be NULL");
+    SLISTA_REQUIRE(N == 0 || (X && Z), SLISTA_ERR_ARG, "lista_forward: X and Z must not be NULL");
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    const size_t need = tcg::lista_ws_bytes(n, N);
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
+                   "lista_forward: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
+    ListaArgs a{D, n, m, X, N, W, alpha, beta, lam, T, Z};
+    return tcg::launch_lista(a, ws, as_stream(stream));
+}
+
 int lasso_support_lipschitz(const float *B, const float *D, int n, int m, int N, const uint32_t *S, const double *L,
                             double *LS, void *ws, size_t ws_bytes, void *stream)
 {
@@ -496,8 +531,8 @@ size_t slista_batched_workspace_bytes(int fn, const slista_problem_t *problems, 
         v[i].N = problems[i].N;
         if (!tcw::supported(v[i].m) || v[i].N < 0) return 0;
     }
-    if (fn == SLISTA_FN_SLISTA_FWD) return tcw::forward_batch_ws_bytes(v.data(), count);
-    if (fn == SLISTA_FN_SLISTA_BWD && T >= 1) return tcw::backward_batch_ws_bytes(v.data(), count, T, ckpt_every);
+    if (fn == SLISTA_FN_SLISTA_FWD) return tcw::persist_forward_ws_bytes(v.data(), count);
+    if (fn == SLISTA_FN_SLISTA_BWD && T >= 1) return tcw::persist_backward_ws_bytes(v.data(), count, T, ckpt_every);
     return 0;
 }
 
@@ -508,10 +543,10 @@ int slista_forward_batched(const slista_problem_t *problems, int count, int T, i
     std::vector<tcw::Problem> v;
     int rc = batch_args(problems, count, T, prec, ckpt_every, false, v, "slista_forward_batched");
     if (rc) return rc;
-    const size_t need = tcw::forward_batch_ws_bytes(v.data(), count);
+    const size_t need = tcw::persist_forward_ws_bytes(v.data(), count);
     SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
                    "slista_forward_batched: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
-    return tcw::forward_batch(v.data(), count, T, ckpt_every, prec, ws, as_stream(stream));
+    return tcw::forward_batch_persist(v.data(), count, T, ckpt_every, prec, ws, as_stream(stream));
 }
 
 int slista_backward_batched(const slista_problem_t *problems, int count, int T, int prec, int ckpt_every, void *ws,
@@ -521,10 +556,10 @@ int slista_backward_batched(const slista_problem_t *problems, int count, int T, 
     std::vector<tcw::Problem> v;
     int rc = batch_args(problems, count, T, prec, ckpt_every, true, v, "slista_backward_batched");
     if (rc) return rc;
-    const size_t need = tcw::backward_batch_ws_bytes(v.data(), count, T, ckpt_every);
+    const size_t need = tcw::persist_backward_ws_bytes(v.data(), count, T, ckpt_every);
     SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
                    "slista_backward_batched: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
-    return tcw::backward_batch(v.data(), count, T, ckpt_every, prec, ws, as_stream(stream));
+    return tcw::backward_batch_persist(v.data(), count, T, ckpt_every, prec, ws, as_stream(stream));
 }
 
 }  // extern "C"

@@ -56,6 +56,18 @@ struct OistaArgs {
     int prec;            // SLISTA_PREC_FP32 (SIMT layers) or BF16 / BF16X3 (tensor-core layers)
 };
 
+struct ListaArgs {
+    const float *D;      // n x m
+    int n, m;
+    const float *X;      // N x n
+    int N;
+    const float *W;      // T x n x m, one matrix per layer
+    const float *alpha, *beta;  // T each (device)
+    float lam;
+    int T;
+    float *Z;            // N x m
+};
+
 struct SupportLsArgs {
     const float *B;
     const float *D;      // nullable: n x m dictionary, for supports larger than 64
@@ -89,6 +101,9 @@ int launch_gram(const float *D, int n, int m, const float *X, int N, float *B, f
                 cudaStream_t st);
 bool objective_supported(int m);
 int launch_objective(const ObjArgs &a, cudaStream_t st);
+// coupled LISTA layers (Eq. lista_layer): two products per layer
+size_t lista_ws_bytes(int n, int N);
+int launch_lista(const ListaArgs &a, void *ws, cudaStream_t st);
 }  // namespace tcg
 
 namespace tc {
@@ -101,6 +116,9 @@ size_t backward_ws_bytes(int m, int N, int T, int K);
 int launch_backward(const BwdArgs &a, int prec, void *ws, cudaStream_t st);
 int launch_forward_noalloc(const PgdArgs &a, int prec, cudaStream_t st);
 int noalloc_max_m();
+// rows per tile of the layer kernels (0: spread the batch evenly over the SMs)
+int set_tile_rows(int rows);
+int tile_rows();
 // One-pass backward: the forward writes the adjoint's inputs (the
 // trajectory, traj_floats() floats; 1 <= T <= 256), the backward is one
 // reverse sweep (gZ, if given, replaces dF/dz^(T)).
@@ -130,6 +148,11 @@ size_t forward_batch_ws_bytes(const Problem *P, int count);
 size_t backward_batch_ws_bytes(const Problem *P, int count, int T, int K);
 int forward_batch(const Problem *P, int count, int T, int K, int prec, void *ws, cudaStream_t st);
 int backward_batch(const Problem *P, int count, int T, int K, int prec, void *ws, cudaStream_t st);
+// the same through the persistent batch kernels (one launch per 64 problems)
+size_t persist_forward_ws_bytes(const Problem *P, int count);
+size_t persist_backward_ws_bytes(const Problem *P, int count, int T, int K);
+int forward_batch_persist(const Problem *P, int count, int T, int K, int prec, void *ws, cudaStream_t st);
+int backward_batch_persist(const Problem *P, int count, int T, int K, int prec, void *ws, cudaStream_t st);
 size_t forward_ws_bytes(int m, int N);
 int launch_forward(const PgdArgs &a, int prec, void *ws, cudaStream_t st);
 size_t backward_ws_bytes(int m, int N, int T, int K);

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(NT) pgd_forward_kernel(
             store_rows<TL>(base + plane, g, row0, N, m, m);
         }
         const float a = alpha ? __ldg(alpha + t) : a_const;
-        const float thr = a * lam;
+        const float thr = __fmul_rn(a, lam);
 #pragma unroll
         for (int i = 0; i < TL::RM; ++i)
 #pragma unroll
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(NT) slista_backward_kernel(
 #pragma unroll 1
             for (int t = t0; t < t1; ++t) {
                 const float a = __ldg(alpha + t);
-                const float thr = a * lam;
+                const float thr = __fmul_rn(a, lam);
                 float *qt = qbuf + (size_t)(t - t0) * npad * MP;
 #pragma unroll
                 for (int i = 0; i < TL::RM; ++i) {

@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(NT) oista_step_kernel(const float *__restrict_
         const bool live = r < N;
         const bool ok = live && ws.flag[r] == 0;
         const float a = ok ? (float)(1.0 / ws.LSv[r]) : aL;
-        const float thr = a * lam;
+        const float thr = __fmul_rn(a, lam);
 #pragma unroll
         for (int j = 0; j < TL::RN; ++j) {
             const float zn = soft_threshold(fmaf(a, g[i][j], z[i][j]), thr);

@@ -4,6 +4,10 @@
 //   GRAM_B :  B = D^T D        (rows and columns: codes, K = n; written symmetric)
 //   OBJ    :  W = Z B          (rows: samples, K = m, columns: codes), finished into
 //             F_i and the duality gap in the epilogue (Eq. lasso)
+//   RESID  :  R = Z D^T - X    (rows: samples, K = m, columns: atoms), the residual
+//             D z - x of a coupled LISTA layer (Eq. lista_layer)
+//   LSTEP  :  V = R W          (rows: samples, K = n, columns: codes), finished into
+//             z <- ST(z - alpha V, beta lam) in place (Eq. lista_layer)
 //
 // These products feed every layer (C), define the layers (B) or are the
 // final reductions (objective), so they are held to FP32 accuracy: each FP32
@@ -54,7 +58,12 @@ constexpr int T_A = 256;                      // A buffer b, part p: [T_A + 96 b
 constexpr int TMEM_COLS = 512;
 constexpr uint32_t IDESC = idesc_bf16(BM, BH);
 
-enum Mode { GRAM_C = 0, GRAM_B = 1, OBJ = 2 };
+enum Mode { GRAM_C = 0, GRAM_B = 1, OBJ = 2, RESID = 3, LSTEP = 4 };
+
+// Operand layouts: A(r, k) is row-major (rows x K) except for GRAM_B (A = D^T);
+// Bop(j, k) is row-major (ncol x K) for OBJ and RESID, else column access of
+// a K x ncol matrix.
+__host__ __device__ constexpr bool b_rowmajor(int mode) { return mode == OBJ || mode == RESID; }
 
 struct Params {
     const float *A;       // GRAM_C: X (rows x K); GRAM_B: D (K x rows, A(a, k) = D[k][a]); OBJ: Z (rows x K)
@@ -65,8 +74,13 @@ struct Params {
     double *xsq;          // GRAM_C: ||x_i||^2 (written by column block 0)
     const float *C;       // OBJ: correlations (rows x ncol)
     const double *xsq_in; // OBJ
-    float lam;            // OBJ
+    float lam;            // OBJ, LSTEP
     double *F, *gap;      // OBJ (gap nullable)
+    const float *Xsub;    // RESID: X (rows x ncol), subtracted
+    float *Zio;           // LSTEP: codes (rows x ncol), updated in place
+    const float *alpha;   // LSTEP: alpha_t = alpha[t], threshold beta[t] lam (device)
+    const float *beta;
+    int t;
 };
 
 // Compensated FP32 accumulation (an unevaluated sum hi + lo): the product
@@ -152,7 +166,7 @@ __device__ __forceinline__ void build_b(const Params &p, int hc0, int kc0, uint8
 #pragma unroll 1
     for (int u = tid; u < BH * BK / 8; u += NT) {
         int jr, ku;
-        if (MODE == OBJ) {  // Bop(j, k) = B[j][k]: eight threads share a 256-byte row segment
+        if (b_rowmajor(MODE)) {  // Bop(j, k) = B[j][k]: eight threads share a 256-byte row segment
             jr = u >> 3;
             ku = u & 7;
         } else {            // Bop(j, k) = D[k][j]: a warp reads 32 consecutive columns per row
@@ -161,7 +175,7 @@ __device__ __forceinline__ void build_b(const Params &p, int hc0, int kc0, uint8
         }
         const int j = hc0 + jr, k = kc0 + 8 * ku;
         float v[8];
-        if (MODE == OBJ) {
+        if (b_rowmajor(MODE)) {
             const float *src = p.Bsrc + (size_t)j * p.K + k;
             if (j < p.ncol && k + 8 <= p.K && (p.K & 3) == 0 && (reinterpret_cast<uintptr_t>(p.Bsrc) & 15) == 0) {
                 const float4 x0 = __ldg(reinterpret_cast<const float4 *>(src));
@@ -281,7 +295,23 @@ __global__ void __launch_bounds__(NT, 1) tc6_gemm_kernel(const Params p)
 #pragma unroll
             for (int j = 0; j < 16; ++j) w[j] += wq[j];
             const int j0 = hc0 + 32 * cg + 16 * pc;
-            if (MODE == GRAM_C) {
+            if (MODE == RESID && rok) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (j0 + j < p.ncol) w[j] -= __ldg(p.Xsub + (size_t)row * p.ncol + j0 + j);
+            }
+            if (MODE == LSTEP) {
+                if (rok) {
+                    const float step = __ldg(p.alpha + p.t), thr = __fmul_rn(__ldg(p.beta + p.t), p.lam);
+                    float *zp = p.Zio + (size_t)row * p.ncol + j0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j0 + j < p.ncol) {
+                            const float u = fmaf(-step, w[j], zp[j]);
+                            zp[j] = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
+                        }
+                }
+            } else if (MODE == GRAM_C || MODE == RESID) {
                 if (rok) {
                     float *dst = p.out + (size_t)row * p.ncol + j0;
                     if (j0 + 16 <= p.ncol && (p.ncol & 3) == 0 && (reinterpret_cast<uintptr_t>(p.out) & 15) == 0) {
@@ -309,11 +339,30 @@ __global__ void __launch_bounds__(NT, 1) tc6_gemm_kernel(const Params p)
                     }
                 }
             } else {  // OBJ
+                float zr[16], cr[16];
+                const float *zs = p.A + (size_t)row * p.K + j0;
+                const float *cs = p.C + (size_t)row * p.ncol + j0;
+                if (rok && j0 + 16 <= p.ncol && (p.ncol & 3) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(p.A) | reinterpret_cast<uintptr_t>(p.C)) & 15) == 0) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 a4 = __ldg(reinterpret_cast<const float4 *>(zs) + u);
+                        const float4 c4 = __ldg(reinterpret_cast<const float4 *>(cs) + u);
+                        zr[4 * u] = a4.x; zr[4 * u + 1] = a4.y; zr[4 * u + 2] = a4.z; zr[4 * u + 3] = a4.w;
+                        cr[4 * u] = c4.x; cr[4 * u + 1] = c4.y; cr[4 * u + 2] = c4.z; cr[4 * u + 3] = c4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const bool ok = rok && j0 + j < p.ncol;
+                        zr[j] = ok ? __ldg(zs + j) : 0.0f;
+                        cr[j] = ok ? __ldg(cs + j) : 0.0f;
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const bool ok = rok && j0 + j < p.ncol;
-                    const float z = ok ? __ldg(p.A + (size_t)row * p.K + j0 + j) : 0.0f;
-                    const float cc = ok ? __ldg(p.C + (size_t)row * p.ncol + j0 + j) : 0.0f;
+                    const float z = zr[j], cc = cr[j];
                     cz.add_prod(cc, z);
                     zw.add_prod(z, w[j]);
                     l1.add(fabsf(z));
@@ -439,6 +488,41 @@ int launch_objective(const ObjArgs &a, cudaStream_t st)
     p.F = a.F;
     p.gap = a.gap;
     return launch<OBJ>(p, st, "tc6_gemm_kernel (objective)");
+}
+
+size_t lista_ws_bytes(int n, int N) { return N > 0 ? (size_t)N * n * sizeof(float) + 256 : 0; }
+
+int launch_lista(const ListaArgs &a, void *ws, cudaStream_t st)
+{
+    if (a.N == 0) return SLISTA_OK;
+    SLISTA_CUDA_TRY(cudaMemsetAsync(a.Z, 0, sizeof(float) * (size_t)a.N * a.m, st));  // z^(0) = 0
+    float *R = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(ws) + 255) & ~(uintptr_t)255);
+    for (int t = 0; t < a.T; ++t) {
+        Params pr{};  // R = Z D^T - X  (the residual D z - x of every sample)
+        pr.A = a.Z;
+        pr.Bsrc = a.D;
+        pr.rows = a.N;
+        pr.K = a.m;
+        pr.ncol = a.n;
+        pr.out = R;
+        pr.Xsub = a.X;
+        int rc = launch<RESID>(pr, st, "tc6_gemm_kernel (LISTA residual)");
+        if (rc) return rc;
+        Params pl{};  // z <- ST(z - alpha_t (R W_t), beta_t lam)
+        pl.A = R;
+        pl.Bsrc = a.W + (size_t)t * a.n * a.m;
+        pl.rows = a.N;
+        pl.K = a.n;
+        pl.ncol = a.m;
+        pl.Zio = a.Z;
+        pl.alpha = a.alpha;
+        pl.beta = a.beta;
+        pl.lam = a.lam;
+        pl.t = t;
+        rc = launch<LSTEP>(pl, st, "tc6_gemm_kernel (LISTA step)");
+        if (rc) return rc;
+    }
+    return SLISTA_OK;
 }
 
 }  // namespace tcg

@@ -27,6 +27,7 @@
 // releasing its tensor memory.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -145,6 +146,7 @@ struct Cfg {
     static constexpr int NPC = CW / 16;
     static constexpr uint32_t IDESC = idesc_bf16(128, MP);
     static_assert(MP % 64 == 0 && MP <= 256, "MP must be 64, 128 or 256");
+    static_assert(NT > 96, "the issuing thread (96) must exist");
     static_assert(COLS_USED <= 512, "tensor memory");
 };
 
@@ -153,6 +155,11 @@ constexpr int ADJ_KMAX = 256;  // layers per recompute segment of the adjoint
 template <int MP, bool SPLIT>
 struct TcEngine {
     using CF = Cfg<MP, SPLIT>;
+    // The thread that initialises the barriers, streams B_lo and issues the
+    // products: lane 0 of warp 3, whose TMEM lanes 96..127 hold tile rows
+    // that are empty whenever a tile has at most 96 rows (the batch spread
+    // over the SMs), so the issuing warp has the least epilogue work.
+    static constexpr int ISSUER = 96;
     uint32_t tmem, lane_base, sB_u;  // sB_u: shared address of the operand area (1024-aligned)
     // producer state, one bit each: phase of bar_mma (0), of bar_full[s]
     // (1 + s) and bar_empty[s] (3 + s); a bulk copy into stage s not yet
@@ -162,7 +169,7 @@ struct TcEngine {
 
     __device__ __forceinline__ uint32_t bit(int i) const { return (bits >> i) & 1u; }
     __device__ __forceinline__ void flip(int i) { bits ^= 1u << i; }
-    // global address of B_lo (read by thread 0 only; kept in shared memory)
+    // global address of B_lo (read by the issuer only; kept in shared memory)
     __device__ __forceinline__ const uint8_t *lo_src() const
     {
         const uint8_t *g;
@@ -184,7 +191,7 @@ struct TcEngine {
         uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + CF::SMEM_OPER + 5 * 8);
         sB_u = smem_u32(smem);
         const int tid = threadIdx.x;
-        if (tid == 0) {
+        if (tid == ISSUER) {
             for (int i = 0; i < 5; ++i) mbar_init(bar(i), 1);
             fence_mbar_init();
             const uint8_t *g = Bsplit + CF::OPER;
@@ -205,7 +212,7 @@ struct TcEngine {
         lane_base = (uint32_t)(((tid >> 5) & 3) * 32) << 16;
         bits = 0u;
         failed = false;
-        if (CF::LO_STREAM && tid == 0 && work) {
+        if (CF::LO_STREAM && tid == ISSUER && work) {
             load_stage(0, 0);
             load_stage(1, 1);
         }
@@ -235,14 +242,23 @@ struct TcEngine {
     }
 
     // Every thread: publish the A operand written to tensor memory, then
-    // thread 0 issues D = [D +] A x B over all K (fresh: the first product
+    // the issuer issues D = [D +] A x B over all K (fresh: the first product
     // overwrites D) and every thread waits for it.  Returns false, uniformly,
     // if a bounded wait expired.
     __device__ __forceinline__ bool contract(bool fresh)
     {
+        contract_issue(fresh);
+        return contract_wait();
+    }
+
+    // The two halves of contract(): every thread publishes the A operand and
+    // the issuer issues the products; other work may run in between, as long as
+    // it writes neither the accumulator nor the A operand.
+    __device__ __forceinline__ void contract_issue(bool fresh)
+    {
         tc_fence_before();
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == ISSUER) {
             tc_fence_after();
             const uint32_t dG = tmem + CF::T_G;
             uint32_t acc = fresh ? 0u : 1u;
@@ -290,10 +306,14 @@ struct TcEngine {
             }
             mma_commit(bar_mma());
         }
+    }
+
+    __device__ __forceinline__ bool contract_wait()
+    {
         const bool ok = mbar_wait(bar_mma(), bit(0), 1);
         flip(0);
         tc_fence_after();
-        if (CF::LO_STREAM && threadIdx.x == 0 && ok && !failed) {
+        if (CF::LO_STREAM && threadIdx.x == ISSUER && ok && !failed) {
             // every product is done: both stages are free, prefetch chunks 0 and 1
             load_stage(0, 0);
             load_stage(1, 1);
@@ -313,7 +333,7 @@ struct TcEngine {
     // Drain outstanding bulk copies, release tensor memory.
     __device__ __forceinline__ void finish()
     {
-        if (CF::LO_STREAM && threadIdx.x == 0)
+        if (CF::LO_STREAM && threadIdx.x == ISSUER)
             for (int s = 0; s < 2; ++s)
                 if (bit(5 + s)) wait_stage(s, 5);
         tc_fence_before();
@@ -418,6 +438,7 @@ struct TcParams {
     int want_gT;          // recompute: form G_T after the last layer
     float *partial;       // T x gridDim.x per-CTA sums of dalpha
     const float *Ginit;   // adjoint: initial G row-major (N x m) instead of Gbuf (nullable)
+    int traj_steps;       // adjoint over a trajectory: slot t holds a_t unless layer t refreshed
 };
 
 // ---------------------------------------------------------------------------
@@ -483,7 +504,7 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
 #pragma unroll 1
         for (int t = tb; t < te; ++t) {
             const float a = alpha ? __ldg(alpha + t) : a_const;
-            const float thr = a * lam;
+            const float thr = __fmul_rn(a, lam);
             if constexpr (!RECOMP) {
                 if (ckpt && t > 0 && t % p.K == 0) {
                     // checkpoint (z^(t), g^(t)) every K layers, layout of slista_forward
@@ -532,7 +553,12 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
                 }
                 if (pc & 1) word = 0u;
             }
-            if constexpr (WRITE_Q) {
+            // trajectory slot t (KM_TRAJ): on layers without a refresh the step
+            // a_t = z^(t) - z^(t+1), read back from the A operand while the
+            // products run (on the support of z^(t+1), q_t = -a_t / alpha_t);
+            // on refresh layers, and in the recompute, q_t itself, before them
+            const bool step_slot = KM == KM_TRAJ && !refresh;
+            if (WRITE_Q && !step_slot) {
                 // q_t = g^(t) - lam sign(z^(t+1)) in a second pass over the
                 // accumulator (still g^(t)), off the first pass's register
                 // budget; every lane takes part in the (warp-wide) loads
@@ -546,7 +572,8 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const float zn = z[16 * pc + j];
-                            if (col0 + j < m)
+                            // the adjoint reads q_t only on the support of z^(t+1)
+                            if (col0 + j < m && zn != 0.0f)
                                 qt[(size_t)(col0 + j) * 32] = gv[j] - lam * (float)((zn > 0.0f) - (zn < 0.0f));
                         }
                 }
@@ -559,7 +586,44 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_pgd_forward_kernel(c
             tmem_st_wait();
             if (!contract_after) break;
             // --- contraction g += a B on the tensor cores
-            if (!E.contract(false)) break;
+            E.contract_issue(false);
+            if (step_slot) {
+                // only codes in the support of z^(t+1) are written: the adjoint reads no others
+                float *qt = p.qbuf + lane_index<MP>(t - tb, p.ntiles, tile, quad, 0, lane);
+#pragma unroll 1
+                for (int pc = 0; pc < CF::NPC; ++pc) {
+                    const int col0 = cbase + 16 * pc;
+                    // support bits of these codes: the mask word this thread just stored
+                    // (read back through the coherent path, off the register budget)
+                    uint32_t wd = 0u;
+                    if (row_ok && col0 < m) wd = p.masks[((size_t)t * N + row) * W + (col0 >> 5)] >> (col0 & 31);
+                    uint32_t hv[8], lv[8];
+                    tmem_ld8(E.taddr(CF::T_AHI + col0 / 2), hv);
+                    if (SPLIT) tmem_ld8(E.taddr(CF::T_ALO + col0 / 2), lv);
+                    if (row_ok)
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hv[jj]));
+                            float2 a2 = h;
+                            if (SPLIT) {
+                                const float2 l = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&lv[jj]));
+                                a2.x += l.x;
+                                a2.y += l.y;
+                            }
+                            if ((wd >> (2 * jj)) & 1u) qt[(size_t)(col0 + 2 * jj) * 32] = a2.x;
+                            if ((wd >> (2 * jj + 1)) & 1u) qt[(size_t)(col0 + 2 * jj + 1) * 32] = a2.y;
+                        }
+                }
+            }
+            {
+                // this tile's rows of C into L2 before a refresh layer reloads them
+                const bool refresh_next = ckpt ? ((t + 2) % p.K == 0) : ((t + 2) % REFRESH == 0);
+                if (refresh_next && row_ok && !last)
+#pragma unroll
+                    for (int c = 0; c < CF::CW; c += 32)
+                        if (cbase + c < m) prefetch_l2(Cg + (size_t)row * m + cbase + c);
+            }
+            if (!E.contract_wait()) break;
             if constexpr (WRITE_Q) {
                 if (last) {
                     // G_T = gZ, or dF/dz^(T) = B z - c + lam sign(z) = -g + lam sign(z); the
@@ -619,6 +683,10 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
     // per-warp sums of dalpha_t over this CTA's tiles, reduced once at the end
     // (a warp writes only its own column: no barrier per layer)
     __shared__ float part_w[ADJ_KMAX][CF::NT / 32];
+    // this thread's support words of the next layer, copied in (cp.async) while
+    // the current layer's products run; double-buffered by layer parity
+    constexpr int NW = CF::CW / 32;
+    __shared__ uint32_t s_mw[2][CF::NT][NW];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, cbase = (warp >> 2) * CF::CW;
     const int N = p.N, m = p.m, TR = p.TR;
@@ -626,7 +694,7 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
     const int W = (m + 31) / 32;
     const float *__restrict__ alpha = p.alpha;
     const uint32_t *__restrict__ masks = p.masks;
-    const float *__restrict__ qbuf = p.qbuf;
+    const float *__restrict__ qbuf = p.qbuf;  // q_t, or (trajectory) the step a_t on layers without a refresh
     float *__restrict__ Gbuf = p.Gbuf;
     TcEngine<MP, SPLIT> E;
     E.init(smem_raw, p.Bsplit, blockIdx.x < ntiles);
@@ -639,6 +707,16 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
         const bool row_ok = (quad * 32 + lane < TR) && row < N;
         // the warp's rows hold samples: its q and mask lines are worth prefetching
         const bool quad_live = quad * 32 < TR && tile * TR + quad * 32 < N;
+        auto fetch_masks = [&](int tt) {
+            if (row_ok) {
+#pragma unroll
+                for (int i = 0; i < NW; ++i)
+                    if (cbase + 32 * i < m)
+                        cp_async4(smem_u32(&s_mw[tt & 1][tid][i]), masks + ((size_t)tt * N + row) * W + ((cbase >> 5) + i));
+            }
+            cp_async_commit();
+        };
+        fetch_masks(p.t1 - 1);
         float G[CF::CW];
         if (p.Ginit) {
 #pragma unroll
@@ -659,14 +737,18 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
             const float a = __ldg(alpha + t);
             const float *qt = qbuf + lane_index<MP>(t - p.t0, p.ntiles, tile, quad, 0, lane);  // + 32 per code
             float part = 0.0f;
+            cp_async_wait_all();  // this layer's support words have landed
+            uint32_t mw[NW];
+#pragma unroll
+            for (int i = 0; i < NW; ++i) mw[i] = s_mw[t & 1][tid][i];
+            if (t - 1 >= p.t0) fetch_masks(t - 1);  // in flight during this layer
 #pragma unroll
             for (int pc = 0; pc < CF::NPC; ++pc) {
                 const int col0 = cbase + 16 * pc;
                 if ((pc & 1) == 0) {
                     // mask bits of code columns col0 .. col0+31 (zero past m)
                     const uint32_t valid = col0 + 32 <= m ? 0xffffffffu : col0 < m ? (1u << (m - col0)) - 1u : 0u;
-                    const uint32_t word =
-                        (row_ok && valid) ? __ldg(masks + ((size_t)t * N + row) * W + (col0 >> 5)) & valid : 0u;
+                    const uint32_t word = (row_ok && valid) ? mw[pc >> 1] & valid : 0u;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) G[16 * pc + j] = ((word >> j) & 1u) ? G[16 * pc + j] : 0.0f;  // h
                     // <h, q_t> over these 32 columns (h = 0 off the support, past m and past N);
@@ -684,7 +766,9 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
             // dalpha_t partial: warp sum into this warp's slot
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) part_w[t - p.t0][warp] += part;
+            // a trajectory slot holding the step a_t: q_t = -a_t / alpha_t on the support
+            const bool step_slot = p.traj_steps && (t + 1) % REFRESH != 0;
+            if (lane == 0) part_w[t - p.t0][warp] += step_slot ? -part / a : part;
             if (t == 0) break;  // G^(0) is not needed
             if (t - 1 >= p.t0 && quad_live) {
                 // q_{t-1} of this warp's codes into L2 while the products run
@@ -692,7 +776,6 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
                 const float *qn = qbuf + lane_index<MP>(t - 1 - p.t0, p.ntiles, tile, quad, 0, 0);
 #pragma unroll
                 for (int c = lane; c < CF::CW; c += 32) prefetch_l2(qn + (size_t)(cbase + c) * 32);
-                if (row_ok) prefetch_l2(masks + ((size_t)(t - 1) * N + row) * W + (cbase >> 5));
             }
             // --- B h on the tensor cores, then G = h - alpha_t B h
             if (!E.contract(true)) break;
@@ -735,6 +818,8 @@ __global__ void tc_reduce_partials_kernel(const float *__restrict__ partial, int
     if (lane == 0) dalpha[t] = (float)s;
 }
 
+std::atomic<int> g_tile_rows{0};
+
 namespace {
 
 int mp_for(int m)
@@ -747,11 +832,17 @@ int mp_for(int m)
 
 // Tiles sized to keep every SM busy: a layer costs the same for a partial
 // tile as for 128 rows, so rows are spread evenly over rounds x SMs tiles.
+// (rows per tile chosen by slista_set_tile_rows, 0: the even spread above)
 void tiling(int N, int *TR, int *grid)
 {
     const int sms = num_sms();
-    const int rounds = ceil_div(ceil_div(N, 128), sms);
-    *TR = N > 0 ? ceil_div(N, (long long)rounds * sms) : 128;
+    const int fixed = g_tile_rows.load(std::memory_order_relaxed);
+    if (fixed > 0) {
+        *TR = fixed;
+    } else {
+        const int rounds = ceil_div(ceil_div(N, 128), sms);
+        *TR = N > 0 ? ceil_div(N, (long long)rounds * sms) : 128;
+    }
     const int ntiles = N > 0 ? ceil_div(N, *TR) : 0;
     *grid = ntiles < sms ? ntiles : sms;
 }
@@ -943,6 +1034,7 @@ int launch_backward_traj_mp(const BwdArgs &a, const float *traj, void *ws, cudaS
     p.Gbuf = const_cast<float *>(traj) + (size_t)a.T * tileset;  // read only: one segment
     p.Ginit = a.gZ;
     p.partial = partial;
+    p.traj_steps = 1;
     p.t0 = 0;
     p.t1 = a.T;
     auto ka = tc_adjoint_kernel<MP, SPLIT>;
@@ -1058,6 +1150,14 @@ void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 }  // namespace
 
 int noalloc_max_m() { return NOALLOC_MAX_M; }
+
+int set_tile_rows(int rows)
+{
+    g_tile_rows.store(rows, std::memory_order_relaxed);
+    return SLISTA_OK;
+}
+
+int tile_rows() { return g_tile_rows.load(std::memory_order_relaxed); }
 
 int launch_forward_noalloc(const PgdArgs &a, int prec, cudaStream_t st)
 {

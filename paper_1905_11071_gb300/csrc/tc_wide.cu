@@ -98,6 +98,7 @@ struct WLayer {
     int *accepted;            // accepted steps at this layer (nullable)
     double *LS_out;           // last layer: L_S per sample (nullable)
     int want_ls, listN, last;
+    int coherent;             // the state was written by this launch: load it through L2 only
 };
 
 template <int NP>
@@ -111,15 +112,22 @@ __host__ __device__ inline int n_colblocks(int m) { return (m + BN - 1) / BN; }
 __host__ __device__ inline int n_kchunks(int m) { return (m + BK - 1) / BK; }
 inline int n_items(int m, int N, int TR = 0) { return ceil_div(N, TR > 0 ? TR : BM) * n_colblocks(m); }
 
+// Loads through the read-only path, or (coh) through L2 only: state written
+// earlier by the same launch (the persistent batch kernels) must not come
+// from the non-coherent cache.
+__device__ __forceinline__ float4 ld4(const float4 *p, bool coh) { return coh ? __ldcg(p) : __ldg(p); }
+__device__ __forceinline__ float ld1(const float *p, bool coh) { return coh ? __ldcg(p) : __ldg(p); }
+
 // 16 consecutive entries (columns k0..k0+15) of row `row` of an N x m FP32
 // matrix, zero outside the matrix or when M is null.
-__device__ __forceinline__ void load16(const float *__restrict__ M, int row, bool ok, int m, int k0, float (&v)[16])
+__device__ __forceinline__ void load16(const float *__restrict__ M, int row, bool ok, int m, int k0, float (&v)[16],
+                                       bool coh = false)
 {
     if (M != nullptr && ok && (m & 3) == 0 && (reinterpret_cast<uintptr_t>(M) & 15) == 0) {
         const float4 *src = reinterpret_cast<const float4 *>(M + (size_t)row * m + k0);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float4 x = k0 + 4 * q < m ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 x = k0 + 4 * q < m ? ld4(src + q, coh) : make_float4(0.f, 0.f, 0.f, 0.f);
             v[4 * q + 0] = x.x;
             v[4 * q + 1] = x.y;
             v[4 * q + 2] = x.z;
@@ -128,7 +136,7 @@ __device__ __forceinline__ void load16(const float *__restrict__ M, int row, boo
     } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-            v[j] = (M != nullptr && ok && k0 + j < m) ? __ldg(M + (size_t)row * m + k0 + j) : 0.0f;
+            v[j] = (M != nullptr && ok && k0 + j < m) ? ld1(M + (size_t)row * m + k0 + j, coh) : 0.0f;
     }
 }
 
@@ -196,7 +204,7 @@ __device__ __forceinline__ bool stage_vec(const float *M0, const float *M1, int 
 template <int NM>
 __device__ __forceinline__ void stage_load(float4 (&x0)[SPER], float4 (&x1)[SPER], const float *__restrict__ M0,
                                            const float *__restrict__ M1, int row0, int cs, int m, int N, int TR,
-                                           int tid)
+                                           int tid, bool coh)
 {
 #pragma unroll
     for (int k = 0; k < SPER; ++k) {
@@ -204,9 +212,9 @@ __device__ __forceinline__ void stage_load(float4 (&x0)[SPER], float4 (&x1)[SPER
         const int gr = row0 + r, gc = cs + c;
         const bool ok = r < TR && gr < N && gc < m;
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-        x0[k] = (ok && M0 != nullptr) ? __ldg(reinterpret_cast<const float4 *>(M0 + (size_t)gr * m + gc)) : zero;
+        x0[k] = (ok && M0 != nullptr) ? ld4(reinterpret_cast<const float4 *>(M0 + (size_t)gr * m + gc), coh) : zero;
         if (NM == 2)
-            x1[k] = (ok && M1 != nullptr) ? __ldg(reinterpret_cast<const float4 *>(M1 + (size_t)gr * m + gc)) : zero;
+            x1[k] = (ok && M1 != nullptr) ? ld4(reinterpret_cast<const float4 *>(M1 + (size_t)gr * m + gc), coh) : zero;
     }
 }
 
@@ -224,11 +232,12 @@ __device__ __forceinline__ void stage_store(const float4 (&x0)[SPER], const floa
 
 template <int NM>
 __device__ __forceinline__ void stage_in(float *t0, const float *__restrict__ M0, float *t1,
-                                         const float *__restrict__ M1, int row0, int cs, int m, int N, int TR, int tid)
+                                         const float *__restrict__ M1, int row0, int cs, int m, int N, int TR, int tid,
+                                         bool coh = false)
 {
     if (stage_vec<NM>(M0, M1, m)) {
         float4 x0[SPER], x1[SPER];
-        stage_load<NM>(x0, x1, M0, M1, row0, cs, m, N, TR, tid);
+        stage_load<NM>(x0, x1, M0, M1, row0, cs, m, N, TR, tid, coh);
         stage_store<NM>(x0, x1, t0, t1, tid);
         return;
     }
@@ -237,8 +246,8 @@ __device__ __forceinline__ void stage_in(float *t0, const float *__restrict__ M0
         const int r = e / SW, c = e % SW;
         const int gr = row0 + r, gc = cs + c;
         const bool ok = r < TR && gr < N && gc < m;
-        t0[sidx(r, c)] = (ok && M0 != nullptr) ? __ldg(M0 + (size_t)gr * m + gc) : 0.0f;
-        if (NM == 2) t1[sidx(r, c)] = (ok && M1 != nullptr) ? __ldg(M1 + (size_t)gr * m + gc) : 0.0f;
+        t0[sidx(r, c)] = (ok && M0 != nullptr) ? ld1(M0 + (size_t)gr * m + gc, coh) : 0.0f;
+        if (NM == 2) t1[sidx(r, c)] = (ok && M1 != nullptr) ? ld1(M1 + (size_t)gr * m + gc, coh) : 0.0f;
     }
 }
 
@@ -289,58 +298,88 @@ __global__ void split_tiles_kernel(const float *__restrict__ B, int m, uint8_t *
 }
 
 // ---------------------------------------------------------------------------
-// The layer kernel.
+// The layer block: one (row tile, column block) of one layer.  A CTA may run
+// many of them (the persistent batch kernels); the barriers, the tensor
+// memory and the mbarrier phases persist across them in WRes.
 // ---------------------------------------------------------------------------
-template <bool SPLIT, int MODE, int NP>
-__global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant__ WBatch<NP> P)
+struct WRes {
+    uint8_t *smem;     // 1024-aligned dynamic shared memory (the two stages / epilogue slices)
+    uint32_t sbase;    // its shared address
+    uint32_t full0;    // full[2]: a stage's B tile landed
+    uint32_t done0;    // done[2]: the MMAs reading a stage retired
+    uint32_t tmem;     // the 128 x 256 FP32 accumulator
+    uint32_t fph;      // thread 0: parity of the next phase of full[s] (bit s)
+    uint32_t pend;     // thread 0: bulk copies into stage s not waited for (bit s)
+    uint32_t dph;      // every thread: parity of the next phase of done[s] (bit s)
+};
+
+// Barriers and tensor memory of a CTA (every thread).
+__device__ __forceinline__ void wres_init(WRes &R, uint8_t *smem_raw, uint64_t *bars, uint32_t *tmem_slot)
 {
-    using CF = WCfg<SPLIT>;
-    extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bars[4];  // full[2] (B tile landed), done[2] (MMAs of the stage retired)
-    __shared__ uint32_t tmem_slot;
-    __shared__ float red[NT / 32];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-    int p = 0;
-    while (p + 1 < P.nprob && (int)blockIdx.x >= P.base[p + 1]) ++p;
-    const WLayer &L = P.L[p];
-    const int m = L.m, N = L.N;
-    const int ncb = n_colblocks(m), nkc = n_kchunks(m);
-    const int local = (int)blockIdx.x - P.base[p];
-    const int TR = L.TR > 0 ? L.TR : BM;  // rows of this tile that are real (the MMA always spans 128)
-    const int row0 = (local / ncb) * TR, col0 = (local % ncb) * BN;
-    const bool do_mma = !L.skip_mma;
-
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const uint32_t sbase = smem_u32(smem);
-    const uint32_t full0 = smem_u32(&bars[0]), done0 = smem_u32(&bars[2]);
+    const int tid = threadIdx.x;
+    R.smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    R.sbase = smem_u32(R.smem);
+    R.full0 = smem_u32(&bars[0]);
+    R.done0 = smem_u32(&bars[2]);
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&bars[i]), 1);
         fence_mbar_init();
     }
-    if (warp == 0) tmem_alloc(&tmem_slot, BN);
+    if ((tid >> 5) == 0) tmem_alloc(tmem_slot, BN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tmem_slot;
+    R.tmem = *tmem_slot;
+    R.fph = R.pend = R.dph = 0u;
+}
+
+// Drain pending bulk copies, release tensor memory (every thread).
+__device__ __forceinline__ void wres_finish(WRes &R)
+{
+    if (threadIdx.x == 0)
+        for (int s = 0; s < 2; ++s)
+            if ((R.pend >> s) & 1u) {
+                mbar_wait(R.full0 + 8 * s, (R.fph >> s) & 1u, 24);
+                R.fph ^= 1u << s;
+            }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if ((threadIdx.x >> 5) == 0) tmem_dealloc(R.tmem, BN);
+}
+
+// Runs block `local` (row tile local / ncb, column block local % ncb) of
+// layer L; returns false (uniformly) if a bounded wait expired.
+template <bool SPLIT, int MODE>
+__device__ __forceinline__ bool layer_block(const WLayer &L, int local, WRes &R)
+{
+    using CF = WCfg<SPLIT>;
+    __shared__ float red[NT / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = L.m, N = L.N;
+    const int ncb = n_colblocks(m), nkc = n_kchunks(m);
+    const int TR = L.TR > 0 ? L.TR : BM;  // rows of this tile that are real (the MMA always spans 128)
+    const int row0 = (local / ncb) * TR, col0 = (local % ncb) * BN;
+    const bool do_mma = !L.skip_mma;
+    uint8_t *smem = R.smem;
+    const uint32_t sbase = R.sbase, full0 = R.full0, done0 = R.done0, tmem = R.tmem;
     const uint8_t *Bcol = L.Bt + (size_t)(col0 / BN) * nkc * TILE_PAIR;
     const float *Zs = L.Zin;
     const float *Gs = (MODE == FWD && L.Zin == nullptr) ? L.C : L.Gin;
+    const bool coh = L.coherent != 0;
 
-    // producer state (thread 0): pending bulk copies and the phases of full[s]
-    uint32_t pend = 0u, fph = 0u;
     bool bad = false;     // thread 0: a wait for a B tile expired (folded into `failed` at the next barrier)
     bool failed = false;  // uniform over the CTA
     auto issue_b = [&](int kc) {
         const int s = kc & 1;
         mbar_arrive_expect_tx(full0 + 8 * s, CF::BBYTES);
         bulk_g2s(sbase + s * CF::STAGE + CF::OFF_B, Bcol + (size_t)kc * TILE_PAIR, CF::BBYTES, full0 + 8 * s);
-        pend |= 1u << s;
+        R.pend |= 1u << s;
     };
     auto wait_b = [&](int s, int code) {
-        const bool ok = mbar_wait(full0 + 8 * s, (fph >> s) & 1u, code);
-        fph ^= 1u << s;
-        pend &= ~(1u << s);
+        const bool ok = mbar_wait(full0 + 8 * s, (R.fph >> s) & 1u, code);
+        R.fph ^= 1u << s;
+        R.pend &= ~(1u << s);
         return ok;
     };
     // The first two B tiles are in flight before the wait below: the tiles
@@ -399,10 +438,10 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
     float nz[16], ng[16];
     if (do_mma) {
         if (MODE != ADJ) {
-            load16(Zs, grow, rok, m, pk, nz);
-            load16(Gs, grow, rok, m, pk, ng);
+            load16(Zs, grow, rok, m, pk, nz, coh);
+            load16(Gs, grow, rok, m, pk, ng, coh && Gs != L.C);
         } else {
-            load16(L.Gin, grow, rok, m, pk, ng);
+            load16(L.Gin, grow, rok, m, pk, ng, coh);
         }
     }
     if (MODE == OIS) {  // (waits for the row inputs while chunk 0 loads)
@@ -411,13 +450,14 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
     }
     if (do_mma) {
         const float pa = (MODE == OIS && rok) ? s_ea[prow] : a;
-        const float pthr = pa * L.lam;
+        const float pthr = __fmul_rn(pa, L.lam);
 #pragma unroll 1
         for (int kc = 0; kc < nkc; ++kc) {
             const int s = kc & 1;
             uint8_t *stage = smem + s * CF::STAGE;
             if (kc >= 2) {  // stage s is free once the MMAs of chunk kc - 2 have retired
-                const bool ok = mbar_wait(done0 + 8 * s, ((kc >> 1) - 1) & 1, 21);
+                const bool ok = mbar_wait(done0 + 8 * s, (R.dph >> s) & 1u, 21);
+                R.dph ^= 1u << s;
                 failed = __syncthreads_or(!ok || bad) != 0;
                 if (failed) break;
                 tc_fence_after();
@@ -439,10 +479,10 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
             }
             if (kc + 1 < nkc) {
                 if (MODE != ADJ) {
-                    load16(Zs, grow, rok, m, k0 + BK, nz);
-                    load16(Gs, grow, rok, m, k0 + BK, ng);
+                    load16(Zs, grow, rok, m, k0 + BK, nz, coh);
+                    load16(Gs, grow, rok, m, k0 + BK, ng, coh && Gs != L.C);
                 } else {
-                    load16(L.Gin, grow, rok, m, k0 + BK, ng);
+                    load16(L.Gin, grow, rok, m, k0 + BK, ng, coh);
                 }
             }
             store_a16<SPLIT>(stage, prow, pk, v);
@@ -467,7 +507,10 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         }
         if (!failed) {  // the last commit fires once every MMA issued before it has retired
             const int kl = nkc - 1;
-            const bool ok = mbar_wait(done0 + 8 * (kl & 1), (kl >> 1) & 1, 23);
+            const bool ok = mbar_wait(done0 + 8 * (kl & 1), (R.dph >> (kl & 1)) & 1u, 23);
+            R.dph ^= 1u << (kl & 1);
+            // the other stage's last commit (chunk nkc - 2) has fired as well
+            if (nkc >= 2) R.dph ^= 1u << ((kl - 1) & 1);
             failed = __syncthreads_or(!ok || bad) != 0;
         }
         tc_fence_after();
@@ -476,7 +519,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
     // --- epilogue
     const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
     const float ea = MODE == OIS ? s_ea[32 * q + lane] : a;
-    const float ethr = ea * L.lam;
+    const float ethr = __fmul_rn(ea, L.lam);
     float part = 0.0f;
     bool obad = false, ochg = false;  // OIS: (star) fails for the next layer; support changed
     int ok_cnt = 0;                   // OIS: support size
@@ -491,7 +534,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         for (int sl = 0; sl < BN / SW; ++sl) {
             const int cs = col0 + sl * SW;
             if (cs >= m) break;  // uniform
-            stage_in<2>(zt, Zs, gt, Gs, row0, cs, m, N, TR, tid);
+            stage_in<2>(zt, Zs, gt, Gs, row0, cs, m, N, TR, tid, coh);
             __syncthreads();
             float acc[32];
             if (do_mma) {
@@ -578,9 +621,9 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
             }
             if (failed || !eok || c >= m) continue;
             float G[16], gq[16], zq[16];
-            load16(L.Gin, erow, true, m, c, G);
-            load16(L.Gq ? L.Gq : L.C, erow, true, m, c, gq);
-            load16(L.Zq, erow, true, m, c, zq);
+            load16(L.Gin, erow, true, m, c, G, coh);
+            load16(L.Gq ? L.Gq : L.C, erow, true, m, c, gq, coh && L.Gq != nullptr);
+            load16(L.Zq, erow, true, m, c, zq, coh);
             const uint32_t bits = mask16(L.mask_in, erow, true, m, c);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -642,14 +685,28 @@ __global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant_
         }
     }
 
-    // --- teardown: drain pending bulk copies, release tensor memory
-    if (tid == 0)
-        for (int s = 0; s < 2; ++s)
-            if ((pend >> s) & 1u) wait_b(s, 24);
+    // the accumulator and the stages are free for the next block (whose bulk
+    // copies overwrite, through the async proxy, what the epilogue staged)
+    fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, BN);
+    return !failed;
+}
+
+// One layer (or Oracle-ISTA step) of up to NP problems: one block per CTA.
+template <bool SPLIT, int MODE, int NP>
+__global__ void __launch_bounds__(NT, 1) tcw_layer_kernel(const __grid_constant__ WBatch<NP> P)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[4];  // full[2] (B tile landed), done[2] (MMAs of the stage retired)
+    __shared__ uint32_t tmem_slot;
+    int p = 0;
+    while (p + 1 < P.nprob && (int)blockIdx.x >= P.base[p + 1]) ++p;
+    WRes R;
+    wres_init(R, smem_raw, bars, &tmem_slot);
+    layer_block<SPLIT, MODE>(P.L[p], (int)blockIdx.x - P.base[p], R);
+    wres_finish(R);
 }
 
 // G_T = gZ (if given) or dF/dz^(T) = B z - c + lam sign(z) = -g^(T) + lam sign(z^(T)).
@@ -677,6 +734,232 @@ __global__ void reduce_items_kernel(const float *__restrict__ partial, int nitem
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) dalpha[t] = (float)s;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batch kernels (ragged batches): every CTA takes items - a row
+// tile of one problem - from a queue in the workspace and runs all of the
+// item's layers, column block after column block, before taking the next.
+// An item's layers depend only on its own rows, so no CTA ever waits for
+// another; the state between layers lives in the workspace (read back
+// through L2: it was written by this launch).  Items are queued largest
+// problem first.
+// ---------------------------------------------------------------------------
+constexpr int PMAXP = 64;
+
+struct PProb {
+    const uint8_t *Bt;        // split B tiles
+    const float *C;
+    int m, N;
+    float lam;
+    const float *alpha;
+    const double *Lp;
+    float *Z;                 // forward: z^(T)
+    uint32_t *masks;
+    float *ckpt;
+    const float *gZ;          // backward
+    float *dalpha;            // backward: T (out)
+    float *buf[4];            // forward: (z, g) ping-pong; backward: (G, G) ping-pong in buf[0], buf[1]
+    uint8_t *seg;             // backward: 2 K + 2 states of the recomputed segment
+    size_t state;             // bytes of one N x m state
+    float *partial;           // backward: T x nitem per-block sums of dalpha
+    int nitem;                // backward: blocks (row tiles x column blocks)
+};
+
+struct PBatch {
+    int nprob, T, K;
+    int base[PMAXP + 1];      // first item of each problem; base[nprob] = total
+    int *queue;               // the next item (zeroed before the launch)
+    PProb q[PMAXP];
+};
+
+// The next item for this CTA (-1 when none are left).
+__device__ __forceinline__ int next_item(const PBatch &P, int *s_item)
+{
+    if (threadIdx.x == 0) *s_item = atomicAdd(P.queue, 1);
+    __syncthreads();
+    const int it = *s_item;
+    __syncthreads();
+    return it < P.base[P.nprob] ? it : -1;
+}
+
+__device__ __forceinline__ int item_problem(const PBatch &P, int it)
+{
+    int p = 0;
+    while (p + 1 < P.nprob && it >= P.base[p + 1]) ++p;
+    return p;
+}
+
+// The layer-t descriptor of the forward of problem q (the buffers of
+// forward_batch: checkpoints every K layers, else the ping-pong; Z last).
+__device__ __forceinline__ WLayer fwd_layer(const PProb &q, int t, int T, int K, bool ck, const float *Zc,
+                                            const float *Gc, int &pp)
+{
+    WLayer L{};
+    L.Bt = q.Bt;
+    L.C = q.C;
+    L.Zin = Zc;
+    L.Gin = Gc;
+    L.alpha = q.alpha;
+    L.Lp = q.Lp;
+    L.t = t;
+    L.m = q.m;
+    L.N = q.N;
+    L.lam = q.lam;
+    L.coherent = 1;
+    L.refresh = (ck && K < T) ? ((t + 1) % K == 0) : ((t + 1) % REFRESH == 0);
+    const int W = (q.m + 31) / 32;
+    L.mask_out = q.masks ? q.masks + (size_t)t * q.N * W : nullptr;
+    if (t == T - 1) {
+        L.Zout = q.Z;
+        L.Gout = nullptr;
+        L.skip_mma = 1;  // g^(T) is not needed
+    } else if (ck && (t + 1) % K == 0) {
+        float *slot = q.ckpt + (size_t)((t + 1) / K - 1) * 2 * q.N * q.m;
+        L.Zout = slot;
+        L.Gout = slot + (size_t)q.N * q.m;
+    } else {
+        L.Zout = q.buf[2 * pp];
+        L.Gout = q.buf[2 * pp + 1];
+        pp ^= 1;
+    }
+    return L;
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(NT, 1) tcw_persist_fwd_kernel(const __grid_constant__ PBatch P)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[4];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_item;
+    WRes R;
+    wres_init(R, smem_raw, bars, &tmem_slot);
+    bool ok = true;
+    for (int it = next_item(P, &s_item); it >= 0 && ok; it = next_item(P, &s_item)) {
+        const PProb &q = P.q[item_problem(P, it)];
+        const int tile = it - P.base[item_problem(P, it)];
+        const int ncb = n_colblocks(q.m);
+        const bool ck = q.ckpt != nullptr && P.K >= 1 && P.K < P.T;
+        const float *Zc = nullptr, *Gc = nullptr;
+        int pp = 0;
+        for (int t = 0; t < P.T && ok; ++t) {
+            const WLayer L = fwd_layer(q, t, P.T, P.K, ck, Zc, Gc, pp);
+            // (each block ends with a CTA barrier: its state is visible to the next layer)
+            for (int cb = 0; cb < ncb && ok; ++cb) ok = layer_block<SPLIT, FWD>(L, tile * ncb + cb, R);
+            Zc = L.Zout;
+            Gc = L.Gout;
+        }
+    }
+    wres_finish(R);
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(NT, 1) tcw_persist_bwd_kernel(const __grid_constant__ PBatch P)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[4];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_item;
+    WRes R;
+    wres_init(R, smem_raw, bars, &tmem_slot);
+    const int T = P.T, K = P.K < P.T ? P.K : P.T;
+    const bool ck = K < T;
+    const int nseg = (T + K - 1) / K;
+    bool ok = true;
+    for (int it = next_item(P, &s_item); it >= 0 && ok; it = next_item(P, &s_item)) {
+        const int pi = item_problem(P, it);
+        const PProb &q = P.q[pi];
+        const int tile = it - P.base[pi];
+        const int ncb = n_colblocks(q.m);
+        const int W = (q.m + 31) / 32;
+        const size_t nm = (size_t)q.N * q.m;
+        auto segZ = [&](int i) { return reinterpret_cast<float *>(q.seg + (size_t)(2 * i) * q.state); };
+        auto segG = [&](int i) { return reinterpret_cast<float *>(q.seg + (size_t)(2 * i + 1) * q.state); };
+        int gcur = 0;
+        for (int sg = nseg - 1; sg >= 0 && ok; --sg) {
+            const int t0 = sg * K, t1 = t0 + K < T ? t0 + K : T;
+            const bool lastseg = sg == nseg - 1;
+            const float *Z0 = t0 > 0 ? q.ckpt + (size_t)(t0 / K - 1) * 2 * nm : nullptr;
+            const float *G0 = t0 > 0 ? Z0 + nm : nullptr;
+            // recompute layers t0 .. t1-1 of this item's rows with the forward's arithmetic
+            for (int t = t0; t < t1 && ok; ++t) {
+                const int j = t - t0;
+                WLayer L{};
+                L.Bt = q.Bt;
+                L.C = q.C;
+                L.Zin = j == 0 ? Z0 : segZ(j);
+                L.Gin = j == 0 ? G0 : segG(j);
+                L.Zout = segZ(j + 1);
+                const bool need_g = (t + 1 < t1) || (lastseg && t + 1 == T);
+                L.Gout = need_g ? segG(j + 1) : nullptr;
+                L.skip_mma = need_g ? 0 : 1;
+                L.alpha = q.alpha;
+                L.t = t;
+                L.m = q.m;
+                L.N = q.N;
+                L.lam = q.lam;
+                L.coherent = 1;
+                L.refresh = ck ? ((t + 1) % K == 0) : ((t + 1) % REFRESH == 0);
+                for (int cb = 0; cb < ncb && ok; ++cb) ok = layer_block<SPLIT, FWD>(L, tile * ncb + cb, R);
+            }
+            if (!ok) break;
+            if (lastseg) {
+                // G_T = gZ, or dF/dz^(T) = -g^(T) + lam sign(z^(T)), on this item's rows
+                const int n = t1 - t0;
+                const float *ZT = segZ(n), *GT = segG(n);
+                const size_t r0 = (size_t)tile * BM, r1 = r0 + BM < (size_t)q.N ? r0 + BM : (size_t)q.N;
+                for (size_t e = r0 * q.m + threadIdx.x; e < r1 * q.m; e += NT) {
+                    float g;
+                    if (q.gZ) {
+                        g = __ldg(q.gZ + e);
+                    } else {
+                        const float z = __ldcg(ZT + e);
+                        g = -__ldcg(GT + e) + q.lam * (float)((z > 0.0f) - (z < 0.0f));
+                    }
+                    q.buf[gcur][e] = g;
+                }
+                __syncthreads();
+            }
+            for (int t = t1 - 1; t >= t0 && ok; --t) {
+                const int j = t - t0;
+                WLayer L{};
+                L.Bt = q.Bt;
+                L.C = q.C;
+                L.Gin = q.buf[gcur];
+                L.Gout = t > 0 ? q.buf[gcur ^ 1] : nullptr;
+                L.skip_mma = t > 0 ? 0 : 1;
+                L.mask_in = q.masks + (size_t)t * q.N * W;
+                L.Zq = segZ(j + 1);
+                L.Gq = j == 0 ? G0 : segG(j);  // nullptr at t = 0: g^(0) = c
+                L.partial = q.partial + (size_t)t * q.nitem;
+                L.alpha = q.alpha;
+                L.t = t;
+                L.m = q.m;
+                L.N = q.N;
+                L.lam = q.lam;
+                L.coherent = 1;
+                for (int cb = 0; cb < ncb && ok; ++cb) ok = layer_block<SPLIT, ADJ>(L, tile * ncb + cb, R);
+                gcur ^= 1;
+            }
+        }
+    }
+    wres_finish(R);
+}
+
+// dalpha of every problem of a persistent batch: one warp per (problem, layer).
+__global__ void reduce_batch_kernel(const __grid_constant__ PBatch P)
+{
+    const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
+    const int p = w / P.T, t = w % P.T;
+    if (p >= P.nprob) return;
+    const PProb &q = P.q[p];
+    double s = 0.0;
+    for (int b = lane; b < q.nitem; b += 32) s += (double)q.partial[(size_t)t * q.nitem + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && q.N > 0) q.dalpha[t] = (float)s;
 }
 
 // ---------------------------------------------------------------------------
@@ -978,6 +1261,158 @@ int backward_batch(const Problem *P, int count, int T, int Kin, int prec, void *
         if (P[i].N == 0) continue;
         reduce_items_kernel<<<ceil_div(T, 8), 256, 0, st>>>(bb[i].partial, bb[i].nitem, T, P[i].dalpha);
         int rc = check_launch("reduce_items_kernel");
+        if (rc) return rc;
+    }
+    return SLISTA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Ragged batches through the persistent kernels: one launch for the forward
+// (and one plus a reduction for the backward) per PMAXP problems.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Problems by decreasing work (rows x m^2), so that the queue hands out the
+// largest items first.
+std::vector<int> by_cost(const Problem *P, int count)
+{
+    std::vector<int> idx(count);
+    for (int i = 0; i < count; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        return (double)P[a].N * P[a].m * P[a].m > (double)P[b].N * P[b].m * P[b].m;
+    });
+    return idx;
+}
+
+template <bool SPLIT, bool BWD>
+int launch_persist(const PBatch &B, cudaStream_t st)
+{
+    const int total = B.base[B.nprob];
+    if (total == 0) return SLISTA_OK;
+    SLISTA_CUDA_TRY(cudaMemsetAsync(B.queue, 0, sizeof(int), st));
+    const int grid = total < num_sms() ? total : num_sms();
+    if (BWD) {
+        auto k = tcw_persist_bwd_kernel<SPLIT>;
+        SLISTA_CUDA_TRY(allow_smem(k, WCfg<SPLIT>::SMEM));
+        k<<<grid, NT, WCfg<SPLIT>::SMEM, st>>>(B);
+        int rc = check_launch("tcw_persist_bwd_kernel");
+        if (rc) return rc;
+        reduce_batch_kernel<<<ceil_div((long long)B.nprob * B.T, 8), 256, 0, st>>>(B);
+        return check_launch("reduce_batch_kernel");
+    }
+    auto k = tcw_persist_fwd_kernel<SPLIT>;
+    SLISTA_CUDA_TRY(allow_smem(k, WCfg<SPLIT>::SMEM));
+    k<<<grid, NT, WCfg<SPLIT>::SMEM, st>>>(B);
+    return check_launch("tcw_persist_fwd_kernel");
+}
+
+}  // namespace
+
+size_t persist_forward_ws_bytes(const Problem *P, int count) { return 256 + forward_batch_ws_bytes(P, count); }
+
+size_t persist_backward_ws_bytes(const Problem *P, int count, int T, int K)
+{
+    return 256 + backward_batch_ws_bytes(P, count, T, K);
+}
+
+int forward_batch_persist(const Problem *P, int count, int T, int K, int prec, void *ws, cudaStream_t st)
+{
+    const bool split = prec == SLISTA_PREC_BF16X3;
+    int *queue = reinterpret_cast<int *>(ws);
+    uint8_t *cur = reinterpret_cast<uint8_t *>(ws) + 256;
+    std::vector<PProb> qs(count);
+    for (int i = 0; i < count; ++i) {
+        PProb &q = qs[i];
+        q = PProb{};
+        q.Bt = cur;
+        cur += align256(tiles_bytes(P[i].m));
+        for (int j = 0; j < 4; ++j) {
+            q.buf[j] = reinterpret_cast<float *>(cur);
+            cur += state_bytes(P[i].m, P[i].N);
+        }
+        q.C = P[i].C;
+        q.m = P[i].m;
+        q.N = P[i].N;
+        q.lam = P[i].lam;
+        q.alpha = P[i].alpha;
+        q.Lp = P[i].L;
+        q.Z = P[i].Z;
+        q.masks = P[i].masks;
+        q.ckpt = P[i].ckpt;
+        int rc = split_tiles(P[i].B, P[i].m, const_cast<uint8_t *>(q.Bt), st);
+        if (rc) return rc;
+        if (T == 0 && P[i].N > 0)
+            SLISTA_CUDA_TRY(cudaMemsetAsync(P[i].Z, 0, sizeof(float) * (size_t)P[i].N * P[i].m, st));
+    }
+    if (T == 0) return SLISTA_OK;
+    const std::vector<int> order = by_cost(P, count);
+    for (size_t c0 = 0; c0 < order.size(); c0 += PMAXP) {
+        PBatch B{};
+        B.T = T;
+        B.K = K;
+        B.queue = queue;
+        B.base[0] = 0;
+        for (size_t c = c0; c < order.size() && B.nprob < PMAXP; ++c) {
+            const PProb &q = qs[order[c]];
+            B.q[B.nprob] = q;
+            B.base[B.nprob + 1] = B.base[B.nprob] + ceil_div(q.N, BM);
+            ++B.nprob;
+        }
+        int rc = split ? launch_persist<true, false>(B, st) : launch_persist<false, false>(B, st);
+        if (rc) return rc;
+    }
+    return SLISTA_OK;
+}
+
+int backward_batch_persist(const Problem *P, int count, int T, int Kin, int prec, void *ws, cudaStream_t st)
+{
+    const bool split = prec == SLISTA_PREC_BF16X3;
+    const int K = Kin < T ? Kin : T;
+    int *queue = reinterpret_cast<int *>(ws);
+    uint8_t *cur = reinterpret_cast<uint8_t *>(ws) + 256;
+    std::vector<PProb> qs(count);
+    for (int i = 0; i < count; ++i) {
+        PProb &q = qs[i];
+        const Problem &p = P[i];
+        q = PProb{};
+        q.state = state_bytes(p.m, p.N);
+        q.Bt = cur;
+        cur += align256(tiles_bytes(p.m));
+        q.seg = cur;
+        cur += (size_t)(2 * K + 2) * q.state;
+        q.buf[0] = reinterpret_cast<float *>(cur);
+        q.buf[1] = reinterpret_cast<float *>(cur + q.state);
+        cur += 2 * q.state;
+        q.partial = reinterpret_cast<float *>(cur);
+        q.nitem = n_items(p.m, p.N);
+        cur += align256(sizeof(float) * (size_t)T * q.nitem);
+        q.C = p.C;
+        q.m = p.m;
+        q.N = p.N;
+        q.lam = p.lam;
+        q.alpha = p.alpha;
+        q.masks = p.masks;
+        q.ckpt = p.ckpt;
+        q.gZ = p.gZ;
+        q.dalpha = p.dalpha;
+        int rc = split_tiles(p.B, p.m, const_cast<uint8_t *>(q.Bt), st);
+        if (rc) return rc;
+        if (p.N == 0) SLISTA_CUDA_TRY(cudaMemsetAsync(p.dalpha, 0, sizeof(float) * T, st));
+    }
+    const std::vector<int> order = by_cost(P, count);
+    for (size_t c0 = 0; c0 < order.size(); c0 += PMAXP) {
+        PBatch B{};
+        B.T = T;
+        B.K = K;
+        B.queue = queue;
+        B.base[0] = 0;
+        for (size_t c = c0; c < order.size() && B.nprob < PMAXP; ++c) {
+            const PProb &q = qs[order[c]];
+            B.q[B.nprob] = q;
+            B.base[B.nprob + 1] = B.base[B.nprob] + ceil_div(q.N, BM);
+            ++B.nprob;
+        }
+        int rc = split ? launch_persist<true, true>(B, st) : launch_persist<false, true>(B, st);
         if (rc) return rc;
     }
     return SLISTA_OK;

@@ -1,0 +1,70 @@
+"""The autotuner of the training step's schedule (tile rows of the layer
+kernels, trajectory or checkpointed backward): it times every candidate,
+caches the best per device and problem class, and every candidate computes
+the same thing - codes bit for bit (samples are independent of the tiling)
+and the step-size sub-gradient up to the order of its sums."""
+import numpy as np
+import pytest
+
+from paper_1905_11071_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib_ready():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1905_11071_gb300 import build, _lib
+    build.build()
+    _lib.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_tuner_caches_the_fastest_schedule(tmp_path, monkeypatch):
+    from paper_1905_11071_gb300 import api, tune, _lib
+    monkeypatch.setenv("SLISTA_TUNE_CACHE", str(tmp_path / "cache.json"))
+    w = synth.slista_64x256(N=3000, T=12)
+    g = api.gram(dev(w.D), dev(w.X))
+    alpha = (1.0 / g.L.double()).float().expand(w.T).contiguous()
+    best, tried = tune.tune(g.B, g.C, w.lam, alpha, prec="bf16x3", reps=2)
+    assert len(tried) >= 4 and best.ms == min(s.ms for s in tried)
+    assert {s.backward for s in tried} == {"traj", "ckpt"}
+    assert _lib.slista_get_tile_rows() == 0  # the tuner leaves the default in place
+    again, only = tune.tune(g.B, g.C, w.lam, alpha, prec="bf16x3")  # from the cache
+    assert len(only) == 1 and (again.tile_rows, again.backward, again.ckpt_every) == \
+        (best.tile_rows, best.backward, best.ckpt_every)
+    assert tune.lookup(g.C.device, w.m, w.N, w.T, "bf16x3") is not None
+
+
+@pytest.mark.parametrize("rows", [64, 96, 128])
+def test_every_tile_setting_gives_the_same_results(rows):
+    """Against the default tiling with the same backward: the checkpointed
+    forward refreshes the accumulator at its checkpoints, the trajectory
+    forward every 8 layers, so the two are compared only with themselves."""
+    from paper_1905_11071_gb300 import api, _lib
+    w = synth.slista_64x256(N=1500, T=10)
+    g = api.gram(dev(w.D), dev(w.X))
+    alpha = dev(synth.step_sizes(w.T, 1.0 / float(g.L.item()), 0.2, seed=3))
+    ref = {}
+    for traj in (True, False):
+        Z0, s0 = api.slista(g.B, g.C, w.lam, alpha, prec="bf16x3", keep_for_backward=True, trajectory=traj)
+        ref[traj] = (Z0, api.slista_grad(g.B, g.C, w.lam, alpha, s0, prec="bf16x3"))
+    _lib.slista_set_tile_rows(rows)
+    try:
+        for traj in (True, False):
+            Z1, s1 = api.slista(g.B, g.C, w.lam, alpha, prec="bf16x3", keep_for_backward=True, trajectory=traj)
+            d1 = api.slista_grad(g.B, g.C, w.lam, alpha, s1, prec="bf16x3")
+            Z0, d0 = ref[traj]
+            assert torch.equal(Z0, Z1)
+            torch.testing.assert_close(d1, d0, rtol=1e-4, atol=1e-4 * float(d0.abs().max()))
+        # a backward must see the tile setting its forward's buffers were laid out for
+        _lib.slista_set_tile_rows(0)
+        with pytest.raises(ValueError):
+            api.slista_grad(g.B, g.C, w.lam, alpha, s1, prec="bf16x3")
+    finally:
+        _lib.slista_set_tile_rows(0)
