@@ -64,6 +64,9 @@ def parse():
                    help="run the fixed schedule (--backward, tiles spread over the SMs) instead of the autotuned one")
     p.add_argument("--sweep", default="100000,1000000", help="batch sizes of the sweep lines ('' = none)")
     p.add_argument("--train-steps", type=int, default=30, help="step-size training steps of the equal-gap leg")
+    p.add_argument("--large-N", type=int, default=100000,
+                   help="batch of the 256 x 1024 leg (T = 50, lam = 0.05 lam_max; 0 = skip)")
+    p.add_argument("--large-train-steps", type=int, default=8, help="step-size training steps of the 256 x 1024 leg")
     p.add_argument("--cpu-samples", type=int, default=0, help="oracle sample size (0 = auto)")
     p.add_argument("--cpu-cores", type=int, default=0, help="oracle worker processes (0 = every core)")
     return p.parse_args()
@@ -492,6 +495,12 @@ def run_legs(args, w, D, X, alpha, timed, pk, pk_kind):
         legs["equal_gap"] = equal_gap_leg(args, w, g, alpha, timed)
     except Exception as ex:  # reported, never silently dropped
         legs["equal_gap"] = {"error": repr(ex)}
+    # ---- the 256 x 1024 dictionary (N = 1e5, T = 50): Gram, forward + backward, equal gap
+    if args.large_N > 0:
+        try:
+            legs["large_256x1024"] = large_leg(args, timed, pk, pk_kind)
+        except Exception as ex:
+            legs["large_256x1024"] = {"error": repr(ex)}
     # ---- the ragged batch of 64 problems, forward + backward, replayed as a CUDA graph
     try:
         legs["ragged_batch"] = ragged_leg(args, timed, pk, pk_kind)
@@ -548,6 +557,110 @@ def ragged_leg(args, timed, pk, pk_kind):
               "note": "forward + backward (checkpoints every ceil(sqrt T) layers, recompute), CUDA-graph replay; "
                       "work counted: forward T-1 products, backward recompute + adjoint"})
     return e
+
+
+def large_leg(args, timed, pk, pk_kind):
+    """The 256 x 1024 dictionary, N = 1e5 samples (z0 ~ Bernoulli(0.02),
+    lam = 0.05 lam_max), T = 50, split BF16 on the wide layer kernels: the
+    Gram against HBM, the forward (checkpoints every ceil(sqrt T) layers) and
+    the backward against the split product's tensor peak; then the step sizes
+    are trained for a few steps and the forward is compared with ISTA at
+    equal mean objective gap (ISTA with 1/L on the same tensor-core kernels:
+    the plain FP32 CUDA-core kernel stops at m = 256)."""
+    import torch
+    from paper_1905_11071_gb300 import api, synth
+    w = synth.large_256x1024(seed=0, N=args.large_N, T=50)
+    N, T, n, m, lam = w.N, w.T, w.n, w.m, w.lam
+    D = torch.from_numpy(w.D).cuda()
+    X = torch.from_numpy(w.X).cuda()
+    g = api.gram(D, X)
+    alpha = (1.0 / g.L.double()).float().expand(T).contiguous()
+    K = api.default_ckpt_every(T)
+    prec = args.prec
+
+    def gram_call(evs):
+        if evs is not None:
+            evs[0].record()
+        api.gram(D, X, with_L=False)
+        if evs is not None:
+            evs[1].record()
+
+    def step(evs, a_=alpha):
+        if evs is not None:
+            evs[0].record()
+        Z, st = api.slista(g.B, g.C, lam, a_, prec=prec, keep_for_backward=True, ckpt_every=K)
+        if evs is not None:
+            evs[1].record()
+        api.objective(g.B, g.C, g.xsq, Z, lam)
+        if evs is not None:
+            evs[2].record()
+        api.slista_grad(g.B, g.C, lam, a_, st, prec=prec)
+        if evs is not None:
+            evs[3].record()
+    steps = max(3, min(args.steps, 5))
+    _, ms_g = timed(gram_call, 2, steps, 2)
+    seg, tot = timed(step, 4, steps, 2)
+    mm = float(m)
+    nseg = -(-T // K)
+    lb, lpk, lsrc = layer_peak(prec, pk, pk_kind)
+    gram_bytes = (4.0 * (n * m + N * n + N * m + m * m) + 8.0 * N) / 1e9
+    out = {"config": {"workload": "large_256x1024", "n": n, "m": m, "N": N, "T": T, "lam_frac": 0.05,
+                      "prec": prec, "ckpt_every": K},
+           "gram": roofline_entry("hbm", gram_bytes, "GB/s", pk["hbm_gbs"], pk_kind, ms_g),
+           "slista_fwd": roofline_entry(lb, 2 * mm * mm * (T - 1) * N / 1e12, "TFLOP/s", lpk, lsrc, seg[0]),
+           "objective_ms": seg[1],
+           "slista_bwd": roofline_entry(lb, 2 * mm * mm * (2 * T - nseg) * N / 1e12, "TFLOP/s", lpk, lsrc, seg[2]),
+           "fwd_bwd_samples_per_s": N / ((seg[0] + seg[2]) / 1e3),
+           "step_samples_per_s": N / (tot / 1e3)}
+    # equal gap: trained Step-LISTA (T = 50) against ISTA (1/L) on the same kernels
+    try:
+        t0 = time.perf_counter()
+        a_tr, hist = api.train_step_sizes(alpha, g, lam, steps=args.large_train_steps, prec=prec)
+        train_s = time.perf_counter() - t0
+        T_ref = 1000
+        Fstar = api.objective(g.B, g.C, g.xsq, api.ista(g.B, g.C, lam, g.L, T_ref, prec=prec), lam,
+                              with_gap=False)
+
+        def mean_gap(Z):
+            return float((api.objective(g.B, g.C, g.xsq, Z, lam, with_gap=False) - Fstar).mean())
+        gap_s = mean_gap(api.slista(g.B, g.C, lam, a_tr, prec=prec))
+        lo, hi = T, T
+        while mean_gap(api.ista(g.B, g.C, lam, g.L, hi, prec=prec)) > gap_s and hi < T_ref:
+            lo, hi = hi, min(2 * hi, T_ref)
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if mean_gap(api.ista(g.B, g.C, lam, g.L, mid, prec=prec)) <= gap_s:
+                hi = mid
+            else:
+                lo = mid + 1
+
+        def s_call(evs):
+            if evs is not None:
+                evs[0].record()
+            api.slista(g.B, g.C, lam, a_tr, prec=prec)
+            if evs is not None:
+                evs[1].record()
+
+        def i_call(evs):
+            if evs is not None:
+                evs[0].record()
+            api.ista(g.B, g.C, lam, g.L, hi, prec=prec)
+            if evs is not None:
+                evs[1].record()
+        _, ms_s = timed(s_call, 2, 3, 1)
+        _, ms_i = timed(i_call, 2, 3, 1)
+        out["equal_gap"] = {"gap_mean": gap_s, "T_slista": T, "T_ista": hi, "F_star_layers": T_ref,
+                            "slista_ms": ms_s, "ista_ms": ms_i, "speedup": ms_i / ms_s,
+                            "train_steps": len(hist) - 1, "train_s": train_s,
+                            "train_steps_per_s": (len(hist) - 1) / train_s if train_s > 0 else None,
+                            "loss_first_last": [hist[0], hist[-1]],
+                            "note": "both forwards split BF16 on the tensor cores; F* = F after %d ISTA layers"
+                                    % T_ref}
+    except Exception as ex:
+        out["equal_gap"] = {"error": repr(ex)}
+    del D, X, g
+    torch.cuda.empty_cache()
+    return out
 
 
 def equal_gap_leg(args, w, g, alpha, timed):
@@ -607,6 +720,7 @@ def equal_gap_leg(args, w, g, alpha, timed):
             "slista_ms": ms_s, "slista_samples_per_s": N / (ms_s / 1e3),
             "ista_fp32_ms": ms_i, "ista_fp32_samples_per_s": N / (ms_i / 1e3),
             "speedup": ms_i / ms_s, "train_steps": len(hist) - 1, "train_s": train_s,
+            "train_steps_per_s": (len(hist) - 1) / train_s if train_s > 0 else None,
             "loss_first_last": [hist[0], hist[-1]],
             "note": "steps trained on this batch; F* = F after %d FP32 ISTA layers" % T_ref}
 

@@ -738,31 +738,54 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
             const float *qt = qbuf + lane_index<MP>(t - p.t0, p.ntiles, tile, quad, 0, lane);  // + 32 per code
             float part = 0.0f;
             cp_async_wait_all();  // this layer's support words have landed
-            uint32_t mw[NW];
+            uint32_t wd[NW];  // this row's support bits of the thread's code columns (zero past m and N)
 #pragma unroll
-            for (int i = 0; i < NW; ++i) mw[i] = s_mw[t & 1][tid][i];
+            for (int i = 0; i < NW; ++i) {
+                const int col0 = cbase + 32 * i;
+                const uint32_t valid = col0 + 32 <= m ? 0xffffffffu : col0 < m ? (1u << (m - col0)) - 1u : 0u;
+                wd[i] = row_ok ? s_mw[t & 1][tid][i] & valid : 0u;
+            }
             if (t - 1 >= p.t0) fetch_masks(t - 1);  // in flight during this layer
+            // h = G * mask_t, split into tensor memory as the products' A operand
 #pragma unroll
             for (int pc = 0; pc < CF::NPC; ++pc) {
                 const int col0 = cbase + 16 * pc;
-                if ((pc & 1) == 0) {
-                    // mask bits of code columns col0 .. col0+31 (zero past m)
-                    const uint32_t valid = col0 + 32 <= m ? 0xffffffffu : col0 < m ? (1u << (m - col0)) - 1u : 0u;
-                    const uint32_t word = (row_ok && valid) ? mw[pc >> 1] & valid : 0u;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) G[16 * pc + j] = ((word >> j) & 1u) ? G[16 * pc + j] : 0.0f;  // h
-                    // <h, q_t> over these 32 columns (h = 0 off the support, past m and past N);
-                    // q_t of one code is 32 consecutive floats over the warp's rows
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if ((word >> j) & 1u) part = fmaf(G[16 * pc + j], __ldg(qt + (size_t)(col0 + j) * 32), part);
-                }
+                const uint32_t word = wd[pc >> 1] >> (16 * (pc & 1));
                 float hv[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) hv[j] = G[16 * pc + j];
+                for (int j = 0; j < 16; ++j) {
+                    G[16 * pc + j] = ((word >> j) & 1u) ? G[16 * pc + j] : 0.0f;
+                    hv[j] = G[16 * pc + j];
+                }
                 store_split16(E, col0, hv);
             }
             tmem_st_wait();
+            if (t > 0) {
+                if (t - 1 >= p.t0 && quad_live) {
+                    // q_{t-1} of this warp's codes into L2 while the products run
+                    // (one 128-byte line per code: the warp's 32 rows)
+                    const float *qn = qbuf + lane_index<MP>(t - 1 - p.t0, p.ntiles, tile, quad, 0, 0);
+#pragma unroll
+                    for (int c = lane; c < CF::CW; c += 32) prefetch_l2(qn + (size_t)(cbase + c) * 32);
+                }
+                // --- B h on the tensor cores (G = h - alpha_t B h below)
+                E.contract_issue(true);
+            }
+            // <h, q_t> while the products run, 16 codes at a time (the compiler
+            // barrier keeps a batch's loads from being hoisted into the one before:
+            // 16 loads in flight per thread, no spills); q_t of one code is 32
+            // consecutive floats over the warp's rows, read only on the support
+#pragma unroll
+            for (int pc = 0; pc < CF::NPC; ++pc) {
+                const int col0 = cbase + 16 * pc;
+                const uint32_t word = wd[pc >> 1] >> (16 * (pc & 1));
+                float qv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) qv[j] = ((word >> j) & 1u) ? __ldg(qt + (size_t)(col0 + j) * 32) : 0.0f;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) part = fmaf(G[16 * pc + j], qv[j], part);
+                asm volatile("" ::: "memory");
+            }
             // dalpha_t partial: warp sum into this warp's slot
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -770,15 +793,7 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
             const bool step_slot = p.traj_steps && (t + 1) % REFRESH != 0;
             if (lane == 0) part_w[t - p.t0][warp] += step_slot ? -part / a : part;
             if (t == 0) break;  // G^(0) is not needed
-            if (t - 1 >= p.t0 && quad_live) {
-                // q_{t-1} of this warp's codes into L2 while the products run
-                // (one 128-byte line per code: the warp's 32 rows)
-                const float *qn = qbuf + lane_index<MP>(t - 1 - p.t0, p.ntiles, tile, quad, 0, 0);
-#pragma unroll
-                for (int c = lane; c < CF::CW; c += 32) prefetch_l2(qn + (size_t)(cbase + c) * 32);
-            }
-            // --- B h on the tensor cores, then G = h - alpha_t B h
-            if (!E.contract(true)) break;
+            if (!E.contract_wait()) break;
 #pragma unroll
             for (int pc = 0; pc < CF::NPC; ++pc) {
                 float bh[16];
