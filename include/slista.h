@@ -326,10 +326,22 @@ SLISTA_API int slista_backward_batched(const slista_problem_t *problems, int cou
  * (star) (zeroed by the call).  Workspace: the per-sample state of the layer
  * loop (slista_workspace_bytes(SLISTA_FN_OISTA, ...)).  prec: SLISTA_PREC_FP32
  * (layers on the CUDA cores) or SLISTA_PREC_BF16X3 / SLISTA_PREC_BF16 (layer
- * products on the tensor cores); TF32 is not built.  m <= 256. */
+ * products on the tensor cores); TF32 is not built.  m <= 256.
+ * With SLISTA_PREC_BF16X3, 128 < m <= 256 and N <= 128 x (the device's SM
+ * count), the call is one cooperative kernel (every layer, condition (star)
+ * and the L_S solves of the whole grid between grid-wide barriers, the
+ * state on chip); otherwise two kernels per layer (the solves, then the
+ * layer) with the state in the workspace.  The results agree up to the
+ * rounding order of the products. */
 SLISTA_API int oista_forward(const float *B, const float *C, const float *D, int n, int m, int N,
                              float lam, const double *L, int T, int prec, float *Z, double *LS,
                              int *accepted, void *ws, size_t ws_bytes, void *stream);
+
+/* Selects the Oracle-ISTA implementation where both apply: 1 (default) the
+ * cooperative kernel, 0 the two kernels per layer.  Process-wide; returns
+ * SLISTA_ERR_ARG for other values.  slista_get_oista_fused reads it. */
+SLISTA_API int slista_set_oista_fused(int enable);
+SLISTA_API int slista_get_oista_fused(void);
 
 /* L_S = largest eigenvalue of B_SS for N given supports S_i (Eq. spca,
  * Section 3; L_empty = L), by the eigen-solver of oista_forward's layers:

@@ -43,7 +43,7 @@ EXPORTS = [
     "slista_batched_workspace_bytes", "slista_forward_batched", "slista_backward_batched",
     "slista_traj_floats", "slista_forward_traj", "slista_backward_traj", "lasso_support_lipschitz",
     "slista_wait_probe", "lista_workspace_bytes", "lista_forward", "slista_set_tile_rows",
-    "slista_get_tile_rows",
+    "slista_get_tile_rows", "slista_set_oista_fused", "slista_get_oista_fused",
 ]
 
 
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH):
         lib.slista_wait_probe.argtypes = [ctypes.c_longlong, vp]
         lib.slista_set_tile_rows.argtypes = [i]
         lib.slista_get_tile_rows.argtypes = []
+        lib.slista_set_oista_fused.argtypes = [i]
+        lib.slista_get_oista_fused.argtypes = []
         lib.slista_workspace_bytes.restype = sz
         lib.slista_workspace_bytes.argtypes = [i, i, i, i, i, i]
         lib.slista_ckpt_floats.restype = sz
@@ -189,6 +191,16 @@ def slista_set_tile_rows(rows: int) -> None:
 
 def slista_get_tile_rows() -> int:
     return int(load().slista_get_tile_rows())
+
+
+def slista_set_oista_fused(enable: bool) -> None:
+    """Oracle-ISTA with split BF16: the cooperative kernel where it applies
+    (True, the default) or two kernels per layer (False)."""
+    _check(load().slista_set_oista_fused(1 if enable else 0), "slista_set_oista_fused")
+
+
+def slista_get_oista_fused() -> bool:
+    return bool(load().slista_get_oista_fused())
 
 
 def slista_workspace_bytes(fn: int, m: int, N: int, T: int, prec: int, ckpt_every: int = 1) -> int:

@@ -4,6 +4,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -84,6 +85,10 @@ int num_sms()
 using namespace slista;
 
 namespace {
+
+// Oracle-ISTA with split BF16: the fused cooperative kernel where it applies
+// (slista_set_oista_fused(0) selects the two-kernel path everywhere)
+std::atomic<int> g_oista_fused{1};
 
 bool valid_prec(int prec)
 {
@@ -194,7 +199,13 @@ size_t slista_workspace_bytes(int fn, int m, int N, int T, int prec, int ckpt_ev
                                         : tcw::supported(m) ? tcw::backward_ws_bytes(m, N, T, K) : 0;
             }
             return simt::backward_ws_bytes(m, N, T, ckpt_every < T ? ckpt_every : T);
-        case SLISTA_FN_OISTA: return simt::padded_mp(m) ? simt::oista_ws_bytes(m, N, T, prec) : 0;
+        case SLISTA_FN_OISTA: {
+            if (!simt::padded_mp(m)) return 0;
+            const size_t two = simt::oista_ws_bytes(m, N, T, prec);
+            // the fused kernel's workspace whenever it may be chosen
+            const size_t one = (prec == SLISTA_PREC_BF16X3 && m > 128) ? tco::ws_bytes(m, N, T) : 0;
+            return two > one ? two : one;
+        }
         case SLISTA_FN_SLISTA_BWD_TRAJ:
             if ((prec == SLISTA_PREC_BF16 || prec == SLISTA_PREC_BF16X3) && tc::supported(m) && T >= 1)
                 return tc::backward_traj_ws_bytes(m, N, T);
@@ -386,6 +397,16 @@ int slista_backward_traj(const float *B, int m, int N, float lam, const float *a
     return tc::launch_backward_traj(a, prec, traj, ws, as_stream(stream));
 }
 
+int slista_set_oista_fused(int enable)
+{
+    clear_error();
+    SLISTA_REQUIRE(enable == 0 || enable == 1, SLISTA_ERR_ARG, "slista_set_oista_fused: 0 or 1 (got %d)", enable);
+    g_oista_fused.store(enable, std::memory_order_relaxed);
+    return SLISTA_OK;
+}
+
+int slista_get_oista_fused(void) { return g_oista_fused.load(std::memory_order_relaxed); }
+
 int oista_forward(const float *B, const float *C, const float *D, int n, int m, int N, float lam, const double *L,
                   int T, int prec, float *Z, double *LS, int *accepted, void *ws, size_t ws_bytes, void *stream)
 {
@@ -399,10 +420,16 @@ int oista_forward(const float *B, const float *C, const float *D, int n, int m, 
     SLISTA_REQUIRE(N == 0 || (C && Z), SLISTA_ERR_ARG, "oista_forward: C and Z must not be NULL");
     int rc = check_lam(lam);
     if (rc) return rc;
+    OistaArgs a{B, C, D, D ? n : 0, m, N, lam, L, T, Z, LS, accepted, prec};
+    if (g_oista_fused.load(std::memory_order_relaxed) && tco::supported(m, N, prec)) {
+        const size_t need = tco::ws_bytes(m, N, T);
+        SLISTA_REQUIRE(ws_bytes >= need && ws && ws_aligned(ws), SLISTA_ERR_WORKSPACE,
+                       "oista_forward: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
+        return tco::launch(a, ws, as_stream(stream));
+    }
     const size_t need = simt::oista_ws_bytes(m, N, T, prec);
     SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
                    "oista_forward: workspace of %zu bytes (256-byte aligned) needed, %zu given", need, ws_bytes);
-    OistaArgs a{B, C, D, D ? n : 0, m, N, lam, L, T, Z, LS, accepted, prec};
     return simt::launch_oista(a, ws, as_stream(stream));
 }
 

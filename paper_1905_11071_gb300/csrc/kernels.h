@@ -100,6 +100,7 @@ namespace tcg {
 int launch_gram(const float *D, int n, int m, const float *X, int N, float *B, float *C, double *xsq,
                 cudaStream_t st);
 bool objective_supported(int m);
+int read_and_clear_flag(cudaStream_t st);
 int launch_objective(const ObjArgs &a, cudaStream_t st);
 // coupled LISTA layers (Eq. lista_layer): two products per layer
 size_t lista_ws_bytes(int n, int N);
@@ -126,7 +127,19 @@ size_t traj_floats(int m, int N, int T);
 size_t backward_traj_ws_bytes(int m, int N, int T);
 int launch_forward_traj(const PgdArgs &a, int prec, float *traj, void *ws, cudaStream_t st);
 int launch_backward_traj(const BwdArgs &a, int prec, const float *traj, void *ws, cudaStream_t st);
+// B -> B_hi, B_lo (BF16, zero-padded to MP, the engine's swizzled layout): 4 MP^2 bytes
+int split_operands(const float *B, int m, int MP, uint8_t *out, cudaStream_t st);
 }  // namespace tc
+
+namespace tco {
+// Oracle-ISTA as one cooperative kernel (split BF16, 128 < m <= 256, at most
+// 128 samples per SM): the layers, condition (star) and the L_S solves of
+// the whole grid between grid-wide barriers.
+bool supported(int m, int N, int prec);
+size_t ws_bytes(int m, int N, int T);
+int launch(const OistaArgs &a, void *ws, cudaStream_t st);
+int read_and_clear_flag(cudaStream_t st);
+}  // namespace tco
 
 namespace tcw {
 // tcgen05 layers for 256 < m <= 1024 and for batches of problems: one launch

@@ -44,6 +44,20 @@
 namespace slista {
 namespace tcg {
 
+int read_and_clear_flag(cudaStream_t st)
+{
+    int h = 0;
+    SLISTA_CUDA_TRY(cudaMemcpyFromSymbolAsync(&h, tc::tc_flag, sizeof(int), 0, cudaMemcpyDeviceToHost, st));
+    SLISTA_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h != 0) {
+        const int zero = 0;
+        SLISTA_CUDA_TRY(cudaMemcpyToSymbolAsync(tc::tc_flag, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st));
+        SLISTA_CUDA_TRY(cudaStreamSynchronize(st));
+        return fail(SLISTA_ERR_TIMEOUT, "a Gram / objective kernel's bounded wait expired (device flag %d)", h);
+    }
+    return SLISTA_OK;
+}
+
 using namespace tc;
 
 constexpr int BM = 128, BN = 256, BK = 64;

@@ -334,6 +334,16 @@ OISTA_LAYER_MARGIN = 5e-6
 TC_OISTA_MARGIN = 1e-4
 
 
+@pytest.fixture(params=[True, False], ids=["fused", "two_kernel"])
+def oista_impl(request):
+    """Oracle-ISTA with split BF16 at 128 < m <= 256: the cooperative kernel
+    (the default) and the two kernels per layer."""
+    from paper_1905_11071_gb300 import _lib
+    _lib.slista_set_oista_fused(request.param)
+    yield request.param
+    _lib.slista_set_oista_fused(True)
+
+
 def _oista_runner(A, g, lam, D=None, prec="bf16x3"):
     def run(t):
         Z, LS, acc = A.oista(g.B, g.C, lam, g.L, t, D=D, prec=prec)
@@ -342,7 +352,7 @@ def _oista_runner(A, g, lam, D=None, prec="bf16x3"):
 
 
 @pytest.mark.parametrize("with_D", [True, False])
-def test_tc_oista_parity_64x256(with_D):
+def test_tc_oista_parity_64x256(with_D, oista_impl):
     """Algorithm 1 with the layer products on the tensor cores (BF16X3),
     compared layer by layer: at least 90 % of the (sample, layer) pairs are
     compared, the codes within the split product's tolerance."""
@@ -382,7 +392,7 @@ def test_tc_oista_zero_above_lambda_max():
     assert not Z.any()
 
 
-def test_tc_oista_full_size_sampled_rows():
+def test_tc_oista_full_size_sampled_rows(oista_impl):
     """The benchmark workload (N = 10000, T = 40) on the tensor cores: 48
     sampled rows against the oracle, layer by layer (samples are
     independent)."""
@@ -409,7 +419,7 @@ def test_tc_oista_full_size_sampled_rows():
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
-def test_oista_odd_batch(prec):
+def test_oista_odd_batch(prec, oista_impl):
     """An odd batch size (N = 301) against the oracle, layer by layer: the
     per-sample state arrays of the workspace start on 256-byte boundaries
     whatever N is, as the layer kernels' 16-byte row loads need."""
