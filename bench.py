@@ -156,7 +156,7 @@ def arm_config(w, args, world: int) -> dict:
     GPU arm's schedule - tile rows, backward mode - is reported beside it)."""
     return {"workload": "slista_64x256", "n": w.n, "m": w.m, "N_per_gpu": w.N, "T": w.T, "lam": w.lam,
             "prec": args.prec, "oista_prec": args.oista_prec,
-            "step": "gram+L -> slista fwd(masks, adjoint inputs) -> objective+gap -> slista bwd",
+            "step": "gram (B, C, ||x||^2) -> slista fwd (masks, adjoint inputs) -> objective+gap -> slista bwd",
             "l2": "flushed between timed steps (write of 2x L2 size, untimed)",
             "parallelism": "dp%d" % world if world > 1 else "single"}
 

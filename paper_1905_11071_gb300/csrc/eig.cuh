@@ -176,6 +176,7 @@ __device__ double lanczos_max_eig_warp(const float *A, int lda, int k, float *q,
                 float acc[RPL][4];
 #pragma unroll
                 for (int rr = 0; rr < RPL; ++rr) acc[rr][0] = acc[rr][1] = acc[rr][2] = acc[rr][3] = 0.0f;
+#pragma unroll 4
                 for (int u = 0; u < ku; ++u) {
                     const float4 y = q4[u];
 #pragma unroll

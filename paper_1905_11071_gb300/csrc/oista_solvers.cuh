@@ -52,8 +52,9 @@ __device__ int support_indices(const uint32_t *words, int W, int *idx)
 
 // B_SS into A (leading dimension lda >= 4 ceil(k/4), k <= 64), columns
 // k .. 4 ceil(k/4) - 1 zeroed; returns whether an off-diagonal entry is
-// non-zero.  Lane l gathers columns l and l + 32 of 8 rows at a time (16
+// non-zero.  Lane l gathers columns l and l + 32 of RG rows at a time (2 RG
 // loads in flight).
+template <int RG = 8>
 __device__ bool gather_bss(const float *__restrict__ B, int m, const int *idx, int k, float *A, int lda)
 {
     const int lane = threadIdx.x & 31;
@@ -62,17 +63,17 @@ __device__ bool gather_bss(const float *__restrict__ B, int m, const int *idx, i
     const int j0 = c0 < k ? idx[c0] : 0, j1 = c1 < k ? idx[c1] : 0;
     bool off = false;
 #pragma unroll 1
-    for (int a0 = 0; a0 < k; a0 += 8) {
-        float x0[8], x1[8];
+    for (int a0 = 0; a0 < k; a0 += RG) {
+        float x0[RG], x1[RG];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < RG; ++u) {
             const int a = a0 + u;
             const float *row = B + (size_t)(a < k ? idx[a] : 0) * m;
             x0[u] = (a < k && c0 < k) ? __ldg(row + j0) : 0.0f;
             x1[u] = (a < k && c1 < k) ? __ldg(row + j1) : 0.0f;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < RG; ++u) {
             const int a = a0 + u;
             if (a < k) {
                 if (c0 < kp) A[a * lda + c0] = x0[u];

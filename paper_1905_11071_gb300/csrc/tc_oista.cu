@@ -273,14 +273,6 @@ __global__ void __launch_bounds__(NT, 1) tc_oista_kernel(const __grid_constant__
             // are many), the others solve only supports of at most 32 codes
             const int nbig = (n0 + n1 + A_WARPS - 1) / A_WARPS;
             const bool big = (int)blockIdx.x < nbig;
-            // At most one sample per warp: the layer waits for its slowest
-            // solve, so the Lanczos runs take fewer convergence checks (each
-            // a Sturm multisection of the tridiagonal): all k steps for
-            // |S| <= 32, checks from 16 steps on and every 4 after that;
-            // otherwise the rule that needs the fewest steps on average.
-            const bool latency = n0 + n1 + n2 <= (int)gridDim.x * (NT / 32);
-            const int j0 = latency ? simt::SMALL_K : eig::LANCZOS_J0, j0b = latency ? 16 : eig::LANCZOS_J0;
-            const int dj = latency ? 4 : eig::LANCZOS_DJ;
             // park z in the A operand's tensor memory (free between the layers)
 #pragma unroll
             for (int pc = 0; pc < CF::NPC; ++pc) {
@@ -307,19 +299,19 @@ __global__ void __launch_bounds__(NT, 1) tc_oista_kernel(const __grid_constant__
                         } else if (k == 1) {
                             LS = (double)__ldg(p.B + (size_t)we.idx[0] * m + we.idx[0]);
                         } else if (k <= simt::SMALL_K) {
-                            LS = simt::solve_small(p.B, m, we.idx, k, we.al, we.be, we.e2, j0, dj);
+                            LS = simt::solve_small(p.B, m, we.idx, k, we.al, we.be, we.e2);
                         } else if (k <= simt::KMAX) {
                             const int lda = eig::vec_ld(k);
-                            if (simt::gather_bss(p.B, m, we.idx, k, we.A, lda))
+                            if (simt::gather_bss<32>(p.B, m, we.idx, k, we.A, lda))
                                 LS = eig::lanczos_max_eig_warp<simt::KMAX / 32>(we.A, lda, k, we.q, we.qp, we.al,
-                                                                                we.be, we.e2, j0b, dj);
+                                                                                we.be, we.e2);
                             else
                                 LS = (double)simt::max_diag(we.A, lda, k);
                         } else if (p.Dt != nullptr) {
                             const int lda = eig::vec_ld(p.n);
                             simt::gram_ds(p.Dt, p.n, we.idx, k, we.A, lda, we.col);
                             LS = eig::lanczos_max_eig_warp<simt::KMAX / 32>(we.A, lda, p.n, we.q, we.qp, we.al,
-                                                                            we.be, we.e2, j0b, dj);
+                                                                            we.be, we.e2);
                         } else {
                             LS = simt::lanczos_global(p.B, m, we.idx, k, we);
                         }
@@ -337,7 +329,7 @@ __global__ void __launch_bounds__(NT, 1) tc_oista_kernel(const __grid_constant__
                     const int k = support_indices_cg(p.Scur + (size_t)i * W, W, ws.idx);
                     const double LS = k == 0   ? L
                                       : k == 1 ? (double)__ldg(p.B + (size_t)ws.idx[0] * m + ws.idx[0])
-                                               : simt::solve_small(p.B, m, ws.idx, k, ws.al, ws.be, ws.e2, j0, dj);
+                                               : simt::solve_small(p.B, m, ws.idx, k, ws.al, ws.be, ws.e2);
                     publish(p, i, W, LS);
                 }
             }

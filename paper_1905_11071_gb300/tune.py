@@ -112,6 +112,10 @@ def save_cache(doc: dict) -> None:
     os.replace(tmp, path)
 
 
+# relative difference below which two timed schedules count as equally fast
+NOISE = 0.02
+
+
 def tune(B, C, lam, alpha, prec: str = "bf16x3", mem_fraction: float = 0.5, reps: int = 5,
          force: bool = False):
     """Times every candidate schedule on (B, C, lam, alpha) and returns
@@ -132,6 +136,10 @@ def tune(B, C, lam, alpha, prec: str = "bf16x3", mem_fraction: float = 0.5, reps
         if not tried:
             raise RuntimeError("no schedule fits the memory budget")
         best = min(tried, key=lambda s: s.ms)
+        # the first candidate is the fixed schedule: another one replaces it
+        # only when it is faster by more than the timing noise
+        if best is not tried[0] and best.ms > (1.0 - NOISE) * tried[0].ms:
+            best = tried[0]
         doc[k] = asdict(best)
         save_cache(doc)
         return best, tried

@@ -22,12 +22,12 @@ def test_traffic_record_names_its_workload():
     with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
         doc = json.load(f)
     assert set(bench.TRAFFIC_KEYS) <= set(doc["config"])
-    assert set(doc["parts"]) == {"gram", "slista_fwd", "objective", "slista_bwd", "oista_fwd"}
+    assert set(doc["parts"]) == {"gram", "slista_fwd", "objective", "slista_bwd"}
 
 
 @pytest.mark.parametrize("N,T,prec,backward", [(1000, 40, "bf16x3", "traj"), (10000, 20, "bf16x3", "traj"),
                                                 (10000, 40, "fp32", "traj"), (10000, 40, "bf16x3", "ckpt")])
 def test_traffic_withheld_for_another_workload(N, T, prec, backward):
     cfg = bench.arm_config(synth.slista_64x256(N=N, T=T), _args(prec, backward), 1)
-    for part in ("gram", "slista_fwd", "objective", "slista_bwd", "oista_fwd"):
+    for part in ("gram", "slista_fwd", "objective", "slista_bwd"):
         assert bench.recorded_traffic(part, cfg) is None

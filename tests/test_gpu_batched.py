@@ -1,5 +1,6 @@
 """Ragged batches of independent Lasso problems (slista_forward_batched /
-slista_backward_batched): one launch per layer for all problems.  Parity of
+slista_backward_batched): one persistent launch for the forward of all
+problems and one (plus a reduction) for the backward.  Parity of
 every problem with the FP64 oracle (BF16X3 tolerances of the tensor-core
 tests), agreement with the single-problem calls, and replay under a CUDA
 graph."""
@@ -138,7 +139,7 @@ def test_batched_forward_replays_under_cuda_graph():
 def test_ragged_64_problems_sampled_rows():
     """The ragged configuration: 64 problems, n ~ U{32..128}, m = 4n,
     N ~ logU[100, 20000], lam = 0.1 lam_max each, T = 30, split BF16, forward
-    and backward in one launch per layer; sampled rows of 8 problems against
+    and backward through the persistent batch kernels; sampled rows of 8 problems against
     the oracle, the gradient of every problem finite and the batch's gradient
     of the 8 problems against their single-problem calls."""
     problems = synth.ragged_problems()

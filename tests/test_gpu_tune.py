@@ -32,7 +32,10 @@ def test_tuner_caches_the_fastest_schedule(tmp_path, monkeypatch):
     g = api.gram(dev(w.D), dev(w.X))
     alpha = (1.0 / g.L.double()).float().expand(w.T).contiguous()
     best, tried = tune.tune(g.B, g.C, w.lam, alpha, prec="bf16x3", reps=2)
-    assert len(tried) >= 4 and best.ms == min(s.ms for s in tried)
+    fastest = min(s.ms for s in tried)
+    assert len(tried) >= 4
+    # the fastest, or the fixed schedule (timed first) when it is within the timing noise of it
+    assert best.ms == fastest or (best is tried[0] and best.ms <= fastest / (1.0 - tune.NOISE))
     assert {s.backward for s in tried} == {"traj", "ckpt"}
     assert _lib.slista_get_tile_rows() == 0  # the tuner leaves the default in place
     again, only = tune.tune(g.B, g.C, w.lam, alpha, prec="bf16x3")  # from the cache
