@@ -352,15 +352,32 @@ def run_ours(args, rank, world, local_rank):
         Gh = torch.empty((N,), dtype=torch.float64).pin_memory()
         dah = torch.empty((T,), dtype=torch.float32).pin_memory()
 
+        copy_stream = torch.cuda.Stream(device=dev)
+
         def e2e_step():
+            """The step as a user runs it: inputs from pinned host memory, the
+            codes copied back on a second stream while the objective and the
+            backward run, then the loss terms and the step-size gradient."""
             Dd = Dh.to(dev, non_blocking=True)
             Xd = Xh.to(dev, non_blocking=True)
             ad = Ah.to(dev, non_blocking=True)
-            g, Z, F, gap, da = step(Dd, Xd, ad)
-            Zh.copy_(Z, non_blocking=True)
-            Fh.copy_(F, non_blocking=True)
-            Gh.copy_(gap, non_blocking=True)
+            g = api.gram(Dd, Xd, with_L=False)
+            Z, st = api.slista(g.B, g.C, lam, ad, prec=args.prec, keep_for_backward=True, ckpt_every=K,
+                               trajectory=traj)
+            copy_stream.wait_stream(stream)
+            with torch.cuda.stream(copy_stream):
+                Z.record_stream(copy_stream)
+                Zh.copy_(Z, non_blocking=True)
+            F, gap = api.objective(g.B, g.C, g.xsq, Z, lam)
+            copy_stream.wait_stream(stream)
+            with torch.cuda.stream(copy_stream):
+                F.record_stream(copy_stream)
+                gap.record_stream(copy_stream)
+                Fh.copy_(F, non_blocking=True)
+                Gh.copy_(gap, non_blocking=True)
+            da = api.slista_grad(g.B, g.C, lam, ad, st, prec=args.prec)
             dah.copy_(da, non_blocking=True)
+            stream.wait_stream(copy_stream)
 
         for _ in range(2):
             e2e_step()

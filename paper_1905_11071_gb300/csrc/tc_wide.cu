@@ -746,6 +746,10 @@ __global__ void reduce_items_kernel(const float *__restrict__ partial, int nitem
 // problem first.
 // ---------------------------------------------------------------------------
 constexpr int PMAXP = 64;
+// Sample rows of a persistent item (the MMA's M: items of 64 rows, whose
+// states in flight would fit in L2 up to m = 512, measured slower - 102 against
+// 79 ms on the 64-problem ragged batch - with the MMAs half filled).
+constexpr int PTR = BM;
 
 struct PProb {
     const uint8_t *Bt;        // split B tiles
@@ -807,6 +811,7 @@ __device__ __forceinline__ WLayer fwd_layer(const PProb &q, int t, int T, int K,
     L.N = q.N;
     L.lam = q.lam;
     L.coherent = 1;
+    L.TR = PTR;
     L.refresh = (ck && K < T) ? ((t + 1) % K == 0) : ((t + 1) % REFRESH == 0);
     const int W = (q.m + 31) / 32;
     L.mask_out = q.masks ? q.masks + (size_t)t * q.N * W : nullptr;
@@ -900,6 +905,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_persist_bwd_kernel(const __grid_con
                 L.N = q.N;
                 L.lam = q.lam;
                 L.coherent = 1;
+                L.TR = PTR;
                 L.refresh = ck ? ((t + 1) % K == 0) : ((t + 1) % REFRESH == 0);
                 for (int cb = 0; cb < ncb && ok; ++cb) ok = layer_block<SPLIT, FWD>(L, tile * ncb + cb, R);
             }
@@ -908,7 +914,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_persist_bwd_kernel(const __grid_con
                 // G_T = gZ, or dF/dz^(T) = -g^(T) + lam sign(z^(T)), on this item's rows
                 const int n = t1 - t0;
                 const float *ZT = segZ(n), *GT = segG(n);
-                const size_t r0 = (size_t)tile * BM, r1 = r0 + BM < (size_t)q.N ? r0 + BM : (size_t)q.N;
+                const size_t r0 = (size_t)tile * PTR, r1 = r0 + PTR < (size_t)q.N ? r0 + PTR : (size_t)q.N;
                 for (size_t e = r0 * q.m + threadIdx.x; e < r1 * q.m; e += NT) {
                     float g;
                     if (q.gZ) {
@@ -939,6 +945,7 @@ __global__ void __launch_bounds__(NT, 1) tcw_persist_bwd_kernel(const __grid_con
                 L.N = q.N;
                 L.lam = q.lam;
                 L.coherent = 1;
+                L.TR = PTR;
                 for (int cb = 0; cb < ncb && ok; ++cb) ok = layer_block<SPLIT, ADJ>(L, tile * ncb + cb, R);
                 gcur ^= 1;
             }
@@ -1312,7 +1319,14 @@ size_t persist_forward_ws_bytes(const Problem *P, int count) { return 256 + forw
 
 size_t persist_backward_ws_bytes(const Problem *P, int count, int T, int K)
 {
-    return 256 + backward_batch_ws_bytes(P, count, T, K);
+    // the layout of backward_batch_persist: tiles, 2 K + 2 segment states, two
+    // adjoint states and T partial sums per item
+    const int Kc = K < T ? K : T;
+    size_t b = 256;
+    for (int i = 0; i < count; ++i)
+        b += align256(tiles_bytes(P[i].m)) + (size_t)(2 * Kc + 4) * state_bytes(P[i].m, P[i].N) +
+             align256(sizeof(float) * (size_t)T * n_items(P[i].m, P[i].N, PTR));
+    return b;
 }
 
 int forward_batch_persist(const Problem *P, int count, int T, int K, int prec, void *ws, cudaStream_t st)
@@ -1355,7 +1369,7 @@ int forward_batch_persist(const Problem *P, int count, int T, int K, int prec, v
         for (size_t c = c0; c < order.size() && B.nprob < PMAXP; ++c) {
             const PProb &q = qs[order[c]];
             B.q[B.nprob] = q;
-            B.base[B.nprob + 1] = B.base[B.nprob] + ceil_div(q.N, BM);
+            B.base[B.nprob + 1] = B.base[B.nprob] + ceil_div(q.N, PTR);
             ++B.nprob;
         }
         int rc = split ? launch_persist<true, false>(B, st) : launch_persist<false, false>(B, st);
@@ -1384,7 +1398,7 @@ int backward_batch_persist(const Problem *P, int count, int T, int Kin, int prec
         q.buf[1] = reinterpret_cast<float *>(cur + q.state);
         cur += 2 * q.state;
         q.partial = reinterpret_cast<float *>(cur);
-        q.nitem = n_items(p.m, p.N);
+        q.nitem = n_items(p.m, p.N, PTR);
         cur += align256(sizeof(float) * (size_t)T * q.nitem);
         q.C = p.C;
         q.m = p.m;
@@ -1409,7 +1423,7 @@ int backward_batch_persist(const Problem *P, int count, int T, int Kin, int prec
         for (size_t c = c0; c < order.size() && B.nprob < PMAXP; ++c) {
             const PProb &q = qs[order[c]];
             B.q[B.nprob] = q;
-            B.base[B.nprob + 1] = B.base[B.nprob] + ceil_div(q.N, BM);
+            B.base[B.nprob + 1] = B.base[B.nprob] + ceil_div(q.N, PTR);
             ++B.nprob;
         }
         int rc = split ? launch_persist<true, true>(B, st) : launch_persist<false, true>(B, st);

@@ -99,8 +99,9 @@ def test_batched_backward_matches_oracle(K):
 
 
 def test_batched_equals_single_calls_for_wide_problems():
-    """For m > 256 the single-problem calls run the same layer kernel: the
-    batch reproduces them bit for bit (forward codes and sub-gradients)."""
+    """For m > 256 the single-problem calls run the same layer arithmetic: the
+    batch reproduces their codes bit for bit and their sub-gradients up to
+    the order of the per-item sums."""
     T = 10
     batch = [b for b in _small_batch(T, seed=9) if b[0].shape[1] > 256]
     A = api()
@@ -111,7 +112,9 @@ def test_batched_equals_single_calls_for_wide_problems():
         Z1, s1 = A.slista(q["B"], q["C"], q["lam"], q["alpha"], prec="bf16x3", keep_for_backward=True,
                           ckpt_every=4)
         assert torch.equal(Z, Z1)
-        assert torch.equal(da, A.slista_grad(q["B"], q["C"], q["lam"], q["alpha"], s1, prec="bf16x3"))
+        # (the per-item partial sums may be grouped differently)
+        torch.testing.assert_close(da, A.slista_grad(q["B"], q["C"], q["lam"], q["alpha"], s1, prec="bf16x3"),
+                                   rtol=1e-5, atol=0.0)
 
 
 def test_batched_forward_replays_under_cuda_graph():
