@@ -270,7 +270,7 @@ def run_ours(args, rank, world, local_rank):
     _lib.slista_set_tile_rows(schedule["tile_rows"])
     nseg = -(-T // K)
     launches_per_step = {
-        "gram": 2,                                            # D^T D, X D (+ ||x||^2)
+        "gram": 1,                                            # D^T D and X D (+ ||x||^2), one launch
         "slista_fwd": 2 if tc else 1,                         # (B split) + layer kernel
         "objective": 1,
         # (B split) + one reverse sweep + reduce, or + recompute/adjoint per segment + reduce

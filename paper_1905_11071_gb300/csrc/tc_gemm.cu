@@ -136,11 +136,11 @@ __device__ __forceinline__ void split3(float v0, float v1, uint32_t &h, uint32_t
 }
 
 // A of chunk c: 16 values of this thread's row (K positions k0 .. k0 + 15),
-// split into tensor memory at column ta (+ 32 per part).
+// loaded one chunk ahead (load_a) and split into tensor memory at column ta
+// (+ 32 per part) when their chunk comes (store_a).
 template <int MODE>
-__device__ __forceinline__ void build_a(const Params &p, int row, bool rok, int k0, uint32_t ta, Acc2 &xx)
+__device__ __forceinline__ void load_a(const Params &p, int row, bool rok, int k0, float (&v)[16])
 {
-    float v[16];
     if (MODE == GRAM_B) {
 #pragma unroll
         for (int j = 0; j < 16; ++j)
@@ -161,9 +161,14 @@ __device__ __forceinline__ void build_a(const Params &p, int row, bool rok, int 
             for (int j = 0; j < 16; ++j) v[j] = (rok && k0 + j < p.K) ? __ldg(src + j) : 0.0f;
         }
     }
-    if (MODE == GRAM_C)
+}
+
+template <int MODE>
+__device__ __forceinline__ void store_a(const float (&v)[16], uint32_t ta, Acc2 *xx)
+{
+    if (MODE == GRAM_C && xx)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) xx.add_prod(v[j], v[j]);
+        for (int j = 0; j < 16; ++j) xx->add_prod(v[j], v[j]);
     uint32_t h[8], mi[8], lo[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) split3(v[2 * j], v[2 * j + 1], h[j], mi[j], lo[j]);
@@ -173,41 +178,60 @@ __device__ __forceinline__ void build_a(const Params &p, int row, bool rok, int 
 }
 
 // B of chunk c for output columns hc0 .. hc0 + BH - 1: units of 8 K values of
-// one column, split into the three parts of stage `stage`.
+// one column (unit u = tid + NT i), loaded one chunk ahead (load_b) and split
+// into the three parts of stage `stage` when their chunk comes (store_b).
+constexpr int BUNITS = BH * BK / 8 / NT;  // units per thread
+static_assert(BUNITS * NT * 8 == BH * BK, "B units");
+
 template <int MODE>
-__device__ __forceinline__ void build_b(const Params &p, int hc0, int kc0, uint8_t *stage, int tid)
+__device__ __forceinline__ void unit_pos(int u, int &jr, int &ku)
 {
-#pragma unroll 1
-    for (int u = tid; u < BH * BK / 8; u += NT) {
+    if (b_rowmajor(MODE)) {  // Bop(j, k) = B[j][k]: eight threads share a 256-byte row segment
+        jr = u >> 3;
+        ku = u & 7;
+    } else {                 // Bop(j, k) = D[k][j]: a warp reads 32 consecutive columns per row
+        jr = u & (BH - 1);
+        ku = u / BH;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void load_b(const Params &p, int hc0, int kc0, int tid, float (&v)[BUNITS][8])
+{
+#pragma unroll
+    for (int i = 0; i < BUNITS; ++i) {
         int jr, ku;
-        if (b_rowmajor(MODE)) {  // Bop(j, k) = B[j][k]: eight threads share a 256-byte row segment
-            jr = u >> 3;
-            ku = u & 7;
-        } else {            // Bop(j, k) = D[k][j]: a warp reads 32 consecutive columns per row
-            jr = u & (BH - 1);
-            ku = u / BH;
-        }
+        unit_pos<MODE>(tid + NT * i, jr, ku);
         const int j = hc0 + jr, k = kc0 + 8 * ku;
-        float v[8];
         if (b_rowmajor(MODE)) {
             const float *src = p.Bsrc + (size_t)j * p.K + k;
             if (j < p.ncol && k + 8 <= p.K && (p.K & 3) == 0 && (reinterpret_cast<uintptr_t>(p.Bsrc) & 15) == 0) {
                 const float4 x0 = __ldg(reinterpret_cast<const float4 *>(src));
                 const float4 x1 = __ldg(reinterpret_cast<const float4 *>(src) + 1);
-                v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
-                v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+                v[i][0] = x0.x; v[i][1] = x0.y; v[i][2] = x0.z; v[i][3] = x0.w;
+                v[i][4] = x1.x; v[i][5] = x1.y; v[i][6] = x1.z; v[i][7] = x1.w;
             } else {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = (j < p.ncol && k + e < p.K) ? __ldg(src + e) : 0.0f;
+                for (int e = 0; e < 8; ++e) v[i][e] = (j < p.ncol && k + e < p.K) ? __ldg(src + e) : 0.0f;
             }
         } else {
 #pragma unroll
             for (int e = 0; e < 8; ++e)
-                v[e] = (j < p.ncol && k + e < p.K) ? __ldg(p.Bsrc + (size_t)(k + e) * p.ncol + j) : 0.0f;
+                v[i][e] = (j < p.ncol && k + e < p.K) ? __ldg(p.Bsrc + (size_t)(k + e) * p.ncol + j) : 0.0f;
         }
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void store_b(const float (&v)[BUNITS][8], uint8_t *stage, int tid)
+{
+#pragma unroll
+    for (int i = 0; i < BUNITS; ++i) {
+        int jr, ku;
+        unit_pos<MODE>(tid + NT * i, jr, ku);
         uint32_t h[4], mi[4], lo[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) split3(v[2 * e], v[2 * e + 1], h[e], mi[e], lo[e]);
+        for (int e = 0; e < 4; ++e) split3(v[i][2 * e], v[i][2 * e + 1], h[e], mi[e], lo[e]);
         const uint32_t off = sw128_offset(BH, jr, 8 * ku);
         *reinterpret_cast<uint4 *>(stage + off) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4 *>(stage + PART_B + off) = make_uint4(mi[0], mi[1], mi[2], mi[3]);
@@ -215,8 +239,9 @@ __device__ __forceinline__ void build_b(const Params &p, int hc0, int kc0, uint8
     }
 }
 
+// One output tile (block `blk` of the mode's grid) of the kernels below.
 template <int MODE>
-__global__ void __launch_bounds__(NT, 1) tc6_gemm_kernel(const Params p)
+__device__ __forceinline__ void gemm_block(const Params &p, int blk)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[2];  // done[b]: the MMAs of the chunk in buffer b retired
@@ -226,7 +251,7 @@ __global__ void __launch_bounds__(NT, 1) tc6_gemm_kernel(const Params p)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, cg = warp >> 2;     // TMEM lane quadrant, column group
     const int ncb = (p.ncol + BN - 1) / BN;
-    const int tile = (int)blockIdx.x / ncb, cb = (int)blockIdx.x % ncb;
+    const int tile = blk / ncb, cb = blk % ncb;
     const int row0 = tile * p.TR, col0 = cb * BN;
     const int rl = 32 * q + lane;               // tile row of this thread (TMEM lane)
     const int row = row0 + rl;
@@ -255,6 +280,11 @@ __global__ void __launch_bounds__(NT, 1) tc6_gemm_kernel(const Params p)
     float cinf = 0.0f;     // OBJ: max |c - Bz| of this thread's columns
     bool failed = false;
     int it = 0;            // chunk iterations so far: buffer it & 1
+    // the operands of the first chunk; each iteration loads the next one's
+    // before it issues its products, so the loads' latency overlaps them
+    float va[16], vb[BUNITS][8];
+    load_a<MODE>(p, row, rok, 16 * cg, va);
+    load_b<MODE>(p, col0, 0, tid, vb);
 #pragma unroll 1
     for (int h = 0; h < nh && !failed; ++h) {
         const int hc0 = col0 + h * BH;
@@ -268,9 +298,16 @@ __global__ void __launch_bounds__(NT, 1) tc6_gemm_kernel(const Params p)
                 tc_fence_after();
             }
             // the A operand does not depend on the half: the first half's ||x||^2 only
-            Acc2 dummy;
-            build_a<MODE>(p, row, rok, c * BK + 16 * cg, tlane + T_A + 96 * b + 8 * cg, h == 0 ? xx : dummy);
-            build_b<MODE>(p, hc0, c * BK, smem + b * STAGE_B, tid);
+            store_a<MODE>(va, tlane + T_A + 96 * b + 8 * cg, h == 0 ? &xx : nullptr);
+            store_b<MODE>(vb, smem + b * STAGE_B, tid);
+            {
+                const bool more_c = c + 1 < nkc;
+                if (more_c || h + 1 < nh) {
+                    const int cn = more_c ? c + 1 : 0, hn = more_c ? hc0 : hc0 + BH;
+                    load_a<MODE>(p, row, rok, cn * BK + 16 * cg, va);
+                    load_b<MODE>(p, hn, cn * BK, tid, vb);
+                }
+            }
             tmem_st_wait();
             fence_proxy_async_smem();
             tc_fence_before();
@@ -435,6 +472,22 @@ __global__ void __launch_bounds__(NT, 1) tc6_gemm_kernel(const Params p)
     if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(NT, 1) tc6_gemm_kernel(const Params p)
+{
+    gemm_block<MODE>(p, (int)blockIdx.x);
+}
+
+// B = D^T D and C = X D (with ||x||^2) in one launch: blocks [0, nb) form B,
+// the others C.
+__global__ void __launch_bounds__(NT, 1) tc6_gram_kernel(const Params pb, const Params pc, int nb)
+{
+    if ((int)blockIdx.x < nb)
+        gemm_block<GRAM_B>(pb, (int)blockIdx.x);
+    else
+        gemm_block<GRAM_C>(pc, (int)blockIdx.x - nb);
+}
+
 namespace {
 
 // Rows per tile: a tile costs the same MMA time for any number of rows up to
@@ -446,6 +499,15 @@ int rows_per_tile(int rows, int ncb)
     const int rounds = ceil_div(ceil_div(rows, BM), per_round > 0 ? per_round : 1);
     const int tr = ceil_div(rows, (long long)rounds * (per_round > 0 ? per_round : 1));
     return tr < 1 ? 1 : (tr > BM ? BM : tr);
+}
+
+// Sets p.TR; returns the number of blocks of the mode's grid.
+int grid_of(Params &p)
+{
+    if (p.rows <= 0 || p.ncol <= 0) return 0;
+    const int ncb = ceil_div(p.ncol, BN);
+    p.TR = rows_per_tile(p.rows, ncb);
+    return ceil_div(p.rows, p.TR) * ncb;
 }
 
 template <int MODE>
@@ -473,8 +535,6 @@ int launch_gram(const float *D, int n, int m, const float *X, int N, float *B, f
     pb.K = n;
     pb.ncol = m;
     pb.out = B;
-    int rc = launch<GRAM_B>(pb, st, "tc6_gemm_kernel (B = D^T D)");
-    if (rc || N == 0) return rc;
     Params pc{};
     pc.A = X;
     pc.Bsrc = D;
@@ -483,7 +543,11 @@ int launch_gram(const float *D, int n, int m, const float *X, int N, float *B, f
     pc.ncol = m;
     pc.out = C;
     pc.xsq = xsq;
-    return launch<GRAM_C>(pc, st, "tc6_gemm_kernel (C = X D)");
+    const int nb = grid_of(pb), nc = grid_of(pc);
+    if (nb + nc == 0) return SLISTA_OK;
+    SLISTA_CUDA_TRY(allow_smem(tc6_gram_kernel, SMEM));
+    tc6_gram_kernel<<<nb + nc, NT, SMEM, st>>>(pb, pc, nb);
+    return check_launch("tc6_gram_kernel");
 }
 
 bool objective_supported(int m) { return m >= 1 && m <= BN; }
