@@ -113,3 +113,27 @@ def test_learned_steps_follow_support_steps_10x20():
     assert np.corrcoef(_rank(a), _rank(med))[0, 1] >= 0.8
     h = T // 2
     assert (med[h:] <= a[h:]).all() and (a[h:] <= top[h:]).all()
+
+
+@pytest.mark.parametrize("method", ["ista", "oista"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_objective_never_increases_along_gpu_layers(method, prec):
+    """The descent property that Sections 2 and 3 rest on, on the GPU's own
+    iterates: with the step 1/L (ISTA, Eq. majorization2) or 1/L_S when
+    condition (star) holds (Oracle-ISTA, Section 3), F(z^(t+1)) <= F(z^(t))
+    for every sample and layer.  An L or L_S from the FP32 Lanczos that came
+    out too small would make a step too long and could break it.  The
+    objective is the GPU's FP64-reduced one; the allowance is its rounding
+    (1e-6 relative)."""
+    from paper_1905_11071_gb300 import api as A
+    w = synth.slista_64x256(N=400, T=30)
+    g = A.gram(dev(w.D), dev(w.X))
+    prev = host(g.xsq) * 0.5  # F(0) = ||x||^2 / 2
+    for t in range(1, w.T + 1):
+        if method == "ista":
+            Z = A.ista(g.B, g.C, w.lam, g.L, t, prec=prec)
+        else:
+            Z, _, _ = A.oista(g.B, g.C, w.lam, g.L, t, D=dev(w.D), prec=prec)
+        F = host(A.objective(g.B, g.C, g.xsq, Z, w.lam, with_gap=False))
+        assert (F <= prev + 1e-6 * np.abs(prev)).all(), (method, prec, t, float((F - prev).max()))
+        prev = F
