@@ -369,6 +369,23 @@ SLISTA_API int lista_forward(const float *D, int n, int m, const float *X, int N
                              const float *alpha, const float *beta, float lam, int T, float *Z, void *ws,
                              size_t ws_bytes, void *stream);
 
+/* Step-LISTA / ISTA forward on a 1-D convolutional dictionary, the
+ * structured dictionaries of Section 6 (future work there): K filters d_k of
+ * length Lf (filters: K x Lf, row k = d_k), signals of length n, and codes of
+ * K maps of P = n - Lf + 1 entries each (valid positions), so that
+ *     (D z)[i] = sum_k sum_l d_k[l] z_k[i - l],  m = K P,
+ * and column k P + j of the equivalent dense dictionary holds d_k at rows
+ * j .. j + Lf - 1.  The layers are Eq. pgd with the product B z replaced by
+ * the operator z -> D^T (D z) (2 K P Lf multiply-adds per sample and layer
+ * instead of m^2); steps alpha[0..T-1] (device, > 0, Eq. steprec) or, with
+ * alpha NULL, 1/L from the device double *L (ISTA, Eq. ista).  X: N x n,
+ * Z: N x m (out), sample-major, device memory.  FP32 on the CUDA cores.
+ * Limits: n <= 8192, K Lf <= 8192, the filters, two signals and one code
+ * vector within 200 KiB of shared memory (SLISTA_ERR_UNSUPPORTED beyond). */
+SLISTA_API int conv_slista_forward(const float *filters, int K, int Lf, const float *X, int N, int n,
+                                   float lam, const float *alpha, const double *L, int T, float *Z,
+                                   void *stream);
+
 /* Per-sample Lasso objective (Eq. lasso) evaluated from the Gram quantities,
  *     F_i = 1/2 xsq_i - c_i^T z_i + 1/2 z_i^T B z_i + lam ||z_i||_1,
  * and (gap nullable) the duality gap of the standard Lasso dual (not in the

@@ -43,7 +43,7 @@ EXPORTS = [
     "slista_batched_workspace_bytes", "slista_forward_batched", "slista_backward_batched",
     "slista_traj_floats", "slista_forward_traj", "slista_backward_traj", "lasso_support_lipschitz",
     "slista_wait_probe", "lista_workspace_bytes", "lista_forward", "slista_set_tile_rows",
-    "slista_get_tile_rows", "slista_set_oista_fused", "slista_get_oista_fused",
+    "slista_get_tile_rows", "slista_set_oista_fused", "slista_get_oista_fused", "conv_slista_forward",
 ]
 
 
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
         lib.lista_workspace_bytes.restype = sz
         lib.lista_workspace_bytes.argtypes = [i, i, i]
         lib.lista_forward.argtypes = [vp, i, i, vp, i, vp, vp, vp, f, i, vp, vp, sz, vp]
+        lib.conv_slista_forward.argtypes = [vp, i, i, vp, i, i, f, vp, vp, i, vp, vp]
         pp = ctypes.POINTER(Problem)
         lib.slista_batched_workspace_bytes.restype = sz
         lib.slista_batched_workspace_bytes.argtypes = [i, pp, i, i, i, i]
@@ -379,6 +380,23 @@ def lasso_support_lipschitz(B, S, L, LS, ws=None, D=None, stream=None) -> None:
 
 def lista_workspace_bytes(n: int, m: int, N: int) -> int:
     return int(load().lista_workspace_bytes(int(n), int(m), int(N)))
+
+
+def conv_slista_forward(filters, X, lam, alpha, L, T, Z, stream=None) -> None:
+    """Layers on a 1-D convolutional dictionary: filters K x Lf, X N x n,
+    Z N x K (n - Lf + 1); alpha (T steps) or, when None, 1/L (L: 1 double)."""
+    import torch
+    K, Lf = filters.shape
+    N, n = X.shape
+    _need(filters, torch.float32, (K, Lf), "filters")
+    _need(X, torch.float32, (N, n), "X")
+    if alpha is not None:
+        _need(alpha, torch.float32, (T,), "alpha")
+    if L is not None:
+        _need(L, torch.float64, (1,), "L")
+    _need(Z, torch.float32, (N, K * (n - Lf + 1)), "Z")
+    _check(load().conv_slista_forward(_ptr(filters), K, Lf, _ptr(X), N, n, float(lam), _ptr(alpha), _ptr(L), int(T),
+                                      _ptr(Z), _stream(stream)), "conv_slista_forward")
 
 
 def lista_forward(D, X, W, alpha, beta, lam, Z, ws=None, stream=None) -> None:

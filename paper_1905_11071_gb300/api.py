@@ -225,6 +225,18 @@ def lista(D, X, W, alpha, beta, lam, stream=None) -> torch.Tensor:
     return Z
 
 
+def conv_slista(filters, X, lam, alpha=None, L=None, T=None, stream=None) -> torch.Tensor:
+    """Step-LISTA (alpha: T steps) or ISTA (alpha None, step 1/L) on a 1-D
+    convolutional dictionary (Section 6): filters K x Lf, X N x n.  Returns
+    the codes, N x K (n - Lf + 1), map k in columns [k P, (k + 1) P)."""
+    K, Lf = filters.shape
+    N, n = X.shape
+    T = int(alpha.shape[0]) if alpha is not None else int(T)
+    Z = torch.empty((N, K * (n - Lf + 1)), dtype=torch.float32, device=X.device)
+    _lib.conv_slista_forward(filters, X, lam, alpha, L, T, Z, stream=stream)
+    return Z
+
+
 def objective(B, C, xsq, Z, lam, with_gap: bool = True, stream=None):
     N = C.shape[0]
     F = torch.empty((N,), dtype=torch.float64, device=C.device)

@@ -433,6 +433,24 @@ int oista_forward(const float *B, const float *C, const float *D, int n, int m, 
     return simt::launch_oista(a, ws, as_stream(stream));
 }
 
+int conv_slista_forward(const float *filters, int K, int Lf, const float *X, int N, int n, float lam,
+                        const float *alpha, const double *L, int T, float *Z, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(K >= 1 && Lf >= 1 && n >= Lf && N >= 0 && T >= 0, SLISTA_ERR_ARG,
+                   "conv_slista_forward: bad sizes K=%d Lf=%d n=%d N=%d T=%d (need n >= Lf >= 1)", K, Lf, n, N, T);
+    SLISTA_REQUIRE(conv::supported(K, Lf, n), SLISTA_ERR_UNSUPPORTED,
+                   "conv_slista_forward: n <= 8192, K Lf <= 8192 and K (n - Lf + 1) + K Lf + 2 n floats within 200 KiB "
+                   "of shared memory (got K=%d Lf=%d n=%d)", K, Lf, n);
+    SLISTA_REQUIRE(filters, SLISTA_ERR_ARG, "conv_slista_forward: filters must not be NULL");
+    SLISTA_REQUIRE(alpha || L, SLISTA_ERR_ARG, "conv_slista_forward: alpha or L must be given");
+    SLISTA_REQUIRE(N == 0 || (X && Z), SLISTA_ERR_ARG, "conv_slista_forward: X and Z must not be NULL");
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    ConvArgs a{filters, K, Lf, X, N, n, lam, alpha, L, T, Z};
+    return conv::launch_forward(a, as_stream(stream));
+}
+
 size_t lista_workspace_bytes(int n, int m, int N)
 {
     if (n < 1 || m < 1 || N < 0) return 0;

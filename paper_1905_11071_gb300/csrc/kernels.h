@@ -56,6 +56,18 @@ struct OistaArgs {
     int prec;            // SLISTA_PREC_FP32 (SIMT layers) or BF16 / BF16X3 (tensor-core layers)
 };
 
+struct ConvArgs {
+    const float *F;      // K x Lf filters
+    int K, Lf;
+    const float *X;      // N x n
+    int N, n;
+    float lam;
+    const float *alpha;  // T steps, or nullptr: 1 / L
+    const double *L;
+    int T;
+    float *Z;            // N x K (n - Lf + 1)
+};
+
 struct ListaArgs {
     const float *D;      // n x m
     int n, m;
@@ -198,6 +210,12 @@ int launch_oista_step(const OistaStep &o, int prec, cudaStream_t st);
 int read_and_clear_device_flag(cudaStream_t st);
 namespace tc {
 int launch_wait_probe(long long limit_cycles, cudaStream_t st);
+}
+
+namespace conv {
+// layers on a 1-D convolutional dictionary (FP32, CUDA cores)
+bool supported(int K, int Lf, int n);
+int launch_forward(const ConvArgs &a, cudaStream_t st);
 }
 
 }  // namespace slista

@@ -170,6 +170,48 @@ def orthogonal_support(n: int = 12, m: int = 30, k: int = 4, N: int = 2, leak: f
     return D.astype(dtype), X.astype(dtype), S
 
 
+def conv_filters(K: int, Lf: int, rng: np.random.Generator) -> np.ndarray:
+    """K filters of length Lf with N(0,1) entries, each scaled to unit norm
+    (float32, K x Lf)."""
+    Fh = rng.standard_normal((K, Lf))
+    Fh /= np.linalg.norm(Fh, axis=1, keepdims=True)
+    return Fh.astype(np.float32)
+
+
+def conv_dictionary(filters: np.ndarray, n: int) -> np.ndarray:
+    """The dense n x K (n - Lf + 1) matrix of a 1-D convolutional dictionary
+    (valid positions): column k (n - Lf + 1) + j holds filter k at rows
+    j .. j + Lf - 1 and zeros elsewhere, so D z = sum_k d_k * z_k (the full
+    convolution of each code map with its filter).  The entries are copies of
+    the float32 filter values."""
+    K, Lf = filters.shape
+    P = n - Lf + 1
+    D = np.zeros((n, K * P), dtype=np.float32)
+    for k in range(K):
+        for j in range(P):
+            D[j:j + Lf, k * P + j] = filters[k]
+    return D
+
+
+@dataclasses.dataclass
+class ConvWorkload(Workload):
+    """A batch on a convolutional dictionary: filters (K x Lf) and the dense D
+    they define (for the FP64 oracle and the dense kernels)."""
+    filters: np.ndarray = None
+
+
+def conv_1d(seed: int = 0, N: int = 10000, T: int = 40, K: int = 8, Lf: int = 16, n: int = 128,
+            density: float = 0.02, frac: float = 0.1) -> ConvWorkload:
+    """Structured-dictionary case (Section 6): K unit-norm filters of length Lf
+    on signals of length n, m = K (n - Lf + 1) codes; x = D z0 + 0.01 noise
+    with z0 = Bernoulli(density) N(0, 1); lam = frac lam_max."""
+    rng = np.random.default_rng(seed)
+    F = conv_filters(K, Lf, rng)
+    D = conv_dictionary(F, n)
+    X = sparse_model_samples(D, N, density, 0.01, rng)
+    return ConvWorkload("conv1d_%dx%d_n%d" % (K, Lf, n), D, X, lam_fraction(D, X, frac), T, seed, F)
+
+
 def step_sizes(T: int, base: float, spread: float, seed: int) -> np.ndarray:
     """T positive step sizes base * U[1 - spread, 1 + spread] (float32)."""
     rng = np.random.default_rng(seed)

@@ -584,3 +584,24 @@ def test_slista_grad_zero_when_output_zero():
     da, loss = oracle.slista_grad(D, X, lam, np.full(6, 0.1))
     assert not da.any()
     np.testing.assert_allclose(loss, 0.5 * (X * X).sum(), rtol=1e-14)
+
+
+def test_convolutional_dictionary_is_the_convolution():
+    """The dense matrix of a 1-D convolutional dictionary (Section 6's
+    structured dictionaries), which the oracle iterates with, against the
+    operator it stands for: D z = sum_k d_k * z_k (numpy's full convolution of
+    each code map with its filter, length P + Lf - 1 = n) and
+    (D^T r)_k = the valid correlation of r with d_k; unit-norm columns."""
+    rng = np.random.default_rng(11)
+    for (K, Lf, n) in [(3, 5, 37), (8, 16, 128), (2, 9, 9)]:
+        F = synth.conv_filters(K, Lf, rng)
+        D = synth.conv_dictionary(F, n).astype(np.float64)
+        P = n - Lf + 1
+        assert D.shape == (n, K * P)
+        np.testing.assert_allclose(np.linalg.norm(D, axis=0), 1.0, rtol=1e-6)
+        z = rng.standard_normal(K * P)
+        r = rng.standard_normal(n)
+        Dz = sum(np.convolve(z[k * P:(k + 1) * P], F[k].astype(np.float64)) for k in range(K))
+        np.testing.assert_allclose(D @ z, Dz, rtol=1e-12, atol=1e-12)
+        Dtr = np.concatenate([np.correlate(r, F[k].astype(np.float64), mode="valid") for k in range(K)])
+        np.testing.assert_allclose(D.T @ r, Dtr, rtol=1e-12, atol=1e-12)
