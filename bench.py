@@ -536,12 +536,56 @@ def run_legs(args, w, D, X, alpha, timed, pk, pk_kind):
             legs["large_256x1024"] = large_leg(args, timed, pk, pk_kind)
         except Exception as ex:
             legs["large_256x1024"] = {"error": repr(ex)}
+    # ---- a 1-D convolutional dictionary (structured dictionaries, Section 6)
+    try:
+        legs["conv1d"] = conv_leg(args, timed)
+    except Exception as ex:
+        legs["conv1d"] = {"error": repr(ex)}
     # ---- the ragged batch of 64 problems, forward + backward, replayed as a CUDA graph
     try:
         legs["ragged_batch"] = ragged_leg(args, timed, pk, pk_kind)
     except Exception as ex:
         legs["ragged_batch"] = {"error": repr(ex)}
     return legs
+
+
+def conv_leg(args, timed):
+    """Step-LISTA forward on a 1-D convolutional dictionary (K = 8 filters of
+    16 taps, signals of 128 samples: m = 904 codes; N = 1e4, T = 40): the fast
+    operator z -> D^T (D z) on the CUDA cores against the dense split-BF16
+    layers on the same 128 x 904 dictionary."""
+    import torch
+    from paper_1905_11071_gb300 import api, synth
+    w = synth.conv_1d()
+    K, Lf = w.filters.shape
+    P = w.n - Lf + 1
+    F = torch.from_numpy(w.filters).cuda()
+    X = torch.from_numpy(w.X).cuda()
+    g = api.gram(torch.from_numpy(w.D).cuda(), X)
+    alpha = (1.0 / g.L.double()).float().expand(w.T).contiguous()
+
+    def c_call(evs):
+        if evs is not None:
+            evs[0].record()
+        api.conv_slista(F, X, w.lam, alpha)
+        if evs is not None:
+            evs[1].record()
+
+    def d_call(evs):
+        if evs is not None:
+            evs[0].record()
+        api.slista(g.B, g.C, w.lam, alpha, prec=args.prec)
+        if evs is not None:
+            evs[1].record()
+    _, ms_c = timed(c_call, 2, args.steps, 2)
+    _, ms_d = timed(d_call, 2, args.steps, 2)
+    flop = 4.0 * K * P * Lf * w.N * w.T / 1e12  # D z and D^T r: 2 K P Lf multiply-adds
+    peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    e = roofline_entry("alu", flop, "TFLOP/s", peak, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz", ms_c)
+    e.update({"config": {"workload": w.name, "K": int(K), "Lf": int(Lf), "n": w.n, "m": w.m, "N": w.N, "T": w.T},
+              "samples_per_s": w.N / (ms_c / 1e3), "dense_split_bf16_ms": ms_d,
+              "speedup_vs_dense": ms_d / ms_c})
+    return e
 
 
 def ragged_leg(args, timed, pk, pk_kind):
