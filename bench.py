@@ -577,14 +577,38 @@ def conv_leg(args, timed):
         api.slista(g.B, g.C, w.lam, alpha, prec=args.prec)
         if evs is not None:
             evs[1].record()
+    # one step-size gradient: trajectory forward + adjoint, against the dense
+    # split-BF16 forward (keeping the adjoint's inputs) + adjoint
+    steps = (alpha * torch.linspace(0.8, 1.2, w.T, device="cuda")).contiguous()
+
+    def cg_call(evs):
+        if evs is not None:
+            evs[0].record()
+        api.conv_slista_grad(F, X, w.lam, steps)
+        if evs is not None:
+            evs[1].record()
+
+    def dg_call(evs):
+        if evs is not None:
+            evs[0].record()
+        _, st = api.slista(g.B, g.C, w.lam, steps, prec=args.prec, keep_for_backward=True)
+        api.slista_grad(g.B, g.C, w.lam, steps, st, prec=args.prec)
+        if evs is not None:
+            evs[1].record()
     _, ms_c = timed(c_call, 2, args.steps, 2)
     _, ms_d = timed(d_call, 2, args.steps, 2)
+    _, ms_cg = timed(cg_call, 2, args.steps, 2)
+    _, ms_dg = timed(dg_call, 2, args.steps, 2)
     flop = 4.0 * K * P * Lf * w.N * w.T / 1e12  # D z and D^T r: 2 K P Lf multiply-adds
     peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     e = roofline_entry("alu", flop, "TFLOP/s", peak, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz", ms_c)
     e.update({"config": {"workload": w.name, "K": int(K), "Lf": int(Lf), "n": w.n, "m": w.m, "N": w.N, "T": w.T},
               "samples_per_s": w.N / (ms_c / 1e3), "dense_split_bf16_ms": ms_d,
-              "speedup_vs_dense": ms_d / ms_c})
+              "speedup_vs_dense": ms_d / ms_c,
+              # forward + adjoint: the adjoint has one more operator product (the seed) and one fewer (layer 0)
+              "grad": {"ms": ms_cg, "samples_per_s": w.N / (ms_cg / 1e3),
+                       "alu_frac": 2 * flop / (ms_cg / 1e3) / peak,
+                       "dense_split_bf16_ms": ms_dg, "speedup_vs_dense": ms_dg / ms_cg}})
     return e
 
 

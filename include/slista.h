@@ -386,6 +386,34 @@ SLISTA_API int conv_slista_forward(const float *filters, int K, int Lf, const fl
                                    float lam, const float *alpha, const double *L, int T, float *Z,
                                    void *stream);
 
+/* Step-size sub-gradient on a 1-D convolutional dictionary: the adjoint of
+ * conv_slista_forward's Step-LISTA layers (Eq. steprec), the analogue of
+ * slista_forward_traj / slista_backward_traj for the structured
+ * dictionaries of Section 6.  Filters of at most 32 taps.
+ *
+ * conv_slista_forward_traj: conv_slista_forward with steps alpha (device,
+ * T >= 1, > 0) that also writes traj (device, N x T x m floats, sample s,
+ * layer t at (s T + t) m) = z^(t+1) of every layer; Z (N x m) = z^(T).
+ *
+ * conv_slista_backward: dalpha (device, T floats) = the sub-gradient with
+ * respect to alpha of sum_i F_{x_i}(z_i^(T)) (Eq. lasso), from the traj of a
+ * conv_slista_forward_traj call with the same filters, X, lam, alpha, T:
+ * per sample G = D^T (D z^(T) - x) + lam sign(z^(T)), then for t = T-1..0
+ * h = G on the support of z^(t+1), dalpha_t += <h, z^(t+1) - z^(t)> / alpha_t,
+ * G = h - alpha_t D^T (D h).  ws: conv_slista_backward_workspace_bytes(K, Lf,
+ * n, N, T) bytes of device memory (256-byte aligned; per-CTA partial sums,
+ * reduced in FP64 in a fixed order, so the result is run-to-run identical);
+ * 0 when the sizes are outside the limits.  Limits: Lf <= 32 and the padded
+ * filters, signal, residual, per-filter partial sums and three code vectors
+ * within 200 KiB of shared memory (SLISTA_ERR_UNSUPPORTED beyond). */
+SLISTA_API size_t conv_slista_backward_workspace_bytes(int K, int Lf, int n, int N, int T);
+SLISTA_API int conv_slista_forward_traj(const float *filters, int K, int Lf, const float *X, int N, int n,
+                                        float lam, const float *alpha, int T, float *Z, float *traj,
+                                        void *stream);
+SLISTA_API int conv_slista_backward(const float *filters, int K, int Lf, const float *X, int N, int n,
+                                    float lam, const float *alpha, int T, const float *traj, float *dalpha,
+                                    void *ws, size_t ws_bytes, void *stream);
+
 /* Per-sample Lasso objective (Eq. lasso) evaluated from the Gram quantities,
  *     F_i = 1/2 xsq_i - c_i^T z_i + 1/2 z_i^T B z_i + lam ||z_i||_1,
  * and (gap nullable) the duality gap of the standard Lasso dual (not in the

@@ -44,12 +44,14 @@ EXPORTS = [
     "slista_traj_floats", "slista_forward_traj", "slista_backward_traj", "lasso_support_lipschitz",
     "slista_wait_probe", "lista_workspace_bytes", "lista_forward", "slista_set_tile_rows",
     "slista_get_tile_rows", "slista_set_oista_fused", "slista_get_oista_fused", "conv_slista_forward",
+    "conv_slista_backward_workspace_bytes", "conv_slista_forward_traj", "conv_slista_backward",
 ]
 
 
 # entry points that return a size (size_t): every other one returns an int status
 SIZE_RETURNING = ("slista_workspace_bytes", "slista_ckpt_floats", "slista_mask_words",
-                  "slista_batched_workspace_bytes", "slista_traj_floats", "lista_workspace_bytes")
+                  "slista_batched_workspace_bytes", "slista_traj_floats", "lista_workspace_bytes",
+                  "conv_slista_backward_workspace_bytes")
 
 
 class Problem(ctypes.Structure):
@@ -115,6 +117,10 @@ def load(path: str = LIB_PATH):
         lib.lista_workspace_bytes.argtypes = [i, i, i]
         lib.lista_forward.argtypes = [vp, i, i, vp, i, vp, vp, vp, f, i, vp, vp, sz, vp]
         lib.conv_slista_forward.argtypes = [vp, i, i, vp, i, i, f, vp, vp, i, vp, vp]
+        lib.conv_slista_backward_workspace_bytes.restype = sz
+        lib.conv_slista_backward_workspace_bytes.argtypes = [i, i, i, i, i]
+        lib.conv_slista_forward_traj.argtypes = [vp, i, i, vp, i, i, f, vp, i, vp, vp, vp]
+        lib.conv_slista_backward.argtypes = [vp, i, i, vp, i, i, f, vp, i, vp, vp, vp, sz, vp]
         pp = ctypes.POINTER(Problem)
         lib.slista_batched_workspace_bytes.restype = sz
         lib.slista_batched_workspace_bytes.argtypes = [i, pp, i, i, i, i]
@@ -397,6 +403,44 @@ def conv_slista_forward(filters, X, lam, alpha, L, T, Z, stream=None) -> None:
     _need(Z, torch.float32, (N, K * (n - Lf + 1)), "Z")
     _check(load().conv_slista_forward(_ptr(filters), K, Lf, _ptr(X), N, n, float(lam), _ptr(alpha), _ptr(L), int(T),
                                       _ptr(Z), _stream(stream)), "conv_slista_forward")
+
+
+def conv_slista_backward_workspace_bytes(K: int, Lf: int, n: int, N: int, T: int) -> int:
+    return int(load().conv_slista_backward_workspace_bytes(int(K), int(Lf), int(n), int(N), int(T)))
+
+
+def conv_slista_forward_traj(filters, X, lam, alpha, Z, traj, stream=None) -> None:
+    """conv_slista_forward with steps alpha that also writes traj, N x T x m
+    (z^(t+1) of every layer t)."""
+    import torch
+    K, Lf = filters.shape
+    N, n = X.shape
+    T = alpha.shape[0]
+    m = K * (n - Lf + 1)
+    _need(filters, torch.float32, (K, Lf), "filters")
+    _need(X, torch.float32, (N, n), "X")
+    _need(alpha, torch.float32, (T,), "alpha")
+    _need(Z, torch.float32, (N, m), "Z")
+    _need(traj, torch.float32, (N, T, m), "traj")
+    _check(load().conv_slista_forward_traj(_ptr(filters), K, Lf, _ptr(X), N, n, float(lam), _ptr(alpha), T, _ptr(Z),
+                                           _ptr(traj), _stream(stream)), "conv_slista_forward_traj")
+
+
+def conv_slista_backward(filters, X, lam, alpha, traj, dalpha, ws=None, stream=None) -> None:
+    """dalpha (T) = d sum_i F_{x_i}(z_i^(T)) / d alpha from traj."""
+    import torch
+    K, Lf = filters.shape
+    N, n = X.shape
+    T = alpha.shape[0]
+    m = K * (n - Lf + 1)
+    _need(filters, torch.float32, (K, Lf), "filters")
+    _need(X, torch.float32, (N, n), "X")
+    _need(alpha, torch.float32, (T,), "alpha")
+    _need(traj, torch.float32, (N, T, m), "traj")
+    _need(dalpha, torch.float32, (T,), "dalpha")
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check(load().conv_slista_backward(_ptr(filters), K, Lf, _ptr(X), N, n, float(lam), _ptr(alpha), T, _ptr(traj),
+                                       _ptr(dalpha), _ptr(ws), wsb, _stream(stream)), "conv_slista_backward")
 
 
 def lista_forward(D, X, W, alpha, beta, lam, Z, ws=None, stream=None) -> None:

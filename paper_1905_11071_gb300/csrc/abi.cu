@@ -451,6 +451,54 @@ int conv_slista_forward(const float *filters, int K, int Lf, const float *X, int
     return conv::launch_forward(a, as_stream(stream));
 }
 
+static int conv_traj_check(const char *fn, const float *filters, int K, int Lf, const float *alpha, int N, int n,
+                           int T, float lam)
+{
+    SLISTA_REQUIRE(K >= 1 && Lf >= 1 && n >= Lf && N >= 0 && T >= 1, SLISTA_ERR_ARG,
+                   "%s: bad sizes K=%d Lf=%d n=%d N=%d T=%d (need n >= Lf >= 1, T >= 1)", fn, K, Lf, n, N, T);
+    SLISTA_REQUIRE(conv::supported(K, Lf, n) && conv::traj_supported(K, Lf, n, T), SLISTA_ERR_UNSUPPORTED,
+                   "%s: filters of at most 32 taps, n <= 8192, and the padded buffers within 200 KiB of shared "
+                   "memory (got K=%d Lf=%d n=%d T=%d)", fn, K, Lf, n, T);
+    SLISTA_REQUIRE(filters && alpha, SLISTA_ERR_ARG, "%s: filters and alpha must not be NULL", fn);
+    return check_lam(lam);
+}
+
+size_t conv_slista_backward_workspace_bytes(int K, int Lf, int n, int N, int T)
+{
+    if (K < 1 || Lf < 1 || n < Lf || N < 0 || T < 1) return 0;
+    if (!conv::supported(K, Lf, n) || !conv::traj_supported(K, Lf, n, T)) return 0;
+    return conv::backward_ws_bytes(K, Lf, n, N, T);
+}
+
+int conv_slista_forward_traj(const float *filters, int K, int Lf, const float *X, int N, int n, float lam,
+                             const float *alpha, int T, float *Z, float *traj, void *stream)
+{
+    clear_error();
+    int rc = conv_traj_check("conv_slista_forward_traj", filters, K, Lf, alpha, N, n, T, lam);
+    if (rc) return rc;
+    SLISTA_REQUIRE(N == 0 || (X && Z && traj), SLISTA_ERR_ARG,
+                   "conv_slista_forward_traj: X, Z and traj must not be NULL");
+    ConvArgs a{filters, K, Lf, X, N, n, lam, alpha, nullptr, T, Z};
+    return conv::launch_forward_traj(a, traj, as_stream(stream));
+}
+
+int conv_slista_backward(const float *filters, int K, int Lf, const float *X, int N, int n, float lam,
+                         const float *alpha, int T, const float *traj, float *dalpha, void *ws, size_t ws_bytes,
+                         void *stream)
+{
+    clear_error();
+    int rc = conv_traj_check("conv_slista_backward", filters, K, Lf, alpha, N, n, T, lam);
+    if (rc) return rc;
+    SLISTA_REQUIRE(dalpha && (N == 0 || (X && traj)), SLISTA_ERR_ARG,
+                   "conv_slista_backward: dalpha, X and traj must not be NULL");
+    const size_t need = N > 0 ? conv::backward_ws_bytes(K, Lf, n, N, T) : 0;
+    SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
+                   "conv_slista_backward: workspace of %zu bytes (256-byte aligned) needed, %zu given", need,
+                   ws_bytes);
+    ConvArgs a{filters, K, Lf, X, N, n, lam, alpha, nullptr, T, nullptr};
+    return conv::launch_backward(a, traj, dalpha, ws, as_stream(stream));
+}
+
 size_t lista_workspace_bytes(int n, int m, int N)
 {
     if (n < 1 || m < 1 || N < 0) return 0;

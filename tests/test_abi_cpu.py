@@ -149,6 +149,33 @@ def test_argument_validation_without_gpu(lib):
     assert lib.lasso_support_lipschitz(vp, None, 0, 40, 0, None, None, None, None, 0, None) == _lib.SLISTA_OK
 
 
+def test_conv_gradient_validation_without_gpu(lib):
+    """The convolutional trajectory forward and adjoint refuse bad sizes,
+    filters longer than 32 taps, T = 0 and a short workspace before any
+    launch (the pointers are never dereferenced)."""
+    vp = ctypes.c_void_p(1)
+    # n < Lf, T = 0
+    assert lib.conv_slista_forward_traj(vp, 4, 16, vp, 8, 10, 0.1, vp, 5, vp, vp, None) == _lib.SLISTA_ERR_ARG
+    assert lib.conv_slista_forward_traj(vp, 4, 16, vp, 8, 128, 0.1, vp, 0, vp, vp, None) == _lib.SLISTA_ERR_ARG
+    # 33 taps
+    assert lib.conv_slista_forward_traj(vp, 4, 33, vp, 8, 128, 0.1, vp, 5, vp, vp, None) == _lib.SLISTA_ERR_UNSUPPORTED
+    assert lib.conv_slista_backward(vp, 4, 33, vp, 8, 128, 0.1, vp, 5, vp, vp, vp, 1 << 20,
+                                    None) == _lib.SLISTA_ERR_UNSUPPORTED
+    assert _lib.conv_slista_backward_workspace_bytes(4, 33, 128, 8, 5) == 0
+    # steps are required (no 1/L form of the adjoint); a null trajectory
+    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, 0.1, None, 5, vp, vp, vp, 1 << 20,
+                                    None) == _lib.SLISTA_ERR_ARG
+    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, 0.1, vp, 5, None, vp, vp, 1 << 20,
+                                    None) == _lib.SLISTA_ERR_ARG
+    # workspace: one per-CTA partial per layer
+    need = _lib.conv_slista_backward_workspace_bytes(4, 16, 128, 8, 5)
+    assert need >= 5 * 4
+    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, 0.1, vp, 5, vp, vp, vp, need - 1,
+                                    None) == _lib.SLISTA_ERR_WORKSPACE
+    # negative lambda
+    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, -0.1, vp, 5, vp, vp, vp, need, None) == _lib.SLISTA_ERR_ARG
+
+
 def test_python_binding_rejects_cpu_tensors(lib):
     torch = pytest.importorskip("torch")
     D = torch.zeros(4, 8)

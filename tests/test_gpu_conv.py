@@ -8,7 +8,12 @@ oracle iterating with the equivalent dense dictionary:
   (Lf = n) and a single filter;
 * lam above lam_max gives exactly zero codes;
 * the fast operator and the dense tensor-core layers on the same dictionary
-  agree within the split-BF16 tolerance.
+  agree within the split-BF16 tolerance;
+* the step-size sub-gradient (conv_slista_forward_traj + conv_slista_backward)
+  against the oracle's adjoint on the dense dictionary (relative 1e-4, the
+  dense FP32 path's bound), its trajectory against the oracle's layers, its
+  degenerate cases (zero codes, T = 1, N = 0) and its run-to-run identity;
+  at the benchmark's size, additivity over samples and sampled rows.
 """
 import numpy as np
 import pytest
@@ -109,3 +114,97 @@ def test_conv_full_size_sampled_rows():
     Z = A.conv_slista(dev(w.filters), dev(w.X), w.lam, dev(alpha))
     rows = np.random.default_rng(2).choice(w.N, size=64, replace=False)
     _close(Z[rows], oracle.pgd(w.D, w.X[rows], w.lam, alpha))
+
+
+GRAD_TOL = 1e-4
+
+
+def _grad_case(K, Lf, n, N, T, seed=0, spread=0.3):
+    w = _workload(K, Lf, n, N, T, seed=seed)
+    alpha = synth.step_sizes(w.T, 1.0 / oracle.lipschitz(w.D), spread, seed=seed + 5)
+    return w, alpha
+
+
+def _rel(dg, do):
+    return float(np.linalg.norm(host(dg).astype(np.float64) - do) / np.linalg.norm(do))
+
+
+def test_conv_backward_matches_oracle():
+    from paper_1905_11071_gb300 import api as A
+    w, alpha = _grad_case(8, 16, 128, 300, 30)
+    Z, da = A.conv_slista_grad(dev(w.filters), dev(w.X), w.lam, dev(alpha))
+    do, _ = oracle.slista_grad(w.D, w.X, w.lam, alpha)
+    assert _rel(da, do) <= GRAD_TOL, (host(da), do)
+    # the trajectory forward repeats the forward's arithmetic exactly
+    assert torch.equal(Z, A.conv_slista(dev(w.filters), dev(w.X), w.lam, dev(alpha)))
+
+
+@pytest.mark.parametrize("K,Lf,n,N,T", [(3, 5, 37, 129, 17), (5, 12, 12, 64, 9), (1, 7, 200, 33, 25),
+                                        (16, 4, 20, 257, 12), (4, 32, 96, 70, 10), (2, 3, 64, 1, 1)])
+def test_conv_backward_odd_shapes(K, Lf, n, N, T):
+    from paper_1905_11071_gb300 import api as A
+    w, alpha = _grad_case(K, Lf, n, N, T, seed=K + n)
+    _, da = A.conv_slista_grad(dev(w.filters), dev(w.X), w.lam, dev(alpha))
+    do, _ = oracle.slista_grad(w.D, w.X, w.lam, alpha)
+    assert _rel(da, do) <= GRAD_TOL, (host(da), do)
+
+
+def test_conv_trajectory_is_every_layer():
+    """traj[:, t] = z^(t+1): the oracle run for t + 1 layers."""
+    from paper_1905_11071_gb300 import _lib
+    w, alpha = _grad_case(8, 16, 128, 100, 12, seed=2)
+    m = w.D.shape[1]
+    Z = torch.empty((w.N, m), dtype=torch.float32, device="cuda")
+    traj = torch.empty((w.N, w.T, m), dtype=torch.float32, device="cuda")
+    _lib.conv_slista_forward_traj(dev(w.filters), dev(w.X), w.lam, dev(alpha), Z, traj)
+    assert torch.equal(traj[:, -1], Z)
+    for t in (0, 1, 5, 11):
+        _close(traj[:, t], oracle.pgd(w.D, w.X, w.lam, alpha[:t + 1]))
+
+
+def test_conv_backward_is_deterministic():
+    from paper_1905_11071_gb300 import api as A
+    w, alpha = _grad_case(8, 16, 128, 2000, 20, seed=4)
+    outs = [A.conv_slista_grad(dev(w.filters), dev(w.X), w.lam, dev(alpha))[1] for _ in range(3)]
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_conv_backward_zero_codes_and_empty_batch():
+    """Above lam_max every code is zero, so no layer has a support and the
+    sub-gradient is exactly zero; N = 0 gives zeros too."""
+    from paper_1905_11071_gb300 import api as A
+    w, alpha = _grad_case(8, 16, 128, 64, 10, seed=3)
+    lam = float(np.float32(np.abs(w.X.astype(np.float64) @ w.D.astype(np.float64)).max() * 1.001))
+    Z, da = A.conv_slista_grad(dev(w.filters), dev(w.X), lam, dev(alpha))
+    assert not Z.any() and not da.any()
+    X0 = torch.empty((0, w.X.shape[1]), dtype=torch.float32, device="cuda")
+    Z0, da0 = A.conv_slista_grad(dev(w.filters), X0, w.lam, dev(alpha))
+    assert Z0.shape[0] == 0 and not da0.any()
+
+
+def test_conv_backward_rejects_long_filters():
+    from paper_1905_11071_gb300 import api as A, _lib
+    w, alpha = _grad_case(2, 40, 128, 8, 4, seed=1)
+    with pytest.raises(_lib.SlistaError) as e:
+        A.conv_slista_grad(dev(w.filters), dev(w.X), w.lam, dev(alpha))
+    assert e.value.code == _lib.SLISTA_ERR_UNSUPPORTED
+
+
+def test_conv_backward_full_size():
+    """The benchmark's convolutional workload (N = 10000, T = 40, one launch
+    of each kernel): the sub-gradient is a sum over samples, so it equals the
+    sum of the two halves' within FP32 rounding, and one 200-sample part
+    matches the oracle."""
+    from paper_1905_11071_gb300 import api as A
+    w = synth.conv_1d()
+    alpha = synth.step_sizes(w.T, 1.0 / oracle.lipschitz(w.D), 0.2, seed=9)
+    F, X, a = dev(w.filters), dev(w.X), dev(alpha)
+    _, da = A.conv_slista_grad(F, X, w.lam, a)
+    _, d1 = A.conv_slista_grad(F, X[:5000].contiguous(), w.lam, a)
+    _, d2 = A.conv_slista_grad(F, X[5000:].contiguous(), w.lam, a)
+    s = (d1.double() + d2.double())
+    assert float((da.double() - s).norm() / s.norm()) <= 1e-5
+    rows = np.sort(np.random.default_rng(2).choice(w.N, size=200, replace=False))
+    _, dr = A.conv_slista_grad(F, X[rows].contiguous(), w.lam, a)
+    do, _ = oracle.slista_grad(w.D, w.X[rows], w.lam, alpha)
+    assert _rel(dr, do) <= GRAD_TOL
