@@ -391,9 +391,15 @@ SLISTA_API int conv_slista_forward(const float *filters, int K, int Lf, const fl
  * slista_forward_traj / slista_backward_traj for the structured
  * dictionaries of Section 6.  Filters of at most 32 taps.
  *
+ * traj: device, conv_slista_traj_floats(K, Lf, n, N, T) floats, 16-byte
+ * aligned, written by conv_slista_forward_traj and read by
+ * conv_slista_backward: z^(t+1) of every layer t, sample s, layer t, map k
+ * at ((s T + t) K + k) PQ with PQ = P rounded up to a multiple of 4 (entries
+ * P .. PQ-1 of a map are zero).  traj_floats is its length; a shorter buffer
+ * returns SLISTA_ERR_WORKSPACE before any launch.
+ *
  * conv_slista_forward_traj: conv_slista_forward with steps alpha (device,
- * T >= 1, > 0) that also writes traj (device, N x T x m floats, sample s,
- * layer t at (s T + t) m) = z^(t+1) of every layer; Z (N x m) = z^(T).
+ * T >= 1, > 0) that also writes traj; Z (N x m) = z^(T).
  *
  * conv_slista_backward: dalpha (device, T floats) = the sub-gradient with
  * respect to alpha of sum_i F_{x_i}(z_i^(T)) (Eq. lasso), from the traj of a
@@ -404,15 +410,16 @@ SLISTA_API int conv_slista_forward(const float *filters, int K, int Lf, const fl
  * n, N, T) bytes of device memory (256-byte aligned; per-CTA partial sums,
  * reduced in FP64 in a fixed order, so the result is run-to-run identical);
  * 0 when the sizes are outside the limits.  Limits: Lf <= 32 and the padded
- * filters, signal, residual, per-filter partial sums and three code vectors
+ * filters, signal, residual, per-pair partial sums and three code vectors
  * within 200 KiB of shared memory (SLISTA_ERR_UNSUPPORTED beyond). */
+SLISTA_API size_t conv_slista_traj_floats(int K, int Lf, int n, int N, int T);
 SLISTA_API size_t conv_slista_backward_workspace_bytes(int K, int Lf, int n, int N, int T);
 SLISTA_API int conv_slista_forward_traj(const float *filters, int K, int Lf, const float *X, int N, int n,
                                         float lam, const float *alpha, int T, float *Z, float *traj,
-                                        void *stream);
+                                        size_t traj_floats, void *stream);
 SLISTA_API int conv_slista_backward(const float *filters, int K, int Lf, const float *X, int N, int n,
-                                    float lam, const float *alpha, int T, const float *traj, float *dalpha,
-                                    void *ws, size_t ws_bytes, void *stream);
+                                    float lam, const float *alpha, int T, const float *traj, size_t traj_floats,
+                                    float *dalpha, void *ws, size_t ws_bytes, void *stream);
 
 /* Per-sample Lasso objective (Eq. lasso) evaluated from the Gram quantities,
  *     F_i = 1/2 xsq_i - c_i^T z_i + 1/2 z_i^T B z_i + lam ||z_i||_1,

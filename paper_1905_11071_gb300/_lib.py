@@ -45,13 +45,14 @@ EXPORTS = [
     "slista_wait_probe", "lista_workspace_bytes", "lista_forward", "slista_set_tile_rows",
     "slista_get_tile_rows", "slista_set_oista_fused", "slista_get_oista_fused", "conv_slista_forward",
     "conv_slista_backward_workspace_bytes", "conv_slista_forward_traj", "conv_slista_backward",
+    "conv_slista_traj_floats",
 ]
 
 
 # entry points that return a size (size_t): every other one returns an int status
 SIZE_RETURNING = ("slista_workspace_bytes", "slista_ckpt_floats", "slista_mask_words",
                   "slista_batched_workspace_bytes", "slista_traj_floats", "lista_workspace_bytes",
-                  "conv_slista_backward_workspace_bytes")
+                  "conv_slista_backward_workspace_bytes", "conv_slista_traj_floats")
 
 
 class Problem(ctypes.Structure):
@@ -119,8 +120,10 @@ def load(path: str = LIB_PATH):
         lib.conv_slista_forward.argtypes = [vp, i, i, vp, i, i, f, vp, vp, i, vp, vp]
         lib.conv_slista_backward_workspace_bytes.restype = sz
         lib.conv_slista_backward_workspace_bytes.argtypes = [i, i, i, i, i]
-        lib.conv_slista_forward_traj.argtypes = [vp, i, i, vp, i, i, f, vp, i, vp, vp, vp]
-        lib.conv_slista_backward.argtypes = [vp, i, i, vp, i, i, f, vp, i, vp, vp, vp, sz, vp]
+        lib.conv_slista_traj_floats.restype = sz
+        lib.conv_slista_traj_floats.argtypes = [i, i, i, i, i]
+        lib.conv_slista_forward_traj.argtypes = [vp, i, i, vp, i, i, f, vp, i, vp, vp, sz, vp]
+        lib.conv_slista_backward.argtypes = [vp, i, i, vp, i, i, f, vp, i, vp, sz, vp, vp, sz, vp]
         pp = ctypes.POINTER(Problem)
         lib.slista_batched_workspace_bytes.restype = sz
         lib.slista_batched_workspace_bytes.argtypes = [i, pp, i, i, i, i]
@@ -409,9 +412,19 @@ def conv_slista_backward_workspace_bytes(K: int, Lf: int, n: int, N: int, T: int
     return int(load().conv_slista_backward_workspace_bytes(int(K), int(Lf), int(n), int(N), int(T)))
 
 
+def conv_slista_traj_floats(K: int, Lf: int, n: int, N: int, T: int) -> int:
+    return int(load().conv_slista_traj_floats(int(K), int(Lf), int(n), int(N), int(T)))
+
+
+def conv_traj_shape(K: int, Lf: int, n: int, N: int, T: int):
+    """Shape of the trajectory buffer: N x T x K x PQ, PQ = P rounded up to 4."""
+    P = n - Lf + 1
+    return (N, T, K, (P + 3) // 4 * 4)
+
+
 def conv_slista_forward_traj(filters, X, lam, alpha, Z, traj, stream=None) -> None:
-    """conv_slista_forward with steps alpha that also writes traj, N x T x m
-    (z^(t+1) of every layer t)."""
+    """conv_slista_forward with steps alpha that also writes traj
+    (conv_traj_shape: z^(t+1) of every layer t, maps padded to PQ)."""
     import torch
     K, Lf = filters.shape
     N, n = X.shape
@@ -421,9 +434,9 @@ def conv_slista_forward_traj(filters, X, lam, alpha, Z, traj, stream=None) -> No
     _need(X, torch.float32, (N, n), "X")
     _need(alpha, torch.float32, (T,), "alpha")
     _need(Z, torch.float32, (N, m), "Z")
-    _need(traj, torch.float32, (N, T, m), "traj")
+    _need(traj, torch.float32, conv_traj_shape(K, Lf, n, N, T), "traj")
     _check(load().conv_slista_forward_traj(_ptr(filters), K, Lf, _ptr(X), N, n, float(lam), _ptr(alpha), T, _ptr(Z),
-                                           _ptr(traj), _stream(stream)), "conv_slista_forward_traj")
+                                           _ptr(traj), traj.numel(), _stream(stream)), "conv_slista_forward_traj")
 
 
 def conv_slista_backward(filters, X, lam, alpha, traj, dalpha, ws=None, stream=None) -> None:
@@ -432,15 +445,15 @@ def conv_slista_backward(filters, X, lam, alpha, traj, dalpha, ws=None, stream=N
     K, Lf = filters.shape
     N, n = X.shape
     T = alpha.shape[0]
-    m = K * (n - Lf + 1)
     _need(filters, torch.float32, (K, Lf), "filters")
     _need(X, torch.float32, (N, n), "X")
     _need(alpha, torch.float32, (T,), "alpha")
-    _need(traj, torch.float32, (N, T, m), "traj")
+    _need(traj, torch.float32, conv_traj_shape(K, Lf, n, N, T), "traj")
     _need(dalpha, torch.float32, (T,), "dalpha")
     wsb = 0 if ws is None else ws.numel() * ws.element_size()
     _check(load().conv_slista_backward(_ptr(filters), K, Lf, _ptr(X), N, n, float(lam), _ptr(alpha), T, _ptr(traj),
-                                       _ptr(dalpha), _ptr(ws), wsb, _stream(stream)), "conv_slista_backward")
+                                       traj.numel(), _ptr(dalpha), _ptr(ws), wsb, _stream(stream)),
+           "conv_slista_backward")
 
 
 def lista_forward(D, X, W, alpha, beta, lam, Z, ws=None, stream=None) -> None:

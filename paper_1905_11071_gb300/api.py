@@ -240,14 +240,14 @@ def conv_slista(filters, X, lam, alpha=None, L=None, T=None, stream=None) -> tor
 def conv_slista_grad(filters, X, lam, alpha, stream=None):
     """Step-LISTA on a 1-D convolutional dictionary and the sub-gradient of
     sum_i F_{x_i}(z_i^(T)) with respect to its steps alpha (Eq. steprec).
-    Returns (Z, dalpha); the trajectory (N x T x m floats) lives only for
-    the call."""
+    Returns (Z, dalpha); the trajectory (N x T x K x P rounded up to 4
+    floats) lives only for the call."""
     K, Lf = filters.shape
     N, n = X.shape
     T = int(alpha.shape[0])
     m = K * (n - Lf + 1)
     Z = torch.empty((N, m), dtype=torch.float32, device=X.device)
-    traj = torch.empty((N, T, m), dtype=torch.float32, device=X.device)
+    traj = torch.empty(_lib.conv_traj_shape(K, Lf, n, N, T), dtype=torch.float32, device=X.device)
     dalpha = torch.empty((T,), dtype=torch.float32, device=X.device)
     ws = workspace(_lib.conv_slista_backward_workspace_bytes(K, Lf, n, N, T), X.device, "conv_bwd")
     _lib.conv_slista_forward_traj(filters, X, lam, alpha, Z, traj, stream=stream)

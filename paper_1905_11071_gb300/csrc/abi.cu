@@ -470,27 +470,48 @@ size_t conv_slista_backward_workspace_bytes(int K, int Lf, int n, int N, int T)
     return conv::backward_ws_bytes(K, Lf, n, N, T);
 }
 
+size_t conv_slista_traj_floats(int K, int Lf, int n, int N, int T)
+{
+    if (K < 1 || Lf < 1 || n < Lf || N < 0 || T < 1) return 0;
+    return conv::traj_floats(K, Lf, n, N, T);
+}
+
+static int conv_traj_buffer_check(const char *fn, const float *traj, size_t traj_floats, int K, int Lf, int n, int N,
+                                  int T)
+{
+    const size_t need = conv::traj_floats(K, Lf, n, N, T);
+    SLISTA_REQUIRE(traj_floats >= need, SLISTA_ERR_WORKSPACE,
+                   "%s: traj of %zu floats (conv_slista_traj_floats) needed, %zu given", fn, need, traj_floats);
+    SLISTA_REQUIRE(need == 0 || (reinterpret_cast<uintptr_t>(traj) & 15) == 0, SLISTA_ERR_ARG,
+                   "%s: traj must be 16-byte aligned", fn);
+    return SLISTA_OK;
+}
+
 int conv_slista_forward_traj(const float *filters, int K, int Lf, const float *X, int N, int n, float lam,
-                             const float *alpha, int T, float *Z, float *traj, void *stream)
+                             const float *alpha, int T, float *Z, float *traj, size_t traj_floats, void *stream)
 {
     clear_error();
     int rc = conv_traj_check("conv_slista_forward_traj", filters, K, Lf, alpha, N, n, T, lam);
     if (rc) return rc;
     SLISTA_REQUIRE(N == 0 || (X && Z && traj), SLISTA_ERR_ARG,
                    "conv_slista_forward_traj: X, Z and traj must not be NULL");
+    rc = conv_traj_buffer_check("conv_slista_forward_traj", traj, traj_floats, K, Lf, n, N, T);
+    if (rc) return rc;
     ConvArgs a{filters, K, Lf, X, N, n, lam, alpha, nullptr, T, Z};
     return conv::launch_forward_traj(a, traj, as_stream(stream));
 }
 
 int conv_slista_backward(const float *filters, int K, int Lf, const float *X, int N, int n, float lam,
-                         const float *alpha, int T, const float *traj, float *dalpha, void *ws, size_t ws_bytes,
-                         void *stream)
+                         const float *alpha, int T, const float *traj, size_t traj_floats, float *dalpha, void *ws,
+                         size_t ws_bytes, void *stream)
 {
     clear_error();
     int rc = conv_traj_check("conv_slista_backward", filters, K, Lf, alpha, N, n, T, lam);
     if (rc) return rc;
     SLISTA_REQUIRE(dalpha && (N == 0 || (X && traj)), SLISTA_ERR_ARG,
                    "conv_slista_backward: dalpha, X and traj must not be NULL");
+    rc = conv_traj_buffer_check("conv_slista_backward", traj, traj_floats, K, Lf, n, N, T);
+    if (rc) return rc;
     const size_t need = N > 0 ? conv::backward_ws_bytes(K, Lf, n, N, T) : 0;
     SLISTA_REQUIRE(ws_bytes >= need && (need == 0 || (ws && ws_aligned(ws))), SLISTA_ERR_WORKSPACE,
                    "conv_slista_backward: workspace of %zu bytes (256-byte aligned) needed, %zu given", need,

@@ -84,42 +84,47 @@ __global__ void __launch_bounds__(NT) conv_pgd_kernel(const float *__restrict__ 
 }
 
 // The same layers with register blocking, for filters of at most LF taps
-// (zero-padded to LF, LF a multiple of 4), in CTAs of NB threads: a work item
-// is JB consecutive outputs of one filter, computed from a window of inputs
-// read as 16-byte vectors (conflict-free: the items of a warp read one
-// contiguous segment) and the taps of its filter (16-byte vectors, the same
-// for the whole warp).  Each code map lives in shared memory with LF zeros on
-// its left and at least LF on its right, the residual with zeros after it,
-// so no item needs bounds checks.  Per layer:
-//   1. y_k[i] = sum_l d_k[l] z_k[i - l] for every filter and i < n  (items k, i-block)
-//   2. r[i] = sum_k y_k[i] - x[i]                                    (fixed order over k)
-//   3. z_k[j] = ST(z_k[j] - a sum_l d_k[l] r[j + l], a lam)          (items k, j-block)
+// (zero-padded to LF, LF a multiple of 4), in CTAs of NB threads.  The
+// filters are taken in groups of KG (K rounded up with all-zero filters); a
+// work item is JB = 4 consecutive outputs for one group, computed from
+// windows of inputs read as 16-byte vectors (conflict-free: the items of a
+// warp read one contiguous segment) and the group's taps (16-byte vectors,
+// the same for the whole warp).  Each code map lives in shared memory with
+// LF zeros on its left and at least LF on its right, the residual with zeros
+// after it, so no item needs bounds checks.  Per layer:
+//   1. y_g[i] = sum_{k in g} sum_l d_k[l] z_k[i - l], i < n   (items g, i-block; k in order)
+//   2. r[i] = sum_g y_g[i] - x[i]                              (fixed order over g)
+//   3. z_k[j] = ST(z_k[j] - a sum_l d_k[l] r[j + l], a lam)    (items g, j-block: one window of r
+//                                                                for the group's filters)
 constexpr int NB = 128;  // threads of a blocked CTA
-constexpr int JB = 8;    // outputs of a work item
+constexpr int JB = 4;    // outputs of a work item
+constexpr int KG = 2;    // filters of a work item
 __host__ __device__ constexpr int up4(int v) { return (v + 3) & ~3; }
 
 template <int LF>
 struct Blk {
-    static_assert(LF % 4 == 0 && JB % 4 == 0 && JB <= LF + 2, "16-byte units; windows within the zero pads");
+    static_assert(LF % 4 == 0, "taps in 16-byte units");
     static constexpr int WV = (LF + JB) / 4;  // 16-byte units of a window
-    int P, XS, RS, YS, PS;                     // positions; strides of x, r, y, the padded maps
+    int P, Kp, NG;                             // positions; filters rounded up to groups; groups
+    int XS, RS, YS, PS;                        // strides of x, r, y, the padded maps
     __host__ __device__ Blk(int K, int Lf, int n)
     {
         P = n - Lf + 1;
+        Kp = (K + KG - 1) / KG * KG;
+        NG = Kp / KG;
         XS = up4(n);
         RS = up4(n + LF + JB);
         YS = up4(n + JB);
         PS = up4(LF + P + LF);
-        (void)K;
     }
     // floats: taps, x, r, y, maps, and one window past the last map
-    __host__ __device__ size_t floats(int K) const
+    __host__ __device__ size_t floats() const
     {
-        return (size_t)K * LF + XS + RS + (size_t)K * YS + (size_t)K * PS + 4 * WV;
+        return (size_t)Kp * LF + XS + RS + (size_t)NG * YS + (size_t)Kp * PS + 4 * WV;
     }
 };
 
-// n floats (a multiple of 4) from 16-byte aligned shared memory into registers
+// 4 NV floats from 16-byte aligned shared memory into registers
 template <int NV>
 __device__ __forceinline__ void load_vec(const float *src, float (&w)[4 * NV])
 {
@@ -133,71 +138,103 @@ __device__ __forceinline__ void load_vec(const float *src, float (&w)[4 * NV])
     }
 }
 
-struct Outs {
-    float v[JB];
-};
-
-// 1. y_k = d_k * u_k for the padded maps u (map k at u + k PS, data from LF)
+// taps of the Kp padded filters (zero past Lf and for k >= K)
 template <int LF>
-__device__ __forceinline__ void phase_dz(const float *d, const float *u, float *y, int K, int nb, int PS, int YS)
+__device__ __forceinline__ void load_taps(const float *F, int K, int Kp, int Lf, float *d)
 {
-    constexpr int WV = Blk<LF>::WV;
-#pragma unroll 1
-    for (int it = threadIdx.x; it < K * nb; it += NB) {
-        const int k = it / nb, i0 = (it - k * nb) * JB;
-        float dk[LF], w[4 * WV];
-        load_vec<LF / 4>(d + k * LF, dk);
-        load_vec<WV>(u + (size_t)k * PS + i0, w);  // u_k[i0 + jj - l] = w[LF + jj - l]
-        float acc[JB];
-#pragma unroll
-        for (int jj = 0; jj < JB; ++jj) acc[jj] = 0.0f;
-#pragma unroll
-        for (int l = 0; l < LF; ++l)
-#pragma unroll
-            for (int jj = 0; jj < JB; ++jj) acc[jj] = fmaf(dk[l], w[LF + jj - l], acc[jj]);
-        float4 *yo = reinterpret_cast<float4 *>(y + (size_t)k * YS + i0);
-#pragma unroll
-        for (int q = 0; q < JB / 4; ++q) yo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    for (int e = threadIdx.x; e < Kp * LF; e += NB) {
+        const int k = e / LF, l = e - k * LF;
+        d[e] = (k < K && l < Lf) ? __ldg(F + k * Lf + l) : 0.0f;
     }
 }
 
-// 2. r = sum_k y_k (- x, when given), the filters in a fixed order
-__device__ __forceinline__ void phase_sum(const float *y, const float *x, float *r, int K, int n, int YS)
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned)
+__device__ __forceinline__ void cp_async16(float *dst, const float *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+
+// 1. y_g = sum_{k in g} d_k * u_k for the padded maps u (map k at u + k PS, data from LF)
+// A thread's work items are it = tid, tid + NB, ... of NG x nb; (g, b) of the
+// first comes from the caller (one division per kernel), the next by stepping.
+struct Item {
+    int g, b, dg, db;  // current item; the step NB = dg nb + db
+    __device__ Item(int it, int nb) : g(it / nb), b(it % nb), dg(NB / nb), db(NB % nb) {}
+    __device__ __forceinline__ void next(int nb)
+    {
+        g += dg;
+        b += db;
+        if (b >= nb) b -= nb, ++g;
+    }
+};
+
+template <int LF>
+__device__ __forceinline__ void phase_dz(const float *d, const float *u, float *y, int NG, int nb, Item c, int PS,
+                                         int YS)
+{
+    constexpr int WV = Blk<LF>::WV;
+#pragma unroll 1
+    for (; c.g < NG; c.next(nb)) {
+        const int g = c.g, i0 = c.b * JB;
+        float acc[JB] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int q = 0; q < KG; ++q) {
+            const int k = g * KG + q;
+            float dk[LF], w[4 * WV];
+            load_vec<LF / 4>(d + k * LF, dk);
+            load_vec<WV>(u + (k * PS + i0), w);  // u_k[i0 + jj - l] = w[LF + jj - l]
+#pragma unroll
+            for (int l = 0; l < LF; ++l)
+#pragma unroll
+                for (int jj = 0; jj < JB; ++jj) acc[jj] = fmaf(dk[l], w[LF + jj - l], acc[jj]);
+        }
+        *reinterpret_cast<float4 *>(y + (g * YS + i0)) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    }
+}
+
+// 2. r = sum_g y_g (- x, when given), the groups in a fixed order
+__device__ __forceinline__ void phase_sum(const float *y, const float *x, float *r, int NG, int n, int YS)
 {
     for (int i = threadIdx.x; i < n; i += NB) {
         float acc = 0.0f;
-        for (int k = 0; k < K; ++k) acc += y[(size_t)k * YS + i];
+        for (int g = 0; g < NG; ++g) acc += y[g * YS + i];
         r[i] = x ? acc - x[i] : acc;
     }
 }
 
-// 3. (D^T r)_k[j0 .. j0 + JB - 1] for each item, handed to f(k, j0, g)
-// (g.v[jj] valid for j0 + jj < P)
+// 3. (D^T r)_k[j0 .. j0 + 3] for each filter k of each item, handed to
+// f(k, j0, g) as a float4 (component jj valid for j0 + jj < P; k may be a
+// padding filter, k >= K)
 template <int LF, class Fn>
-__device__ __forceinline__ void phase_dtr(const float *d, const float *r, int K, int pb, Fn f)
+__device__ __forceinline__ void phase_dtr(const float *d, const float *r, int NG, int pb, Item c, Fn f)
 {
     constexpr int WV = Blk<LF>::WV;
 #pragma unroll 1
-    for (int it = threadIdx.x; it < K * pb; it += NB) {
-        const int k = it / pb, j0 = (it - k * pb) * JB;
-        float dk[LF], w[4 * WV];
-        load_vec<LF / 4>(d + k * LF, dk);
+    for (; c.g < NG; c.next(pb)) {
+        const int g = c.g, j0 = c.b * JB;
+        float w[4 * WV];
         load_vec<WV>(r + j0, w);
-        Outs g;
 #pragma unroll
-        for (int jj = 0; jj < JB; ++jj) g.v[jj] = 0.0f;
+        for (int q = 0; q < KG; ++q) {
+            const int k = g * KG + q;
+            float dk[LF];
+            load_vec<LF / 4>(d + k * LF, dk);
+            float o[JB] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int l = 0; l < LF; ++l)
+            for (int l = 0; l < LF; ++l)
 #pragma unroll
-            for (int jj = 0; jj < JB; ++jj) g.v[jj] = fmaf(dk[l], w[jj + l], g.v[jj]);
-        f(k, j0, g);
+                for (int jj = 0; jj < JB; ++jj) o[jj] = fmaf(dk[l], w[jj + l], o[jj]);
+            f(k, j0, make_float4(o[0], o[1], o[2], o[3]));
+        }
     }
 }
 
-// Forward; with traj, z^(t+1) of every layer t is written to traj (sample
-// s, layer t at (s T + t) m), the input of the adjoint below.
+// Forward; with traj, z^(t+1) of every layer t is written to traj, the input
+// of the adjoint below: sample s, layer t, map k at ((s T + t) K + k) PQ, PQ =
+// P rounded up to a multiple of 4 (entries past P zero), so that every item
+// stores 16 bytes and the adjoint loads 16 bytes at a time.
 template <int LF, bool TRAJ>
-__global__ void __launch_bounds__(NB) conv_pgd_blk_kernel(const float *__restrict__ F, int K, int Lf,
+__global__ void __launch_bounds__(NB, LF >= 32 ? 7 : 10) conv_pgd_blk_kernel(const float *__restrict__ F, int K, int Lf,
                                                           const float *__restrict__ X, int N, int n, float lam,
                                                           const float *__restrict__ alpha,
                                                           const double *__restrict__ Lp, int T, float *__restrict__ Z,
@@ -205,65 +242,66 @@ __global__ void __launch_bounds__(NB) conv_pgd_blk_kernel(const float *__restric
 {
     constexpr int WV = Blk<LF>::WV;
     const Blk<LF> bl(K, Lf, n);
-    const int P = bl.P, m = K * P, PS = bl.PS, YS = bl.YS;
+    const int P = bl.P, m = K * P, PS = bl.PS, YS = bl.YS, NG = bl.NG;
     extern __shared__ float4 sm4[];
-    float *d = reinterpret_cast<float *>(sm4);  // K x LF taps (zero past Lf)
-    float *x = d + K * LF;                      // n
+    float *d = reinterpret_cast<float *>(sm4);  // Kp x LF taps
+    float *x = d + bl.Kp * LF;                  // n
     float *r = x + bl.XS;                       // n, then zeros
-    float *y = r + bl.RS;                       // K x YS: per-filter partial sums of D z
-    float *z = y + (size_t)K * YS;              // K x PS: map k at [k PS + LF, k PS + LF + P)
-    const int nb = (n + JB - 1) / JB;           // output blocks of D z per filter
-    const int pb = (P + JB - 1) / JB;           // output blocks of D^T r per filter
+    float *y = r + bl.RS;                       // NG x YS: per-group partial sums of D z
+    float *z = y + (size_t)NG * YS;             // Kp x PS: map k at [k PS + LF, k PS + LF + P)
+    const int nb = (n + JB - 1) / JB;           // output blocks of D z
+    const int pb = (P + JB - 1) / JB;           // output blocks of D^T r
     const int tid = threadIdx.x;
-    for (int e = tid; e < K * LF; e += NB) {
-        const int k = e / LF, l = e - k * LF;
-        d[e] = l < Lf ? __ldg(F + k * Lf + l) : 0.0f;
-    }
+    const Item it_dz(tid, nb), it_dtr(tid, pb);
+    const size_t mq = (size_t)K * up4(P);       // floats of one layer in traj
+    load_taps<LF>(F, K, bl.Kp, Lf, d);
     const float a_const = alpha ? 0.0f : (float)(1.0 / __ldg(Lp));
 #pragma unroll 1
     for (int s = blockIdx.x; s < N; s += gridDim.x) {
         __syncthreads();  // the previous sample's codes are stored
         for (int e = tid; e < n; e += NB) x[e] = __ldg(X + (size_t)s * n + e);
         for (int e = tid; e < bl.RS; e += NB) r[e] = 0.0f;
-        for (int e = tid; e < K * PS + 4 * WV; e += NB) z[e] = 0.0f;
+        for (int e = tid; e < bl.Kp * PS + 4 * WV; e += NB) z[e] = 0.0f;
         __syncthreads();
 #pragma unroll 1
         for (int t = 0; t < T; ++t) {
             const float a = alpha ? __ldg(alpha + t) : a_const;
             const float thr = __fmul_rn(a, lam);
-            phase_dz<LF>(d, z, y, K, nb, PS, YS);
+            phase_dz<LF>(d, z, y, NG, nb, it_dz, PS, YS);
             __syncthreads();
-            phase_sum(y, x, r, K, n, YS);
+            phase_sum(y, x, r, NG, n, YS);
             __syncthreads();
-            phase_dtr<LF>(d, r, K, pb, [&](int k, int j0, Outs g) {
-                float *zk = z + (size_t)k * PS + LF + j0;
+            // the step; with TRAJ the new codes also go to traj (16-byte stores)
+            float *zt = TRAJ ? traj + ((size_t)s * T + t) * mq : nullptr;
+            phase_dtr<LF>(d, r, NG, pb, it_dtr, [&](int k, int j0, float4 g4) {
+                if (k >= K) return;
+                const float g[JB] = {g4.x, g4.y, g4.z, g4.w};
+                float *zk = z + (k * PS + LF + j0);
+                float zz[JB];
                 if (j0 + JB <= P) {
+                    const float4 v = *reinterpret_cast<const float4 *>(zk);
+                    zz[0] = v.x, zz[1] = v.y, zz[2] = v.z, zz[3] = v.w;
 #pragma unroll
-                    for (int q = 0; q < JB / 4; ++q) {
-                        const float4 v = reinterpret_cast<const float4 *>(zk)[q];
-                        float zz[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) {
-                            const float u = fmaf(-a, g.v[4 * q + jj], zz[jj]);
-                            zz[jj] = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
-                        }
-                        reinterpret_cast<float4 *>(zk)[q] = make_float4(zz[0], zz[1], zz[2], zz[3]);
+                    for (int jj = 0; jj < JB; ++jj) {
+                        const float u = fmaf(-a, g[jj], zz[jj]);
+                        zz[jj] = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
                     }
+                    *reinterpret_cast<float4 *>(zk) = make_float4(zz[0], zz[1], zz[2], zz[3]);
                 } else {
 #pragma unroll
-                    for (int jj = 0; jj < JB; ++jj)
+                    for (int jj = 0; jj < JB; ++jj) {
+                        zz[jj] = 0.0f;
                         if (j0 + jj < P) {
-                            const float u = fmaf(-a, g.v[jj], zk[jj]);
-                            zk[jj] = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
+                            const float u = fmaf(-a, g[jj], zk[jj]);
+                            zz[jj] = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
+                            zk[jj] = zz[jj];
                         }
+                    }
                 }
+                if (TRAJ)
+                    *reinterpret_cast<float4 *>(zt + (k * up4(P) + j0)) = make_float4(zz[0], zz[1], zz[2], zz[3]);
             });
             __syncthreads();
-            if (TRAJ)
-                for (int e = tid; e < m; e += NB) {
-                    const int k = e / P, j = e - k * P;
-                    traj[((size_t)s * T + t) * m + e] = z[(size_t)k * PS + LF + j];
-                }
         }
         for (int e = tid; e < m; e += NB) {
             const int k = e / P, j = e - k * P;
@@ -277,10 +315,15 @@ __global__ void __launch_bounds__(NB) conv_pgd_blk_kernel(const float *__restric
 //   h = G * [z^(t+1) != 0];  dalpha_t += <h, z^(t+1) - z^(t)> / alpha_t;
 //   G = h - alpha_t D^T (D h)
 // (on the support of z^(t+1), dz^(t+1)/dalpha_t = (z^(t+1) - z^(t)) / alpha_t).
-// The CTA's per-layer sums of <h, z^(t+1) - z^(t)> over its samples go to
-// partial[t gridDim.x + block]; the division by alpha_t is left to the reduction.
+// The masking and the dot product of layer t - 1 are done in the epilogue of
+// layer t's D^T product, so each layer is one pass of the three phases.  The
+// adjoint state and two code vectors (z^(t), z^(t-1), the next arriving by
+// cp.async while the products run) are kept per map with a 16-byte aligned
+// stride PQ.  The CTA's per-layer sums of <h, z^(t+1) - z^(t)> over its
+// samples go to partial[t gridDim.x + block]; the division by alpha_t is left
+// to the reduction.
 template <int LF>
-__global__ void __launch_bounds__(NB, 8) conv_adjoint_blk_kernel(const float *__restrict__ F, int K, int Lf,
+__global__ void __launch_bounds__(NB, LF == 16 ? 9 : (LF >= 32 ? 7 : 8)) conv_adjoint_blk_kernel(const float *__restrict__ F, int K, int Lf,
                                                               const float *__restrict__ X, int N, int n, float lam,
                                                               const float *__restrict__ alpha, int T,
                                                               const float *__restrict__ traj,
@@ -288,99 +331,117 @@ __global__ void __launch_bounds__(NB, 8) conv_adjoint_blk_kernel(const float *__
 {
     constexpr int WV = Blk<LF>::WV;
     const Blk<LF> bl(K, Lf, n);
-    const int P = bl.P, m = K * P, PS = bl.PS, YS = bl.YS;
+    const int P = bl.P, PS = bl.PS, YS = bl.YS, NG = bl.NG, PQ = up4(P);
+    const int mq = K * PQ;                      // floats of one layer in traj
     extern __shared__ float4 sm4[];
-    float *d = reinterpret_cast<float *>(sm4);  // K x LF taps
-    float *x = d + K * LF;                      // n
+    float *d = reinterpret_cast<float *>(sm4);  // Kp x LF taps
+    float *x = d + bl.Kp * LF;                  // n
     float *r = x + bl.XS;                       // n, then zeros
-    float *y = r + bl.RS;                       // K x YS
-    float *u = y + (size_t)K * YS;              // K x PS: padded maps (z^(T), then h)
-    float *G = u + (size_t)K * PS + 4 * WV;     // m: the adjoint state
-    float *zn = G + up4(m);                     // three rotating code buffers: z^(t+1),
-    float *zo = zn + up4(m);                    // z^(t),
-    float *zp = zo + up4(m);                    // and z^(t-1) arriving (cp.async)
-    float *acc = zp + up4(m);                   // NB / 32 x T: each warp's sums of alpha_t dalpha_t
+    float *y = r + bl.RS;                       // NG x YS
+    float *u = y + (size_t)NG * YS;             // Kp x PS: padded maps (z^(T), then h)
+    float *G = u + (size_t)bl.Kp * PS + 4 * WV; // K x PQ: the adjoint state
+    float *zc = G + (size_t)K * PQ;             // K x PQ: z^(t)
+    float *zp = zc + (size_t)K * PQ;            // K x PQ: z^(t-1)
+    float *acc = zp + (size_t)K * PQ;           // NB / 32 x T: each warp's sums of alpha_t dalpha_t
     const int nb = (n + JB - 1) / JB, pb = (P + JB - 1) / JB;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < K * LF; e += NB) {
-        const int k = e / LF, l = e - k * LF;
-        d[e] = l < Lf ? __ldg(F + k * Lf + l) : 0.0f;
-    }
+    const Item it_dz(tid, nb), it_dtr(tid, pb);
+    load_taps<LF>(F, K, bl.Kp, Lf, d);
     for (int e = tid; e < (NB / 32) * T; e += NB) acc[e] = 0.0f;
+    // the dot product of layer tt: this thread's part, summed over the warp
+    auto add_part = [&](float part, int tt) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) acc[warp * T + tt] += part;
+    };
+    // layer tt's mask and dot product for codes (k, j0 .. j0 + 3) given the new
+    // adjoint state gv: h = gv on the support of znew; part += <h, znew - zold>;
+    // h to the padded maps and to G
+    auto mask_step = [&](int k, int j0, const float (&gv)[JB], const float *znew, const float *zold, float &part) {
+        const int q = k * PQ + j0;
+        float zn4[JB], zo4[JB], h[JB];
+        load_vec<1>(znew + q, zn4);
+        load_vec<1>(zold + q, zo4);
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {  // past P the codes are zero, so h is too
+            h[jj] = zn4[jj] != 0.0f ? gv[jj] : 0.0f;
+            part = fmaf(h[jj], zn4[jj] - zo4[jj], part);
+        }
+        const float4 h4 = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4 *>(G + q) = h4;
+        *reinterpret_cast<float4 *>(u + (k * PS + LF + j0)) = h4;  // zeros past P keep the pad
+    };
+    // codes of layer tt of this sample (z^(tt+1), K x PQ; zeros for tt < 0), 16 bytes at a time
+    auto fetch = [&](const float *ts, int tt, float *dst, bool async) {
+        const float *src = ts + (size_t)tt * mq;
+        for (int e = 4 * tid; e < mq; e += 4 * NB) {
+            if (tt < 0)
+                *reinterpret_cast<float4 *>(dst + e) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            else if (async)
+                cp_async16(dst + e, src + e);
+            else
+                *reinterpret_cast<float4 *>(dst + e) = __ldg(reinterpret_cast<const float4 *>(src + e));
+        }
+    };
 #pragma unroll 1
     for (int s = blockIdx.x; s < N; s += gridDim.x) {
-        const float *ts = traj + (size_t)s * T * m;
+        const float *ts = traj + (size_t)s * T * mq;
         __syncthreads();
         for (int e = tid; e < n; e += NB) x[e] = __ldg(X + (size_t)s * n + e);
         for (int e = tid; e < bl.RS; e += NB) r[e] = 0.0f;
-        for (int e = tid; e < K * PS + 4 * WV; e += NB) u[e] = 0.0f;
+        for (int e = tid; e < bl.Kp * PS + 4 * WV; e += NB) u[e] = 0.0f;
+        fetch(ts, T - 1, zc, false);  // z^(T)
+        fetch(ts, T - 2, zp, false);  // z^(T-1)
         __syncthreads();
-        for (int e = tid; e < m; e += NB) {
-            const int k = e / P, j = e - k * P;
-            const float v = __ldg(ts + (size_t)(T - 1) * m + e);
-            zn[e] = v;
-            u[(size_t)k * PS + LF + j] = v;
-            zo[e] = T >= 2 ? __ldg(ts + (size_t)(T - 2) * m + e) : 0.0f;
+        // z^(T) into the padded maps (16 bytes at a time: the entries past P are zero)
+        for (int e = 4 * tid; e < mq; e += 4 * NB) {
+            const int k = e / PQ, j = e - k * PQ;
+            *reinterpret_cast<float4 *>(u + (size_t)k * PS + LF + j) = *reinterpret_cast<const float4 *>(zc + e);
         }
         __syncthreads();
-        // G = D^T (D z^(T) - x) + lam sign(z^(T))
-        phase_dz<LF>(d, u, y, K, nb, PS, YS);
+        // G = D^T (D z^(T) - x) + lam sign(z^(T)), then layer T-1's mask and dot product
+        phase_dz<LF>(d, u, y, NG, nb, it_dz, PS, YS);
         __syncthreads();
-        phase_sum(y, x, r, K, n, YS);
+        phase_sum(y, x, r, NG, n, YS);
         __syncthreads();
-        phase_dtr<LF>(d, r, K, pb, [&](int k, int j0, Outs g) {
+        float part = 0.0f;
+        phase_dtr<LF>(d, r, NG, pb, it_dtr, [&](int k, int j0, float4 g4) {
+            if (k >= K) return;
+            const float g[JB] = {g4.x, g4.y, g4.z, g4.w};
+            float gv[JB];
+            const float *zk = zc + (k * PQ + j0);
 #pragma unroll
-            for (int jj = 0; jj < JB; ++jj)
-                if (j0 + jj < P) {
-                    const int e = k * P + j0 + jj;
-                    const float z = zn[e];
-                    G[e] = g.v[jj] + lam * (float)((z > 0.0f) - (z < 0.0f));
-                }
+            for (int jj = 0; jj < JB; ++jj) gv[jj] = g[jj] + lam * (float)((zk[jj] > 0.0f) - (zk[jj] < 0.0f));
+            mask_step(k, j0, gv, zc, zp, part);
         });
-        __syncthreads();
+        add_part(part, T - 1);
 #pragma unroll 1
-        for (int t = T - 1; t >= 0; --t) {
-            // h = G on the support of z^(t+1), into the padded maps; <h, z^(t+1) - z^(t)>
-            float part = 0.0f;
-            for (int e = tid; e < m; e += NB) {
-                const int k = e / P, j = e - k * P;
-                const float h = zn[e] != 0.0f ? G[e] : 0.0f;
-                part = fmaf(h, zn[e] - zo[e], part);
-                u[(size_t)k * PS + LF + j] = h;
-                G[e] = h;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) acc[warp * T + t] += part;
-            if (t == 0) break;  // G^(0) is not needed
-            // z^(t-1) into the free buffer while the products run (zero for t = 1)
-            if (t >= 2) {
-                for (int e = tid; e < m; e += NB) tc::cp_async4(tc::smem_u32(zp + e), ts + (size_t)(t - 2) * m + e);
-                tc::cp_async_commit();
-            } else {
-                for (int e = tid; e < m; e += NB) zp[e] = 0.0f;
-            }
+        for (int t = T - 1; t >= 1; --t) {
+            // here G = h of layer t (also in the padded maps), zc = z^(t+1), zp = z^(t)
+            float *const zq = zc;  // z^(t+1) is no longer needed: z^(t-1) arrives there
+            zc = zp;
+            zp = zq;
             __syncthreads();
-            // G = h - a D^T (D h)
+            fetch(ts, t - 2, zp, true);
+            tc::cp_async_commit();
+            // G = h - a D^T (D h), then layer t-1's mask and dot product
             const float a = __ldg(alpha + t);
-            phase_dz<LF>(d, u, y, K, nb, PS, YS);
+            phase_dz<LF>(d, u, y, NG, nb, it_dz, PS, YS);
             __syncthreads();
-            phase_sum(y, nullptr, r, K, n, YS);
-            __syncthreads();
-            phase_dtr<LF>(d, r, K, pb, [&](int k, int j0, Outs g) {
-#pragma unroll
-                for (int jj = 0; jj < JB; ++jj)
-                    if (j0 + jj < P) {
-                        const int e = k * P + j0 + jj;
-                        G[e] = fmaf(-a, g.v[jj], G[e]);
-                    }
-            });
+            phase_sum(y, nullptr, r, NG, n, YS);
             tc::cp_async_wait_all();
             __syncthreads();
-            float *const fr = zn;  // z^(t+1) <- z^(t), z^(t) <- z^(t-1)
-            zn = zo;
-            zo = zp;
-            zp = fr;
+            part = 0.0f;
+            phase_dtr<LF>(d, r, NG, pb, it_dtr, [&](int k, int j0, float4 g4) {
+                if (k >= K) return;
+                const float g[JB] = {g4.x, g4.y, g4.z, g4.w};
+                float gv[JB], gk[JB];
+                load_vec<1>(G + (k * PQ + j0), gk);
+#pragma unroll
+                for (int jj = 0; jj < JB; ++jj) gv[jj] = fmaf(-a, g[jj], gk[jj]);
+                mask_step(k, j0, gv, zc, zp, part);
+            });
+            add_part(part, t - 1);
         }
     }
     __syncthreads();
@@ -408,14 +469,13 @@ __global__ void conv_reduce_kernel(const float *__restrict__ partial, int nblk, 
 template <int LF>
 size_t blk_smem_bytes(int K, int Lf, int n)
 {
-    return sizeof(float) * Blk<LF>(K, Lf, n).floats(K);
+    return sizeof(float) * Blk<LF>(K, Lf, n).floats();
 }
 
 template <int LF>
 size_t adj_smem_bytes(int K, int Lf, int n, int T)
 {
-    const int m = K * (n - Lf + 1);
-    return blk_smem_bytes<LF>(K, Lf, n) + sizeof(float) * (4 * (size_t)up4(m) + (size_t)(NB / 32) * T);
+    return blk_smem_bytes<LF>(K, Lf, n) + sizeof(float) * (3 * (size_t)K * up4(n - Lf + 1) + (size_t)(NB / 32) * T);
 }
 
 template <int LF, bool TRAJ>
@@ -522,6 +582,11 @@ int launch_forward(const ConvArgs &a, cudaStream_t st)
 }
 
 bool traj_supported(int K, int Lf, int n, int T) { return T >= 1 && pick_lf(K, Lf, n, T, true) != 0; }
+
+size_t traj_floats(int K, int Lf, int n, int N, int T)
+{
+    return (size_t)N * (size_t)T * (size_t)K * (size_t)up4(n - Lf + 1);
+}
 
 size_t backward_ws_bytes(int K, int Lf, int n, int N, int T)
 {

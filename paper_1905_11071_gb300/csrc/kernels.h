@@ -218,6 +218,7 @@ bool supported(int K, int Lf, int n);
 int launch_forward(const ConvArgs &a, cudaStream_t st);
 // trajectory forward and its adjoint (filters of at most 32 taps)
 bool traj_supported(int K, int Lf, int n, int T);
+size_t traj_floats(int K, int Lf, int n, int N, int T);
 size_t backward_ws_bytes(int K, int Lf, int n, int N, int T);
 int launch_forward_traj(const ConvArgs &a, float *traj, cudaStream_t st);
 int launch_backward(const ConvArgs &a, const float *traj, float *dalpha, void *ws, cudaStream_t st);

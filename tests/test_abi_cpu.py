@@ -154,26 +154,40 @@ def test_conv_gradient_validation_without_gpu(lib):
     filters longer than 32 taps, T = 0 and a short workspace before any
     launch (the pointers are never dereferenced)."""
     vp = ctypes.c_void_p(1)
+    big = 1 << 40
     # n < Lf, T = 0
-    assert lib.conv_slista_forward_traj(vp, 4, 16, vp, 8, 10, 0.1, vp, 5, vp, vp, None) == _lib.SLISTA_ERR_ARG
-    assert lib.conv_slista_forward_traj(vp, 4, 16, vp, 8, 128, 0.1, vp, 0, vp, vp, None) == _lib.SLISTA_ERR_ARG
+    assert lib.conv_slista_forward_traj(vp, 4, 16, vp, 8, 10, 0.1, vp, 5, vp, vp, big, None) == _lib.SLISTA_ERR_ARG
+    assert lib.conv_slista_forward_traj(vp, 4, 16, vp, 8, 128, 0.1, vp, 0, vp, vp, big, None) == _lib.SLISTA_ERR_ARG
     # 33 taps
-    assert lib.conv_slista_forward_traj(vp, 4, 33, vp, 8, 128, 0.1, vp, 5, vp, vp, None) == _lib.SLISTA_ERR_UNSUPPORTED
-    assert lib.conv_slista_backward(vp, 4, 33, vp, 8, 128, 0.1, vp, 5, vp, vp, vp, 1 << 20,
+    assert lib.conv_slista_forward_traj(vp, 4, 33, vp, 8, 128, 0.1, vp, 5, vp, vp, big,
+                                        None) == _lib.SLISTA_ERR_UNSUPPORTED
+    assert lib.conv_slista_backward(vp, 4, 33, vp, 8, 128, 0.1, vp, 5, vp, big, vp, vp, 1 << 20,
                                     None) == _lib.SLISTA_ERR_UNSUPPORTED
     assert _lib.conv_slista_backward_workspace_bytes(4, 33, 128, 8, 5) == 0
     # steps are required (no 1/L form of the adjoint); a null trajectory
-    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, 0.1, None, 5, vp, vp, vp, 1 << 20,
+    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, 0.1, None, 5, vp, big, vp, vp, 1 << 20,
                                     None) == _lib.SLISTA_ERR_ARG
-    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, 0.1, vp, 5, None, vp, vp, 1 << 20,
+    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, 0.1, vp, 5, None, big, vp, vp, 1 << 20,
                                     None) == _lib.SLISTA_ERR_ARG
+    # the trajectory: maps padded to a multiple of 4 (P = 113 -> 116), its length checked, 16-byte aligned
+    assert _lib.conv_slista_traj_floats(4, 16, 128, 8, 5) == 8 * 5 * 4 * 116
+    assert _lib.conv_slista_traj_floats(4, 13, 128, 8, 5) == 8 * 5 * 4 * 116
+    tf = _lib.conv_slista_traj_floats(4, 16, 128, 8, 5)
+    aligned = ctypes.c_void_p(0x1000)
+    assert lib.conv_slista_forward_traj(vp, 4, 16, vp, 8, 128, 0.1, vp, 5, vp, aligned, tf - 1,
+                                        None) == _lib.SLISTA_ERR_WORKSPACE
+    assert lib.conv_slista_forward_traj(vp, 4, 16, vp, 8, 128, 0.1, vp, 5, vp, ctypes.c_void_p(0x1004), tf,
+                                        None) == _lib.SLISTA_ERR_ARG
+    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, 0.1, vp, 5, aligned, tf - 1, vp, vp, 1 << 20,
+                                    None) == _lib.SLISTA_ERR_WORKSPACE
     # workspace: one per-CTA partial per layer
     need = _lib.conv_slista_backward_workspace_bytes(4, 16, 128, 8, 5)
     assert need >= 5 * 4
-    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, 0.1, vp, 5, vp, vp, vp, need - 1,
+    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, 0.1, vp, 5, aligned, tf, vp, vp, need - 1,
                                     None) == _lib.SLISTA_ERR_WORKSPACE
     # negative lambda
-    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, -0.1, vp, 5, vp, vp, vp, need, None) == _lib.SLISTA_ERR_ARG
+    assert lib.conv_slista_backward(vp, 4, 16, vp, 8, 128, -0.1, vp, 5, aligned, tf, vp, vp, need,
+                                    None) == _lib.SLISTA_ERR_ARG
 
 
 def test_python_binding_rejects_cpu_tensors(lib):

@@ -152,14 +152,40 @@ def test_conv_backward_odd_shapes(K, Lf, n, N, T):
 def test_conv_trajectory_is_every_layer():
     """traj[:, t] = z^(t+1): the oracle run for t + 1 layers."""
     from paper_1905_11071_gb300 import _lib
-    w, alpha = _grad_case(8, 16, 128, 100, 12, seed=2)
+    w, alpha = _grad_case(8, 13, 128, 100, 12, seed=2)  # P = 116: maps padded to 116
+    K, Lf = w.filters.shape
+    P = w.n - Lf + 1
     m = w.D.shape[1]
+    shape = _lib.conv_traj_shape(K, Lf, w.n, w.N, w.T)
+    assert shape[3] % 4 == 0 and shape[3] >= P
+    assert _lib.conv_slista_traj_floats(K, Lf, w.n, w.N, w.T) == int(np.prod(shape))
     Z = torch.empty((w.N, m), dtype=torch.float32, device="cuda")
-    traj = torch.empty((w.N, w.T, m), dtype=torch.float32, device="cuda")
+    traj = torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
     _lib.conv_slista_forward_traj(dev(w.filters), dev(w.X), w.lam, dev(alpha), Z, traj)
-    assert torch.equal(traj[:, -1], Z)
+    assert not traj[..., P:].any()  # the padding is written, with zeros
+    codes = traj[..., :P].reshape(w.N, w.T, m)
+    assert torch.equal(codes[:, -1], Z)
     for t in (0, 1, 5, 11):
-        _close(traj[:, t], oracle.pgd(w.D, w.X, w.lam, alpha[:t + 1]))
+        _close(codes[:, t], oracle.pgd(w.D, w.X, w.lam, alpha[:t + 1]))
+
+
+def test_conv_trajectory_padding_and_short_buffer():
+    """P = 113 (maps padded to 116): the padding reads as zeros; a buffer one
+    float short is refused before any launch."""
+    from paper_1905_11071_gb300 import _lib
+    w, alpha = _grad_case(8, 16, 128, 40, 5, seed=6)
+    K, Lf = w.filters.shape
+    P = w.n - Lf + 1
+    shape = _lib.conv_traj_shape(K, Lf, w.n, w.N, w.T)
+    assert shape[3] == 116
+    Z = torch.empty((w.N, K * P), dtype=torch.float32, device="cuda")
+    traj = torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
+    _lib.conv_slista_forward_traj(dev(w.filters), dev(w.X), w.lam, dev(alpha), Z, traj)
+    assert not traj[..., P:].any()
+    lib = _lib.load()
+    rc = lib.conv_slista_forward_traj(_lib._ptr(dev(w.filters)), K, Lf, _lib._ptr(dev(w.X)), w.N, w.n, w.lam,
+                                      _lib._ptr(dev(alpha)), w.T, _lib._ptr(Z), _lib._ptr(traj), traj.numel() - 1, None)
+    assert rc == _lib.SLISTA_ERR_WORKSPACE
 
 
 def test_conv_backward_is_deterministic():
