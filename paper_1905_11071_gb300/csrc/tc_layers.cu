@@ -387,8 +387,13 @@ __global__ void __launch_bounds__(Cfg<MP, SPLIT>::NT, 1) tc_adjoint_kernel(const
     for (int tile = blockIdx.x; tile < ntiles && !E.failed; tile += gridDim.x) {
         const int row = tile * TR + quad * 32 + lane;
         const bool row_ok = (quad * 32 + lane < TR) && row < N;
-        // the warp's rows hold samples: its q and mask lines are worth prefetching
-        const bool quad_live = quad * 32 < TR && tile * TR + quad * 32 < N;
+        // the warp's q lines are worth prefetching when at least 8 of its 32
+        // rows hold samples: a prefetch brings the whole 128-byte line of a
+        // code, the demand loads of a few rows only their 32-byte sectors (a
+        // 66-row tile's third quad has 2 rows: prefetching its lines read
+        // 16 times the bytes it uses)
+        const int quad_rows = min(min(TR, N - tile * TR) - quad * 32, 32);
+        const bool quad_live = quad_rows >= 8;
         auto fetch_masks = [&](int tt) {
             if (row_ok) {
 #pragma unroll
