@@ -304,20 +304,42 @@ def slista_loss(alpha, g: Gram, lam, ckpt_every=None, prec="fp32"):
 
 
 def train_step_sizes(alpha0: torch.Tensor, g: Gram, lam: float, steps: int = 50, lr0: Optional[float] = None,
-                     grow: float = 1.2, max_halvings: int = 20, min_alpha: float = 1e-6, prec="fp32"):
+                     grow: float = 1.2, max_halvings: int = 20, min_alpha: float = 1e-6, prec="fp32",
+                     group=None, loss_fn=None):
     """Full-batch sub-gradient descent with backtracking on the step sizes
     (Appendix E).  A trial step alpha - lr * dalpha is accepted when the loss
     does not increase; otherwise lr is halved (at most max_halvings times).
     After an accepted step lr grows by `grow`.  Steps stay >= min_alpha.
     prec: precision of the forward and of the adjoint ("fp32", "bf16x3",
-    "bf16").  Returns (alpha, history of losses)."""
+    "bf16").  Returns (alpha, history of losses).
+
+    group: a torch.distributed process group whose ranks each hold their own
+    samples (their own g): the loss of every trial and the gradient of every
+    accepted step are summed over the ranks (an all-reduce of 1 and of T
+    values), so every rank takes the same decisions and ends with the same
+    steps - data-parallel training of the loss over all the ranks' samples.
+    loss_fn(alpha) -> scalar loss, differentiable in alpha, replaces the
+    Step-LISTA loss on g (default)."""
+    if loss_fn is None:
+        def loss_fn(a):
+            return slista_loss(a, g, lam, prec=prec)
+    if group is not None:
+        import torch.distributed as dist
+
+    def total(v: torch.Tensor) -> torch.Tensor:
+        """v summed over the ranks of group (float64)."""
+        v = v.detach().double().clone()
+        if group is not None:
+            dist.all_reduce(v, group=group)
+        return v
+
     alpha = alpha0.detach().clone()
     hist = []
     a = alpha.clone().requires_grad_(True)
-    loss = slista_loss(a, g, lam, prec=prec)
+    loss = loss_fn(a)
     loss.backward()
-    cur = float(loss.detach())
-    grad = a.grad.detach().clone()
+    cur = float(total(loss.reshape(1)))
+    grad = total(a.grad).to(alpha.dtype)
     hist.append(cur)
     if lr0 is None:
         gmax = float(grad.abs().max())
@@ -328,11 +350,11 @@ def train_step_sizes(alpha0: torch.Tensor, g: Gram, lam: float, steps: int = 50,
         for _h in range(max_halvings):
             trial = torch.clamp(alpha - lr * grad, min=min_alpha)
             t = trial.clone().requires_grad_(True)
-            tl = slista_loss(t, g, lam, prec=prec)
-            tv = float(tl.detach())
+            tl = loss_fn(t)
+            tv = float(total(tl.reshape(1)))
             if tv <= cur:
                 tl.backward()
-                alpha, cur, grad = trial, tv, t.grad.detach().clone()
+                alpha, cur, grad = trial, tv, total(t.grad).to(alpha.dtype)
                 lr *= grow
                 accepted = True
                 break

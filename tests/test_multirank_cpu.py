@@ -1,7 +1,8 @@
 """The multi-rank logic of bench.py on CPU: two gloo ranks (world_size 2)
 combine their step times by the maximum and report the whole job's samples/s
 (weak scaling: each rank works on its own samples, no data-path collective);
-each rank draws its own seeded samples; the reference arm runs on rank 0 only."""
+each rank draws its own seeded samples; the reference arm runs on rank 0 only;
+data-parallel step-size training sums the loss and gradient over the ranks."""
 import os
 import socket
 
@@ -63,3 +64,59 @@ def test_single_rank_needs_no_process_group():
     assert bench.max_over_ranks(2.5, 1, "cpu") == 2.5
     assert bench.job_throughput(100, 1, 1000.0) == pytest.approx(100.0)
     assert np.isfinite(bench.job_throughput(1, 8, 1e-3))
+
+
+# --- data-parallel step-size training: the loss and its gradient summed over ranks
+
+def _shard(rank, world, T=6, N=40):
+    """Rank r's samples of a fixed least-squares problem in the steps (a
+    stand-in for the Step-LISTA loss, which needs a GPU): rows r, r + world, ..."""
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((N, T))
+    y = A @ np.linspace(0.5, 1.5, T) + 0.1 * rng.standard_normal(N)
+    return A[rank::world], y[rank::world]
+
+
+def _loss_fn(A, y):
+    At, yt = torch.from_numpy(A), torch.from_numpy(y)
+
+    def f(a):  # a sum over the samples, like the Step-LISTA loss (non-smooth too)
+        r = At @ a - yt
+        return (0.5 * r * r + 0.05 * r.abs()).sum()
+    return f
+
+
+def _train_worker(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1905_11071_gb300 import api
+    A, y = _shard(rank, world)
+    a0 = torch.full((A.shape[1],), 0.2, dtype=torch.float64)
+    alpha, hist = api.train_step_sizes(a0, None, 0.0, steps=25, group=dist.group.WORLD, loss_fn=_loss_fn(A, y))
+    out[rank] = (alpha.numpy().tolist(), hist)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_data_parallel_step_training_matches_one_process():
+    """Two gloo ranks, each with half the samples, train the steps with the
+    loss and gradient summed over the ranks: both end with the same steps
+    (bit for bit) and follow the same trajectory as one process holding all
+    the samples (up to the order of the sums)."""
+    from paper_1905_11071_gb300 import api
+    world = 2
+    port = _free_port()
+    with mp.Manager() as man:
+        out = man.dict()
+        mp.spawn(_train_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[0][0] == res[1][0] and res[0][1] == res[1][1]
+    A, y = _shard(0, 1)
+    a0 = torch.full((A.shape[1],), 0.2, dtype=torch.float64)
+    alpha, hist = api.train_step_sizes(a0, None, 0.0, steps=25, loss_fn=_loss_fn(A, y))
+    assert len(hist) == len(res[0][1])
+    np.testing.assert_allclose(res[0][0], alpha.numpy(), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(res[0][1], hist, rtol=1e-10)
+    assert hist[-1] < hist[0]  # the trainer made progress
