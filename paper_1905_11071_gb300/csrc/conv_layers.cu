@@ -154,7 +154,6 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
 }
 
-// 1. y_g = sum_{k in g} d_k * u_k for the padded maps u (map k at u + k PS, data from LF)
 // A thread's work items are it = tid, tid + NB, ... of NG x nb; (g, b) of the
 // first comes from the caller (one division per kernel), the next by stepping.
 struct Item {
@@ -168,6 +167,7 @@ struct Item {
     }
 };
 
+// 1. y_g = sum_{k in g} d_k * u_k for the padded maps u (map k at u + k PS, data from LF)
 template <int LF>
 __device__ __forceinline__ void phase_dz(const float *d, const float *u, float *y, int NG, int nb, Item c, int PS,
                                          int YS)
