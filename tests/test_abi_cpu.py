@@ -198,6 +198,20 @@ def test_python_binding_rejects_cpu_tensors(lib):
         _lib.lasso_gram(D, X, torch.zeros(8, 8), torch.zeros(3, 8), torch.zeros(3, dtype=torch.float64))
 
 
+def test_conv_gradient_binding_layout_and_host_tensors(lib):
+    """conv_traj_shape pads each map to a multiple of 4 codes, and the
+    bindings of the convolutional trajectory forward and adjoint refuse host
+    tensors before calling the library."""
+    torch = pytest.importorskip("torch")
+    assert _lib.conv_traj_shape(8, 16, 128, 10, 5) == (10, 5, 8, 116)
+    assert _lib.conv_traj_shape(3, 5, 37, 2, 1) == (2, 1, 3, 36)
+    F, X, a = torch.zeros(8, 16), torch.zeros(10, 128), torch.full((5,), 0.1)
+    with pytest.raises(ValueError, match="CUDA"):
+        _lib.conv_slista_forward_traj(F, X, 0.1, a, torch.zeros(10, 8 * 113), torch.zeros(10, 5, 8, 116))
+    with pytest.raises(ValueError, match="CUDA"):
+        _lib.conv_slista_backward(F, X, 0.1, a, torch.zeros(10, 5, 8, 116), torch.zeros(5))
+
+
 def test_support_lipschitz_binding_rejects_host_tensors(lib):
     """The binding of lasso_support_lipschitz refuses host tensors before any
     call into the library."""
