@@ -386,6 +386,23 @@ SLISTA_API int conv_slista_forward(const float *filters, int K, int Lf, const fl
                                    float lam, const float *alpha, const double *L, int T, float *Z,
                                    void *stream);
 
+/* Step-LISTA / ISTA forward on a 2-D convolutional dictionary (Section 6's
+ * structured dictionaries, on images): K filters of Lh x Lw taps (filters:
+ * K x Lh x Lw, row-major), images of H x W pixels (X: N x H x W, row-major)
+ * and codes of K maps of Ph x Pw = (H - Lh + 1) x (W - Lw + 1) valid
+ * positions (Z: N x K x Ph x Pw, out), so that
+ *     (D z)[i, j] = sum_k sum_{a,b} d_k[a, b] z_k[i - a, j - b],
+ * and column (k Ph + p) Pw + q of the equivalent dense dictionary holds d_k
+ * with its top-left tap at pixel (p, q).  The layers are Eq. pgd with B z
+ * replaced by z -> D^T (D z); steps alpha[0..T-1] (device, > 0, Eq. steprec)
+ * or, with alpha NULL, 1/L from the device double *L (Eq. ista).  Device
+ * memory throughout; FP32 on the CUDA cores.  Limits: H W <= 16384,
+ * K Lh Lw <= 8192, the filters, two images and one code vector within
+ * 200 KiB of shared memory (SLISTA_ERR_UNSUPPORTED beyond). */
+SLISTA_API int conv2d_slista_forward(const float *filters, int K, int Lh, int Lw, const float *X, int N, int H,
+                                     int W, float lam, const float *alpha, const double *L, int T, float *Z,
+                                     void *stream);
+
 /* Step-size sub-gradient on a 1-D convolutional dictionary: the adjoint of
  * conv_slista_forward's Step-LISTA layers (Eq. steprec), the analogue of
  * slista_forward_traj / slista_backward_traj for the structured

@@ -45,7 +45,7 @@ EXPORTS = [
     "slista_wait_probe", "lista_workspace_bytes", "lista_forward", "slista_set_tile_rows",
     "slista_get_tile_rows", "slista_set_oista_fused", "slista_get_oista_fused", "conv_slista_forward",
     "conv_slista_backward_workspace_bytes", "conv_slista_forward_traj", "conv_slista_backward",
-    "conv_slista_traj_floats",
+    "conv_slista_traj_floats", "conv2d_slista_forward",
 ]
 
 
@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
         lib.conv_slista_forward.argtypes = [vp, i, i, vp, i, i, f, vp, vp, i, vp, vp]
         lib.conv_slista_backward_workspace_bytes.restype = sz
         lib.conv_slista_backward_workspace_bytes.argtypes = [i, i, i, i, i]
+        lib.conv2d_slista_forward.argtypes = [vp, i, i, i, vp, i, i, i, f, vp, vp, i, vp, vp]
         lib.conv_slista_traj_floats.restype = sz
         lib.conv_slista_traj_floats.argtypes = [i, i, i, i, i]
         lib.conv_slista_forward_traj.argtypes = [vp, i, i, vp, i, i, f, vp, i, vp, vp, sz, vp]
@@ -410,6 +411,24 @@ def conv_slista_forward(filters, X, lam, alpha, L, T, Z, stream=None) -> None:
 
 def conv_slista_backward_workspace_bytes(K: int, Lf: int, n: int, N: int, T: int) -> int:
     return int(load().conv_slista_backward_workspace_bytes(int(K), int(Lf), int(n), int(N), int(T)))
+
+
+def conv2d_slista_forward(filters, X, lam, alpha, L, T, Z, stream=None) -> None:
+    """Layers on a 2-D convolutional dictionary: filters K x Lh x Lw, X N x H
+    x W, Z N x K x (H - Lh + 1) x (W - Lw + 1); alpha (T steps) or, when None,
+    1/L (L: 1 double)."""
+    import torch
+    K, Lh, Lw = filters.shape
+    N, H, W = X.shape
+    _need(filters, torch.float32, (K, Lh, Lw), "filters")
+    _need(X, torch.float32, (N, H, W), "X")
+    if alpha is not None:
+        _need(alpha, torch.float32, (T,), "alpha")
+    if L is not None:
+        _need(L, torch.float64, (1,), "L")
+    _need(Z, torch.float32, (N, K, H - Lh + 1, W - Lw + 1), "Z")
+    _check(load().conv2d_slista_forward(_ptr(filters), K, Lh, Lw, _ptr(X), N, H, W, float(lam), _ptr(alpha), _ptr(L),
+                                        int(T), _ptr(Z), _stream(stream)), "conv2d_slista_forward")
 
 
 def conv_slista_traj_floats(K: int, Lf: int, n: int, N: int, T: int) -> int:

@@ -237,6 +237,18 @@ def conv_slista(filters, X, lam, alpha=None, L=None, T=None, stream=None) -> tor
     return Z
 
 
+def conv2d_slista(filters, X, lam, alpha=None, L=None, T=None, stream=None) -> torch.Tensor:
+    """Step-LISTA (alpha: T steps) or ISTA (alpha None, step 1/L) on a 2-D
+    convolutional dictionary (Section 6): filters K x Lh x Lw, X N x H x W
+    images.  Returns the codes, N x K x (H - Lh + 1) x (W - Lw + 1)."""
+    K, Lh, Lw = filters.shape
+    N, H, W = X.shape
+    T = int(alpha.shape[0]) if alpha is not None else int(T)
+    Z = torch.empty((N, K, H - Lh + 1, W - Lw + 1), dtype=torch.float32, device=X.device)
+    _lib.conv2d_slista_forward(filters, X, lam, alpha, L, T, Z, stream=stream)
+    return Z
+
+
 def conv_slista_grad(filters, X, lam, alpha, stream=None):
     """Step-LISTA on a 1-D convolutional dictionary and the sub-gradient of
     sum_i F_{x_i}(z_i^(T)) with respect to its steps alpha (Eq. steprec).

@@ -451,6 +451,25 @@ int conv_slista_forward(const float *filters, int K, int Lf, const float *X, int
     return conv::launch_forward(a, as_stream(stream));
 }
 
+int conv2d_slista_forward(const float *filters, int K, int Lh, int Lw, const float *X, int N, int H, int W,
+                          float lam, const float *alpha, const double *L, int T, float *Z, void *stream)
+{
+    clear_error();
+    SLISTA_REQUIRE(K >= 1 && Lh >= 1 && Lw >= 1 && H >= Lh && W >= Lw && N >= 0 && T >= 0, SLISTA_ERR_ARG,
+                   "conv2d_slista_forward: bad sizes K=%d Lh=%d Lw=%d H=%d W=%d N=%d T=%d (need H >= Lh >= 1, "
+                   "W >= Lw >= 1)", K, Lh, Lw, H, W, N, T);
+    SLISTA_REQUIRE(conv::supported2d(K, Lh, Lw, H, W), SLISTA_ERR_UNSUPPORTED,
+                   "conv2d_slista_forward: H W <= 16384, K Lh Lw <= 8192 and the filters, two images and one code "
+                   "vector within 200 KiB of shared memory (got K=%d Lh=%d Lw=%d H=%d W=%d)", K, Lh, Lw, H, W);
+    SLISTA_REQUIRE(filters, SLISTA_ERR_ARG, "conv2d_slista_forward: filters must not be NULL");
+    SLISTA_REQUIRE(alpha || L, SLISTA_ERR_ARG, "conv2d_slista_forward: alpha or L must be given");
+    SLISTA_REQUIRE(N == 0 || (X && Z), SLISTA_ERR_ARG, "conv2d_slista_forward: X and Z must not be NULL");
+    int rc = check_lam(lam);
+    if (rc) return rc;
+    Conv2dArgs a{filters, K, Lh, Lw, X, N, H, W, lam, alpha, L, T, Z};
+    return conv::launch_forward2d(a, as_stream(stream));
+}
+
 static int conv_traj_check(const char *fn, const float *filters, int K, int Lf, const float *alpha, int N, int n,
                            int T, float lam)
 {

@@ -83,6 +83,75 @@ __global__ void __launch_bounds__(NT) conv_pgd_kernel(const float *__restrict__ 
     }
 }
 
+// The same layers on a 2-D convolutional dictionary: K filters of Lh x Lw
+// taps on H x W images, codes of K maps of Ph x Pw = (H - Lh + 1) x
+// (W - Lw + 1) valid positions (images and maps row-major), so that
+//   (D z)[i, j]      = sum_k sum_{a, b} d_k[a, b] z_k[i - a, j - b]
+//   (D^T r)_k[p, q]  = sum_{a, b} d_k[a, b] r[p + a, q + b]
+// One CTA per image at a time with the filters, the image, the residual and
+// the codes in shared memory; a thread per pixel of D z (the filters summed
+// in order, the taps limited to valid code positions) and per code of
+// D^T r.  Consecutive threads take consecutive pixels or codes, so their
+// shared-memory reads are consecutive words.
+__global__ void __launch_bounds__(NT) conv2d_pgd_kernel(const float *__restrict__ F, int K, int Lh, int Lw,
+                                                        const float *__restrict__ X, int N, int H, int W, float lam,
+                                                        const float *__restrict__ alpha,
+                                                        const double *__restrict__ Lp, int T, float *__restrict__ Z)
+{
+    extern __shared__ float sm[];
+    const int Ph = H - Lh + 1, Pw = W - Lw + 1, PP = Ph * Pw, m = K * PP, n = H * W, LL = Lh * Lw;
+    float *d = sm;          // K x Lh x Lw
+    float *x = d + K * LL;  // H x W
+    float *r = x + n;       // H x W: D z - x
+    float *z = r + n;       // K x Ph x Pw
+    const int tid = threadIdx.x;
+    for (int e = tid; e < K * LL; e += NT) d[e] = __ldg(F + e);
+    const float a_const = alpha ? 0.0f : (float)(1.0 / __ldg(Lp));
+#pragma unroll 1
+    for (int s = blockIdx.x; s < N; s += gridDim.x) {
+        __syncthreads();  // the previous image's codes are stored
+        for (int e = tid; e < n; e += NT) x[e] = __ldg(X + (size_t)s * n + e);
+        for (int e = tid; e < m; e += NT) z[e] = 0.0f;
+        __syncthreads();
+#pragma unroll 1
+        for (int t = 0; t < T; ++t) {
+            const float a = alpha ? __ldg(alpha + t) : a_const;
+            const float thr = __fmul_rn(a, lam);
+            // r = D z - x
+#pragma unroll 1
+            for (int e = tid; e < n; e += NT) {
+                const int i = e / W, j = e - i * W;
+                const int a0 = max(0, i - Ph + 1), a1 = min(Lh - 1, i);
+                const int b0 = max(0, j - Pw + 1), b1 = min(Lw - 1, j);
+                float acc = 0.0f;
+                for (int k = 0; k < K; ++k) {
+                    const float *dk = d + k * LL;
+                    const float *zk = z + k * PP;
+                    for (int ta = a0; ta <= a1; ++ta)
+                        for (int tb = b0; tb <= b1; ++tb)
+                            acc = fmaf(dk[ta * Lw + tb], zk[(i - ta) * Pw + (j - tb)], acc);
+                }
+                r[e] = acc - x[e];
+            }
+            __syncthreads();
+            // z = ST(z - a D^T r, a lam)
+#pragma unroll 1
+            for (int e = tid; e < m; e += NT) {
+                const int k = e / PP, pq = e - k * PP, p = pq / Pw, q = pq - p * Pw;
+                const float *dk = d + k * LL;
+                const float *rp = r + p * W + q;
+                float g = 0.0f;
+                for (int ta = 0; ta < Lh; ++ta)
+                    for (int tb = 0; tb < Lw; ++tb) g = fmaf(dk[ta * Lw + tb], rp[ta * W + tb], g);
+                const float u = fmaf(-a, g, z[e]);
+                z[e] = copysignf(fmaxf(fabsf(u) - thr, 0.0f), u);
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < m; e += NT) Z[(size_t)s * m + e] = z[e];
+    }
+}
+
 // The same layers with register blocking, for filters of at most LF taps
 // (zero-padded to LF, LF a multiple of 4), in CTAs of NB threads.  The
 // filters are taken in groups of KG (K rounded up with all-zero filters); a
@@ -543,6 +612,36 @@ int launch_adj(const ConvArgs &a, const float *traj, float *dalpha, void *ws, cu
 }
 
 }  // namespace
+
+size_t smem2d_bytes(int K, int Lh, int Lw, int H, int W)
+{
+    return sizeof(float) * ((size_t)K * Lh * Lw + 2 * (size_t)H * W + (size_t)K * (H - Lh + 1) * (W - Lw + 1));
+}
+
+bool supported2d(int K, int Lh, int Lw, int H, int W)
+{
+    return K >= 1 && Lh >= 1 && Lw >= 1 && H >= Lh && W >= Lw && (long long)H * W <= 16384 &&
+           (long long)K * Lh * Lw <= 8192 && smem2d_bytes(K, Lh, Lw, H, W) <= 200 * 1024;
+}
+
+int launch_forward2d(const Conv2dArgs &a, cudaStream_t st)
+{
+    const size_t m = (size_t)a.K * (a.H - a.Lh + 1) * (a.W - a.Lw + 1);
+    if (a.N == 0) return SLISTA_OK;
+    if (a.T == 0) {
+        SLISTA_CUDA_TRY(cudaMemsetAsync(a.Z, 0, sizeof(float) * (size_t)a.N * m, st));
+        return SLISTA_OK;
+    }
+    const size_t smem = smem2d_bytes(a.K, a.Lh, a.Lw, a.H, a.W);
+    SLISTA_CUDA_TRY(allow_smem(conv2d_pgd_kernel, smem));
+    int per_sm = 0;
+    SLISTA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv2d_pgd_kernel, NT, smem));
+    const long long want = (long long)num_sms() * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(a.N < want ? a.N : want);
+    conv2d_pgd_kernel<<<grid, NT, smem, st>>>(a.F, a.K, a.Lh, a.Lw, a.X, a.N, a.H, a.W, a.lam, a.alpha, a.L, a.T,
+                                              a.Z);
+    return check_launch("conv2d_pgd_kernel");
+}
 
 size_t smem_bytes(int K, int Lf, int n) { return sizeof(float) * ((size_t)K * Lf + 2 * (size_t)n + (size_t)K * (n - Lf + 1)); }
 

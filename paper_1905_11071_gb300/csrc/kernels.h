@@ -68,6 +68,18 @@ struct ConvArgs {
     float *Z;            // N x K (n - Lf + 1)
 };
 
+struct Conv2dArgs {
+    const float *F;      // K x Lh x Lw filters
+    int K, Lh, Lw;
+    const float *X;      // N x H x W images
+    int N, H, W;
+    float lam;
+    const float *alpha;  // T steps, or nullptr: 1 / L
+    const double *L;
+    int T;
+    float *Z;            // N x K x (H - Lh + 1) x (W - Lw + 1)
+};
+
 struct ListaArgs {
     const float *D;      // n x m
     int n, m;
@@ -222,6 +234,9 @@ size_t traj_floats(int K, int Lf, int n, int N, int T);
 size_t backward_ws_bytes(int K, int Lf, int n, int N, int T);
 int launch_forward_traj(const ConvArgs &a, float *traj, cudaStream_t st);
 int launch_backward(const ConvArgs &a, const float *traj, float *dalpha, void *ws, cudaStream_t st);
+// layers on a 2-D convolutional dictionary (FP32, CUDA cores)
+bool supported2d(int K, int Lh, int Lw, int H, int W);
+int launch_forward2d(const Conv2dArgs &a, cudaStream_t st);
 }
 
 }  // namespace slista

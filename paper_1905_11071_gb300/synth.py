@@ -212,6 +212,56 @@ def conv_1d(seed: int = 0, N: int = 10000, T: int = 40, K: int = 8, Lf: int = 16
     return ConvWorkload("conv1d_%dx%d_n%d" % (K, Lf, n), D, X, lam_fraction(D, X, frac), T, seed, F)
 
 
+def conv2d_filters(K: int, Lh: int, Lw: int, rng: np.random.Generator) -> np.ndarray:
+    """K filters of Lh x Lw taps with N(0,1) entries, each scaled to unit
+    (Frobenius) norm (float32, K x Lh x Lw)."""
+    Fh = rng.standard_normal((K, Lh, Lw))
+    Fh /= np.linalg.norm(Fh.reshape(K, -1), axis=1)[:, None, None]
+    return Fh.astype(np.float32)
+
+
+def conv2d_dictionary(filters: np.ndarray, H: int, W: int) -> np.ndarray:
+    """The dense (H W) x K Ph Pw matrix of a 2-D convolutional dictionary on
+    H x W images (valid positions, Ph = H - Lh + 1, Pw = W - Lw + 1; images and
+    code maps row-major): column (k Ph + p) Pw + q holds filter k with its
+    top-left tap at pixel (p, q), so D z = sum_k d_k * z_k (the full 2-D
+    convolution of each code map with its filter).  Entries are copies of the
+    float32 filter values."""
+    K, Lh, Lw = filters.shape
+    Ph, Pw = H - Lh + 1, W - Lw + 1
+    D = np.zeros((H * W, K * Ph * Pw), dtype=np.float32)
+    img = np.zeros((H, W), dtype=np.float32)
+    for k in range(K):
+        for p in range(Ph):
+            for q in range(Pw):
+                img[:] = 0.0
+                img[p:p + Lh, q:q + Lw] = filters[k]
+                D[:, (k * Ph + p) * Pw + q] = img.reshape(-1)
+    return D
+
+
+@dataclasses.dataclass
+class Conv2dWorkload(Workload):
+    """A batch of H x W images on a 2-D convolutional dictionary: filters
+    (K x Lh x Lw) and the dense D they define (for the FP64 oracle)."""
+    filters: np.ndarray = None
+    H: int = 0
+    W: int = 0
+
+
+def conv_2d(seed: int = 0, N: int = 2000, T: int = 30, K: int = 8, Lh: int = 5, Lw: int = 5, H: int = 28,
+            W: int = 28, density: float = 0.01, frac: float = 0.1) -> Conv2dWorkload:
+    """Structured-dictionary case on images (Section 6): K unit-norm Lh x Lw
+    filters on H x W images, m = K (H - Lh + 1)(W - Lw + 1) codes;
+    x = D z0 + 0.01 noise with z0 = Bernoulli(density) N(0, 1); lam = frac lam_max."""
+    rng = np.random.default_rng(seed)
+    F = conv2d_filters(K, Lh, Lw, rng)
+    D = conv2d_dictionary(F, H, W)
+    X = sparse_model_samples(D, N, density, 0.01, rng)
+    return Conv2dWorkload("conv2d_%dx%dx%d_%dx%d" % (K, Lh, Lw, H, W), D, X, lam_fraction(D, X, frac), T, seed, F,
+                          H, W)
+
+
 def step_sizes(T: int, base: float, spread: float, seed: int) -> np.ndarray:
     """T positive step sizes base * U[1 - spread, 1 + spread] (float32)."""
     rng = np.random.default_rng(seed)

@@ -190,6 +190,18 @@ def test_conv_gradient_validation_without_gpu(lib):
                                     None) == _lib.SLISTA_ERR_ARG
 
 
+def test_conv2d_validation_without_gpu(lib):
+    """The 2-D convolutional forward refuses bad sizes, images too large for
+    its shared memory, missing steps and a negative lambda before any launch."""
+    vp = ctypes.c_void_p(1)
+    assert lib.conv2d_slista_forward(vp, 4, 5, 5, vp, 8, 4, 16, 0.1, vp, None, 5, vp, None) == _lib.SLISTA_ERR_ARG
+    assert lib.conv2d_slista_forward(vp, 4, 5, 0, vp, 8, 16, 16, 0.1, vp, None, 5, vp, None) == _lib.SLISTA_ERR_ARG
+    assert lib.conv2d_slista_forward(vp, 4, 5, 5, vp, 8, 256, 256, 0.1, vp, None, 5, vp,
+                                     None) == _lib.SLISTA_ERR_UNSUPPORTED
+    assert lib.conv2d_slista_forward(vp, 4, 5, 5, vp, 8, 16, 16, 0.1, None, None, 5, vp, None) == _lib.SLISTA_ERR_ARG
+    assert lib.conv2d_slista_forward(vp, 4, 5, 5, vp, 8, 16, 16, -0.1, vp, None, 5, vp, None) == _lib.SLISTA_ERR_ARG
+
+
 def test_python_binding_rejects_cpu_tensors(lib):
     torch = pytest.importorskip("torch")
     D = torch.zeros(4, 8)

@@ -13,7 +13,11 @@ oracle iterating with the equivalent dense dictionary:
   against the oracle's adjoint on the dense dictionary (relative 1e-4, the
   dense FP32 path's bound), its trajectory against the oracle's layers, its
   degenerate cases (zero codes, T = 1, N = 0) and its run-to-run identity;
-  at the benchmark's size, additivity over samples and sampled rows.
+  at the benchmark's size, additivity over samples and sampled rows;
+* 2-D convolutional dictionaries (images): codes against the oracle on the
+  equivalent dense dictionary for learned steps and ISTA's 1/L, odd shapes
+  (non-square filters, one position per column of a map, 1 x 1 filters), zero
+  codes above lam_max, and sampled rows of a 2000-image batch.
 """
 import numpy as np
 import pytest
@@ -234,3 +238,65 @@ def test_conv_backward_full_size():
     _, dr = A.conv_slista_grad(F, X[rows].contiguous(), w.lam, a)
     do, _ = oracle.slista_grad(w.D, w.X[rows], w.lam, alpha)
     assert _rel(dr, do) <= GRAD_TOL
+
+
+
+# --- 2-D convolutional dictionaries
+
+def _workload2d(K, Lh, Lw, H, W, N, T, seed=0):
+    return synth.conv_2d(seed=seed, N=N, T=T, K=K, Lh=Lh, Lw=Lw, H=H, W=W)
+
+
+def _images(w):
+    return dev(w.X.reshape(w.X.shape[0], w.H, w.W))
+
+
+def _L(D):
+    """Largest eigenvalue of D^T D from the smaller Gram D D^T (numpy, FP64):
+    the scale of the test's step sizes (the oracle's Jacobi works on the
+    m x m Gram, too slow at m = 4608)."""
+    D = D.astype(np.float64)
+    return float(np.linalg.eigvalsh(D @ D.T)[-1])
+
+
+def test_conv2d_slista_and_ista_match_oracle():
+    from paper_1905_11071_gb300 import api as A
+    w = _workload2d(4, 5, 5, 16, 16, 200, 20)
+    alpha = synth.step_sizes(w.T, 1.0 / _L(w.D), 0.3, seed=3)
+    Z = A.conv2d_slista(dev(w.filters), _images(w), w.lam, dev(alpha))
+    assert Z.shape == (w.N, 4, 12, 12)
+    _close(Z.reshape(w.N, -1), oracle.pgd(w.D, w.X, w.lam, alpha))
+    g = A.gram(dev(w.D), dev(w.X))  # L of the dictionary, on the GPU
+    Zi = A.conv2d_slista(dev(w.filters), _images(w), w.lam, L=g.L, T=w.T)
+    _close(Zi.reshape(w.N, -1), oracle.ista(w.D, w.X, w.lam, oracle.lipschitz(w.D), w.T))  # m = 576
+
+
+@pytest.mark.parametrize("K,Lh,Lw,H,W,N", [(3, 3, 4, 9, 11, 65), (2, 7, 2, 7, 5, 33), (5, 1, 1, 6, 6, 17),
+                                           (16, 3, 3, 12, 10, 129)])
+def test_conv2d_odd_shapes(K, Lh, Lw, H, W, N):
+    from paper_1905_11071_gb300 import api as A
+    w = _workload2d(K, Lh, Lw, H, W, N, 15, seed=K + H)
+    alpha = synth.step_sizes(w.T, 1.0 / _L(w.D), 0.3, seed=K)
+    Z = A.conv2d_slista(dev(w.filters), _images(w), w.lam, dev(alpha))
+    _close(Z.reshape(w.N, -1), oracle.pgd(w.D, w.X, w.lam, alpha))
+
+
+def test_conv2d_zero_above_lambda_max_and_empty_batch():
+    from paper_1905_11071_gb300 import api as A
+    w = _workload2d(4, 5, 5, 16, 16, 40, 8, seed=5)
+    lam = float(np.float32(np.abs(w.X.astype(np.float64) @ w.D.astype(np.float64)).max() * 1.001))
+    alpha = np.full(w.T, 1.0 / _L(w.D), dtype=np.float32)
+    assert not A.conv2d_slista(dev(w.filters), _images(w), lam, dev(alpha)).any()
+    X0 = torch.empty((0, w.H, w.W), dtype=torch.float32, device="cuda")
+    assert A.conv2d_slista(dev(w.filters), X0, w.lam, dev(alpha)).shape == (0, 4, 12, 12)
+
+
+def test_conv2d_batch_sampled_rows():
+    """2000 images of 28 x 28 on 8 filters of 5 x 5 (m = 4608 codes), T = 30,
+    one launch: 16 sampled images against the oracle (images are independent)."""
+    from paper_1905_11071_gb300 import api as A
+    w = synth.conv_2d()
+    alpha = synth.step_sizes(w.T, 1.0 / _L(w.D), 0.2, seed=9)
+    Z = A.conv2d_slista(dev(w.filters), _images(w), w.lam, dev(alpha))
+    rows = np.random.default_rng(4).choice(w.N, size=16, replace=False)
+    _close(Z.reshape(w.N, -1)[rows], oracle.pgd(w.D, w.X[rows], w.lam, alpha))

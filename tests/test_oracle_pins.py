@@ -605,3 +605,25 @@ def test_convolutional_dictionary_is_the_convolution():
         np.testing.assert_allclose(D @ z, Dz, rtol=1e-12, atol=1e-12)
         Dtr = np.concatenate([np.correlate(r, F[k].astype(np.float64), mode="valid") for k in range(K)])
         np.testing.assert_allclose(D.T @ r, Dtr, rtol=1e-12, atol=1e-12)
+
+
+def test_2d_convolutional_dictionary_is_the_convolution():
+    """The dense matrix of a 2-D convolutional dictionary against the operator
+    it stands for: D z = sum_k d_k * z_k (scipy's full 2-D convolution of each
+    code map with its filter, (Ph + Lh - 1) x (Pw + Lw - 1) = H x W) and
+    (D^T r)_k = the valid 2-D correlation of r with d_k; unit-norm columns."""
+    signal = pytest.importorskip("scipy.signal")
+    rng = np.random.default_rng(12)
+    for (K, Lh, Lw, H, W) in [(3, 3, 4, 9, 11), (4, 5, 5, 16, 16), (2, 7, 2, 7, 5)]:
+        F = synth.conv2d_filters(K, Lh, Lw, rng)
+        D = synth.conv2d_dictionary(F, H, W).astype(np.float64)
+        Ph, Pw = H - Lh + 1, W - Lw + 1
+        assert D.shape == (H * W, K * Ph * Pw)
+        np.testing.assert_allclose(np.linalg.norm(D, axis=0), 1.0, rtol=1e-6)
+        z = rng.standard_normal((K, Ph, Pw))
+        r = rng.standard_normal((H, W))
+        Fd = F.astype(np.float64)
+        Dz = sum(signal.convolve2d(z[k], Fd[k], mode="full") for k in range(K))
+        np.testing.assert_allclose(D @ z.reshape(-1), Dz.reshape(-1), rtol=1e-12, atol=1e-12)
+        Dtr = np.stack([signal.correlate2d(r, Fd[k], mode="valid") for k in range(K)])
+        np.testing.assert_allclose(D.T @ r.reshape(-1), Dtr.reshape(-1), rtol=1e-12, atol=1e-12)
