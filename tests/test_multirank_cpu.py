@@ -44,7 +44,7 @@ def _worker(rank, world, port, out):
 def test_two_gloo_ranks_combine_by_max():
     world = 2
     port = _free_port()
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
@@ -108,7 +108,7 @@ def test_data_parallel_step_training_matches_one_process():
     from paper_1905_11071_gb300 import api
     world = 2
     port = _free_port()
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.spawn(_train_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
