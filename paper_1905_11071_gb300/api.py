@@ -264,6 +264,8 @@ def conv_slista_grad(filters, X, lam, alpha, stream=None):
     ws = workspace(_lib.conv_slista_backward_workspace_bytes(K, Lf, n, N, T), X.device, "conv_bwd")
     _lib.conv_slista_forward_traj(filters, X, lam, alpha, Z, traj, stream=stream)
     _lib.conv_slista_backward(filters, X, lam, alpha, traj, dalpha, ws=ws, stream=stream)
+    if stream is not None:
+        traj.record_stream(stream)  # freed here, still read on that stream
     return Z, dalpha
 
 
